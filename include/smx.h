@@ -1,0 +1,215 @@
+/*
+ * smx.h -- C ABI of the GB300 (sm_103a) leapfrog for the spline geometric
+ * discretisation of Maxwell's equations of Kapidani & Vazquez, "High order
+ * geometric methods with splines: fast solution with explicit time-stepping
+ * for Maxwell equations" (arXiv 2302.04979), scheme 2 (Sec. 3.4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Fields (Sec. 2.4, field placement; Sec. 3.1):
+ *   E in X^1_{h,0} (primal 1-forms, degrees p-1/p, zero tangential trace)
+ *   B in X^2_{h,0} (primal 2-forms)
+ *   H in X~^1      (dual 1-forms, degrees p-2/p-1)
+ *   D in X~^2      (dual 2-forms)
+ * len(e) = len(d) = N_e and len(b) = len(h) = N_h (dim X^1_{h,0} = dim X~^2,
+ * dim X^2_{h,0} = dim X~^1, Sec. 2.3).  With n_a = nel_a + p_a:
+ *   E/D component c has (n-1) functions along axis c and (n-2) along the others;
+ *   B/H component c has (n-2) functions along axis c and (n-1) along the others.
+ * Layout: the three components are stored one after the other (x, y, z; for
+ * 2-forms the coefficients of dy^dz, dz^dx, dx^dy); inside a component the
+ * index is i + N_x (j + N_y k) -- x fastest, the vec convention of Sec. 4.2.
+ * All field pointers are DEVICE pointers to FP64 arrays owned by the caller
+ * (normally torch tensors); the library never allocates device memory.
+ * All device work is enqueued on the stream set with smx_set_stream (default
+ * the legacy default stream) and returns after enqueue unless stated.
+ * Every call returns SMX_OK (0) or a negative status; smx_strerror names it.
+ * A call that fails argument checks enqueues nothing.
+ */
+#ifndef SMX_H
+#define SMX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SMX_OK 0
+#define SMX_EINVAL (-1)      /* bad argument: p < 2, nel < 1, null pointer, nsteps < 0, dt <= 0 ... */
+#define SMX_EGEOM (-2)       /* det J_F <= 0 (or non-finite) at some quadrature point */
+#define SMX_EMAT (-3)        /* eps or mu <= 0 or non-finite */
+#define SMX_ECUDA (-4)       /* a CUDA runtime call failed (launch, copy, ...) */
+#define SMX_ENONFINITE (-5)  /* a reduction saw NaN or Inf in the fields */
+#define SMX_ESTATE (-6)      /* workspace missing or too small */
+#define SMX_ENOMEM (-7)      /* host allocation failed */
+#define SMX_ESINGULAR (-8)   /* a 1D pairing factor has a (near) zero pivot */
+
+/* ---- geometry map F : (0,1)^3 -> Omega (Sec. 2.3) ---- */
+#define SMX_GEOM_IDENTITY 0  /* F = identity: the unit-cube cavity of Sec. 5.1.1 */
+#define SMX_GEOM_SINE_BUMP 1 /* F_i = x_i + a sin(pi x) sin(pi y) sin(pi z), a = geom_amplitude */
+
+/* ---- material description (eps or mu) ---- */
+#define SMX_MAT_CONST 0      /* one value everywhere */
+#define SMX_MAT_BLOCKS 1     /* piecewise constant on a grid of element blocks aligned with the mesh */
+#define SMX_MAT_POINTWISE 2  /* host callback evaluated at the physical quadrature points (setup only) */
+
+/* ---- field selectors ---- */
+#define SMX_FIELD_E 0
+#define SMX_FIELD_B 1
+#define SMX_FIELD_H 2
+#define SMX_FIELD_D 3
+
+/* Host callback for SMX_MAT_POINTWISE: out[i] = material at the physical point
+ * (xyz[3i], xyz[3i+1], xyz[3i+2]), i < n.  Called only inside smx_create. */
+typedef void (*smx_material_fn)(int64_t n, const double* xyz, double* out, void* user);
+
+typedef struct {
+    int kind;                   /* SMX_MAT_* */
+    double value;               /* SMX_MAT_CONST */
+    int blocks[3];              /* SMX_MAT_BLOCKS: block counts along x, y, z; each divides nel */
+    const double* block_values; /* SMX_MAT_BLOCKS: host array, blocks[0]*blocks[1]*blocks[2], x fastest */
+    smx_material_fn fn;         /* SMX_MAT_POINTWISE */
+    void* user;                 /* passed to fn */
+} smx_material;
+
+typedef struct {
+    int p[3];              /* spline degree per axis, p >= 2 (Sec. 2.3; per-axis degrees, Eq. tensor_K) */
+    int nel[3];            /* uniform elements per axis, nel >= 1 (maximal smoothness, Sec. 5) */
+    int geometry;          /* SMX_GEOM_* */
+    double geom_amplitude; /* SMX_GEOM_SINE_BUMP amplitude a; |a| < 1/(3 pi) keeps det J_F > 0 */
+    smx_material eps;      /* permittivity: weights M~^2_{1/eps} (Eq. discrete2_hodge_eps) */
+    smx_material mu;       /* permeability: weights M^2_{1/mu} (Eq. discrete2_hodge_mu) */
+} smx_params;
+
+typedef struct smx_ctx smx_ctx;
+
+/* Build a context: knots, 1D pairing matrices G-hat, M-hat and their banded LU
+ * (Sec. 4.1-4.3, Table 1 setup rows), Hodge tables (1D masses or quadrature
+ * metric) -- all on the host in FP64.  Owns host memory only.
+ * Errors: SMX_EINVAL, SMX_EGEOM, SMX_EMAT, SMX_ESINGULAR, SMX_ENOMEM. */
+int smx_create(const smx_params* params, smx_ctx** out);
+
+/* Free the context's host memory (the bound workspace stays the caller's). */
+int smx_destroy(smx_ctx* ctx);
+
+/* Static text for a status code. */
+const char* smx_strerror(int status);
+
+/* N_e = dim X^1_{h,0} = dim X~^2, N_h = dim X^2_{h,0} = dim X~^1 (Sec. 2.3). */
+int smx_sizes(const smx_ctx* ctx, int64_t* n_e, int64_t* n_h);
+
+/* Shape of component comp of a field: shape[0] = N_x, shape[1] = N_y, shape[2] = N_z. */
+int smx_comp_shape(const smx_ctx* ctx, int field, int comp, int64_t shape[3]);
+
+/* Device workspace size in bytes (tables + scratch).  The caller allocates it
+ * (256-byte aligned) and binds it; the library never calls cudaMalloc. */
+int smx_workspace_bytes(const smx_ctx* ctx, size_t* bytes);
+
+/* Bind device memory of at least smx_workspace_bytes bytes and upload the
+ * tables into it (synchronous on the context stream).  Errors: SMX_ESTATE if
+ * too small or misaligned, SMX_ECUDA. */
+int smx_bind_workspace(smx_ctx* ctx, void* device_ptr, size_t bytes);
+
+/* Stream for all later device work (a cudaStream_t passed as void*; NULL =
+ * legacy default stream). */
+int smx_set_stream(smx_ctx* ctx, void* stream);
+
+/* b += alpha * D^1 e: primal curl by the +-1 incidence matrix (Eq. discrete2_faraday,
+ * Remark on incidence matrices after Table 1).  e: N_e, b: N_h, device, no aliasing. */
+int smx_curl_primal(smx_ctx* ctx, const double* e, double* b, double alpha);
+
+/* d += alpha * (D~^1 h - s * jhat): dual curl plus the current source
+ * (Eq. discrete2_ampere).  jhat (N_e, device) may be NULL, then s is ignored. */
+int smx_curl_dual(smx_ctx* ctx, const double* h, double* d, double alpha,
+                  const double* jhat, double s);
+
+/* y = M x, the Hodge mass apply: field SMX_FIELD_B -> M^2_{1/mu} (N_h),
+ * SMX_FIELD_D -> M~^2_{1/eps} (N_e) (Eq. discrete2_hodge_mu / _eps right-hand
+ * sides, Sec. 3.4).  Matrix free; y is overwritten; x and y must not alias. */
+int smx_hodge_apply(smx_ctx* ctx, int field, const double* x, double* y);
+
+/* x = K^{-1} y, the pairing solve by per-axis 1D banded solves (Sec. 4.2,
+ * Eq. kroninverse): which = SMX_FIELD_E solves K_1 e = y (y in the D layout,
+ * N_e); which = SMX_FIELD_H solves K~_1 h = y (y in the B layout, N_h).
+ * y is left unchanged; x may equal y (in place). */
+int smx_pairing_solve(smx_ctx* ctx, int which, const double* y, double* x);
+
+/* One discrete Hodge star of scheme 2: e = K_1^{-1} M~^2_{1/eps} d (field SMX_FIELD_D,
+ * out = e) or h = K~_1^{-1} M^2_{1/mu} b (field SMX_FIELD_B, out = h)
+ * (Eq. discrete2_hodge_eps / _mu).  Uses the workspace scratch. */
+int smx_hodge_star(smx_ctx* ctx, int field, const double* x, double* out);
+
+/* nsteps kick-drift-kick leapfrog steps of scheme 2 (Sec. 3.4, Sec. 4.2):
+ *   b -= dt/2 D^1 e;  h = K~_1^{-1} M b;  d += dt (D~^1 h - amp[n] jhat);
+ *   e = K_1^{-1} M~ d;  b -= dt/2 D^1 e.
+ * d, e: N_e; b, h: N_h; device, updated in place.  On entry e must be
+ * consistent with d (e.g. from smx_hodge_star); on return e is consistent
+ * with the new d and h holds the last half-step value.  jhat (N_e) and amp
+ * (nsteps values, amp[n] = s(t_n + dt/2)) are device arrays; jhat = NULL
+ * means J = 0 (amp ignored).  Errors: SMX_EINVAL (dt <= 0 or non-finite,
+ * nsteps < 0), SMX_ESTATE, SMX_ECUDA. */
+int smx_step(smx_ctx* ctx, double* d, double* b, double* e, double* h,
+             const double* jhat, const double* amp, double dt, int nsteps);
+
+/* Energies at a synchronised time (Eq. energy_matrix_wedge, Sec. 3.4):
+ * out[0] = E_h = 1/2 (d^T M~ d + b^T M b);
+ * out[1] = W = E_h - dt^2/8 (D^1 e)^T M (D^1 e), the quantity the leapfrog
+ * conserves exactly (e may be NULL: then out[1] = out[0]).
+ * Synchronises the stream.  Returns SMX_ENONFINITE if a sum is NaN or Inf. */
+int smx_energy(smx_ctx* ctx, const double* d, const double* b, const double* e,
+               double dt, double out[2]);
+
+/* Largest stable leapfrog dt: 2/sqrt(lambda_max) of L M L^T M~ with
+ * L = D~^1 K~_1^{-1} (Sec. 5.2 CFL), by power iteration on the device from a
+ * fixed pseudo-random start; stops after iters or when the Rayleigh quotient
+ * changes by less than tol (relative).  Uses 3 device vectors of the caller:
+ * v (N_e), w (N_e), t (N_h).  Synchronises the stream. */
+int smx_cfl(smx_ctx* ctx, int iters, double tol, double* v, double* w, double* t,
+            double* dt_max);
+
+/* nsteps leapfrog steps on HOST state: copies d, b, e (host, FP64) into the
+ * workspace's state vectors, runs smx_step there, copies d, b, e, h back and
+ * synchronises.  Host buffers should be pinned for asynchronous copies.
+ * jhat and amp as in smx_step (device pointers or NULL). */
+int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
+                  const double* jhat, const double* amp, double dt, int nsteps);
+
+/* Kernel accounting for benchmarks.  smx_launch_count returns the number of
+ * device kernels this context has launched so far (memsets and copies are not
+ * counted).  smx_set_timing(ctx, 1) brackets every later launch with CUDA
+ * events on the context stream; smx_kernel_times synchronises, adds up the
+ * bracketed durations per kernel class and clears them:
+ *   0 curl_primal, 1 curl_dual, 2 hodge_block, 3 hodge_quad,
+ *   4 solve along x, 5 solve along y, 6 solve along z, 7 reductions.
+ * ms[8] receives milliseconds, counts[8] launches per class. */
+#define SMX_NCLASS 8
+int smx_launch_count(const smx_ctx* ctx, int64_t* n);
+int smx_set_timing(smx_ctx* ctx, int enable);
+int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);
+
+/* Algorithmic work of ONE launch of kernel class cls (numbering above) on
+ * field (SMX_FIELD_*: the field the launch writes -- B or H for curl_primal /
+ * solves of K~_1 / the M^2 Hodge, D or E for curl_dual / solves of K_1 / the
+ * M~^2 Hodge): FP64 flops the kernel's algorithm performs (an FMA counts 2)
+ * and the bytes it must move to and from device memory at minimum (each input
+ * read once, each output written once).  SMX_EINVAL for a class that the
+ * context does not launch for that field. */
+int smx_kernel_work(const smx_ctx* ctx, int cls, int field, double* flops, double* bytes);
+
+/* Diagnostics for tests: copy the host-side banded LU of one 1D factor.
+ * axis 0..2; which 0 = G-hat, 1 = M-hat, 2 = G-hat^T, 3 = M-hat^T (Sec. 4.1).
+ * dense_out receives the n x n factor matrix A (row-major) rebuilt from the
+ * stored L and U, so tests can compare it with the definition. */
+int smx_factor_matrix(const smx_ctx* ctx, int axis, int which, int64_t* n, double* dense_out);
+
+/* Which Hodge kernel a field uses: 0 = block Kronecker (identity map with
+ * block-constant material), 1 = quadrature (curved map or pointwise material). */
+int smx_hodge_mode(const smx_ctx* ctx, int field, int* mode);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMX_H */

@@ -1,0 +1,850 @@
+// C ABI of the scheme-2 leapfrog (include/smx.h): host setup, workspace
+// binding and the enqueue of the device kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/smx.h"
+#include "internal.h"
+#include "setup.h"
+
+using namespace smx;
+
+namespace {
+
+struct HodgeHost {
+    int mode = 0;  // 0 block Kronecker, 1 quadrature
+    // block mode
+    int ntile[3] = {0, 0, 0};
+    std::vector<int> tf0[3], tlen[3];
+    std::vector<double> tmat[3];
+    std::vector<double> gamma;
+    // quadrature mode
+    int q[3] = {0, 0, 0};
+    std::vector<double> bval[3];
+    std::vector<double> G;
+    long long Qtot = 0;
+    int Qn[3] = {0, 0, 0};
+    // device offsets in the workspace (bytes)
+    size_t o_tf0[3], o_tlen[3], o_tmat[3], o_gamma, o_bval[3], o_G;
+};
+
+struct Blob {
+    std::vector<unsigned char> bytes;
+    template <class T>
+    size_t add(const std::vector<T>& v) {
+        const size_t off = (bytes.size() + 255) & ~size_t(255);
+        bytes.resize(off + v.size() * sizeof(T));
+        if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+};
+
+uint64_t splitmix64(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct smx_ctx {
+    int p[3], nel[3];
+    int geometry;
+    double amp;
+    DevField fld[4];
+    long long N_e, N_h;
+    BandLU fac[3][4];  // per axis: G, M, G^T, M^T
+    HodgeHost hodge[2];  // 0: B (mu), 1: D (eps)
+    Blob blob;
+    size_t o_fac[3][4][3];
+    size_t tables_bytes = 0, o_scratch = 0, o_scratch2 = 0, o_partial = 0, o_dots = 0, total_bytes = 0;
+    unsigned char* ws = nullptr;
+    cudaStream_t stream = nullptr;
+    // device argument blocks (valid once bound)
+    SolveArgs solve[2][3];  // [K1, Kt1][axis]
+    HodgeBlockArgs hb[2];
+    HodgeQuadArgs hq[2];
+    double* scratch = nullptr;
+    double* scratch2 = nullptr;
+    double* state = nullptr;  // d, e (N_e each), b, h (N_h each) for smx_step_host
+    size_t o_state = 0;
+    long long launches = 0;
+    int timing = 0;
+    struct Timed {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> timed;
+    double* partial = nullptr;
+    double* dots = nullptr;
+};
+
+namespace {
+
+const int kFieldOfHodge[2] = {SMX_FIELD_B, SMX_FIELD_D};
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// map, Jacobian and determinant at a parametric point
+void geometry_eval(int geom, double a, const double xh[3], double X[3], double J[9]) {
+    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int i = 0; i < 3; ++i) X[i] = xh[i];
+    if (geom == SMX_GEOM_SINE_BUMP) {
+        const double pi = 3.14159265358979323846;
+        const double sx = std::sin(pi * xh[0]), sy = std::sin(pi * xh[1]), sz = std::sin(pi * xh[2]);
+        const double cx = std::cos(pi * xh[0]), cy = std::cos(pi * xh[1]), cz = std::cos(pi * xh[2]);
+        const double S = sx * sy * sz;
+        const double g[3] = {pi * cx * sy * sz, pi * sx * cy * sz, pi * sx * sy * cz};
+        for (int i = 0; i < 3; ++i) {
+            X[i] += a * S;
+            for (int j = 0; j < 3; ++j) J[3 * i + j] += a * g[j];
+        }
+    }
+}
+
+double det3(const double J[9]) {
+    return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+int check_material(const smx_material& m, const int nel[3]) {
+    if (m.kind == SMX_MAT_CONST) return finite_pos(m.value) ? SMX_OK : SMX_EMAT;
+    if (m.kind == SMX_MAT_BLOCKS) {
+        if (!m.block_values) return SMX_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if (m.blocks[a] < 1 || nel[a] % m.blocks[a] != 0) return SMX_EINVAL;
+        const long long nb = (long long)m.blocks[0] * m.blocks[1] * m.blocks[2];
+        for (long long i = 0; i < nb; ++i)
+            if (!finite_pos(m.block_values[i])) return SMX_EMAT;
+        return SMX_OK;
+    }
+    if (m.kind == SMX_MAT_POINTWISE) return m.fn ? SMX_OK : SMX_EINVAL;
+    return SMX_EINVAL;
+}
+
+// Element ranges of the Hodge tiles along one axis: every material block is cut
+// into ceil(len/8) nearly equal tiles so no tile straddles a material jump.
+std::vector<int> tile_bounds(int nel, int nblocks) {
+    std::vector<int> b{0};
+    const int bl = nel / nblocks;
+    for (int k = 0; k < nblocks; ++k) {
+        const int lo = k * bl, nt = (bl + kTileMax - 1) / kTileMax;
+        for (int t = 1; t <= nt; ++t) b.push_back(lo + (int)((long long)bl * t / nt));
+    }
+    return b;
+}
+
+int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
+    HodgeHost& H = C->hodge[h];
+    const int field = kFieldOfHodge[h];
+    std::vector<int> bounds[3];
+    for (int a = 0; a < 3; ++a) {
+        const int nb = (m.kind == SMX_MAT_BLOCKS) ? m.blocks[a] : 1;
+        bounds[a] = tile_bounds(C->nel[a], nb);
+        H.ntile[a] = (int)bounds[a].size() - 1;
+    }
+    for (int a = 0; a < 3; ++a) {
+        const int p = C->p[a], nel = C->nel[a], nt = H.ntile[a];
+        H.tf0[a].assign(4 * nt, 0);
+        H.tlen[a].assign(4 * nt, 0);
+        H.tmat[a].assign((size_t)4 * nt * kLMax * kLMax, 0.0);
+        for (int kind = 0; kind < 4; ++kind) {
+            const int d = kind_degree(kind, p), off = kind_offset(kind), dim = kind_dim(kind, p, nel);
+            for (int t = 0; t < nt; ++t) {
+                const int e0 = bounds[a][t], e1 = bounds[a][t + 1];
+                const int flo = std::max(0, e0 + off), fhi = std::min(dim - 1, e1 - 1 + d + off);
+                const int len = fhi - flo + 1;
+                if (len > kLMax || len < 1) return SMX_EINVAL;
+                H.tf0[a][kind * nt + t] = flo;
+                H.tlen[a][kind * nt + t] = len;
+                double* M = &H.tmat[a][(size_t)(kind * nt + t) * kLMax * kLMax];
+                for (int e = e0; e < e1; ++e) {
+                    const std::vector<double> Me = element_mass(kind, p, nel, e);
+                    for (int r = 0; r <= d; ++r) {
+                        const int i = e + r + off;
+                        if (i < 0 || i >= dim) continue;
+                        for (int s = 0; s <= d; ++s) {
+                            const int j = e + s + off;
+                            if (j < 0 || j >= dim) continue;
+                            M[(i - flo) * kLMax + (j - flo)] += Me[r * (d + 1) + s];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    (void)field;
+    H.gamma.assign((size_t)H.ntile[0] * H.ntile[1] * H.ntile[2], 0.0);
+    for (int tz = 0; tz < H.ntile[2]; ++tz)
+        for (int ty = 0; ty < H.ntile[1]; ++ty)
+            for (int tx = 0; tx < H.ntile[0]; ++tx) {
+                double v = m.value;
+                if (m.kind == SMX_MAT_BLOCKS) {
+                    const int t3[3] = {tx, ty, tz};
+                    int b3[3];
+                    for (int a = 0; a < 3; ++a) b3[a] = bounds[a][t3[a]] / (C->nel[a] / m.blocks[a]);
+                    v = m.block_values[(b3[2] * m.blocks[1] + b3[1]) * m.blocks[0] + b3[0]];
+                }
+                H.gamma[((size_t)tz * H.ntile[1] + ty) * H.ntile[0] + tx] = 1.0 / v;
+            }
+    return SMX_OK;
+}
+
+int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
+    HodgeHost& H = C->hodge[h];
+    std::vector<double> gx[3], gw[3];
+    for (int a = 0; a < 3; ++a) {
+        const int p = C->p[a], nel = C->nel[a];
+        H.q[a] = p + 1;
+        H.Qn[a] = nel * H.q[a];
+        gauss_legendre01(H.q[a], gx[a], gw[a]);
+        H.bval[a].assign((size_t)4 * nel * H.q[a] * kRMax, 0.0);
+        for (int kind = 0; kind < 4; ++kind)
+            for (int e = 0; e < nel; ++e)
+                for (int k = 0; k < H.q[a]; ++k) {
+                    double v[16];
+                    local_basis(kind, p, nel, e, (e + gx[a][k]) / nel, v);
+                    const int d = kind_degree(kind, p);
+                    for (int r = 0; r <= d; ++r)
+                        H.bval[a][(((size_t)kind * nel + e) * H.q[a] + k) * kRMax + r] = v[r];
+                }
+    }
+    H.Qtot = (long long)H.Qn[0] * H.Qn[1] * H.Qn[2];
+    const long long Q = H.Qtot;
+    std::vector<double> X3(3 * Q), Jall(9 * Q), wdet(Q);
+    for (long long qi = 0; qi < Q; ++qi) {
+        const int ix = (int)(qi % H.Qn[0]);
+        const int iy = (int)((qi / H.Qn[0]) % H.Qn[1]);
+        const int iz = (int)(qi / ((long long)H.Qn[0] * H.Qn[1]));
+        const int ii[3] = {ix, iy, iz};
+        double xh[3], w = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            const int e = ii[a] / H.q[a], k = ii[a] % H.q[a];
+            xh[a] = (e + gx[a][k]) / C->nel[a];
+            w *= gw[a][k] / C->nel[a];
+        }
+        geometry_eval(C->geometry, C->amp, xh, &X3[3 * qi], &Jall[9 * qi]);
+        const double dj = det3(&Jall[9 * qi]);
+        if (!(dj > 0.0) || !std::isfinite(dj)) return SMX_EGEOM;
+        wdet[qi] = w / dj;
+    }
+    std::vector<double> mat(Q);
+    if (m.kind == SMX_MAT_POINTWISE) {
+        m.fn(Q, X3.data(), mat.data(), m.user);
+    } else {
+        for (long long qi = 0; qi < Q; ++qi) {
+            double v = m.value;
+            if (m.kind == SMX_MAT_BLOCKS) {
+                const int ix = (int)(qi % H.Qn[0]);
+                const int iy = (int)((qi / H.Qn[0]) % H.Qn[1]);
+                const int iz = (int)(qi / ((long long)H.Qn[0] * H.Qn[1]));
+                const int ii[3] = {ix, iy, iz};
+                int b3[3];
+                for (int a = 0; a < 3; ++a) b3[a] = (ii[a] / H.q[a]) / (C->nel[a] / m.blocks[a]);
+                v = m.block_values[(b3[2] * m.blocks[1] + b3[1]) * m.blocks[0] + b3[0]];
+            }
+            mat[qi] = v;
+        }
+    }
+    H.G.assign(6 * Q, 0.0);
+    for (long long qi = 0; qi < Q; ++qi) {
+        if (!finite_pos(mat[qi])) return SMX_EMAT;
+        const double s = wdet[qi] / mat[qi];
+        const double* J = &Jall[9 * qi];
+        double JtJ[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) JtJ[i][j] = J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j];
+        H.G[0 * Q + qi] = s * JtJ[0][0];
+        H.G[1 * Q + qi] = s * JtJ[0][1];
+        H.G[2 * Q + qi] = s * JtJ[0][2];
+        H.G[3 * Q + qi] = s * JtJ[1][1];
+        H.G[4 * Q + qi] = s * JtJ[1][2];
+        H.G[5 * Q + qi] = s * JtJ[2][2];
+    }
+    return SMX_OK;
+}
+
+std::vector<double> transpose(const std::vector<double>& A, int n) {
+    std::vector<double> T(A.size());
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) T[(size_t)j * n + i] = A[(size_t)i * n + j];
+    return T;
+}
+
+bool is_banded(const std::vector<double>& A, int n, int bw) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (std::abs(i - j) > bw && A[(size_t)i * n + j] != 0.0) return false;
+    return true;
+}
+
+// Which 1D factor block c of K_1 (K1 = 0) or K~_1 (1) uses along axis a:
+// (D1 rows, P0 cols) -> G, (D0, P1) -> M, transposed for K~_1 (Eq. tensor_K, Eq. tensor_Ktilde).
+int factor_index(int which, int c, int a) {
+    const int row_kind = kFieldKinds[which == 0 ? SMX_FIELD_D : SMX_FIELD_B][c][a];
+    if (which == 0) return row_kind == D1 ? 0 : 1;
+    return row_kind == P0 ? 2 : 3;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t err_ = (call);                        \
+        if (err_ != cudaSuccess) return SMX_ECUDA;        \
+    } while (0)
+
+// Launch through f() and account for it: kernel count, and CUDA events around
+// it when timing is on (class cls, see smx_kernel_times).
+template <class F>
+int run(smx_ctx* C, int cls, int nkernels, F&& f) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (C->timing) {
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(cudaEventRecord(a, C->stream));
+    }
+    CK(f());
+    if (C->timing) {
+        CK(cudaEventRecord(b, C->stream));
+        C->timed.push_back({cls, a, b});
+    }
+    C->launches += nkernels;
+    return SMX_OK;
+}
+
+int curl_primal_impl(smx_ctx* C, const double* e, double* b, double alpha) {
+    return run(C, 0, 1, [&] {
+        return launch_curl_primal(C->fld[SMX_FIELD_E], C->fld[SMX_FIELD_B], e, b, alpha, C->stream);
+    });
+}
+
+int curl_dual_impl(smx_ctx* C, const double* h, double* d, double alpha, const double* jhat, const double* amp,
+                   int idx, double s) {
+    return run(C, 1, 1, [&] {
+        return launch_curl_dual(C->fld[SMX_FIELD_H], C->fld[SMX_FIELD_D], h, d, alpha, jhat, amp, idx, s, C->stream);
+    });
+}
+
+int hodge_apply_impl(smx_ctx* C, int h, const double* x, double* y) {
+    const DevField& F = C->fld[kFieldOfHodge[h]];
+    CK(cudaMemsetAsync(y, 0, F.total * sizeof(double), C->stream));
+    if (C->hodge[h].mode == 0) return run(C, 2, 1, [&] { return launch_hodge_block(C->hb[h], x, y, C->stream); });
+    return run(C, 3, 1, [&] { return launch_hodge_quad(C->hq[h], x, y, C->stream); });
+}
+
+int solve_impl(smx_ctx* C, int which, const double* y, double* x) {
+    // x-sweep reads y and writes x; the y and z sweeps work in place in x
+    int st = run(C, 4, 1, [&] { return launch_solve_axis(C->solve[which][0], C->p[0] - 1, y, x, C->stream); });
+    if (st) return st;
+    st = run(C, 5, 1, [&] { return launch_solve_axis(C->solve[which][1], C->p[1] - 1, x, x, C->stream); });
+    if (st) return st;
+    return run(C, 6, 1, [&] { return launch_solve_axis(C->solve[which][2], C->p[2] - 1, x, x, C->stream); });
+}
+
+int dot_impl(smx_ctx* C, const double* x, const double* y, long long n, int slot) {
+    return run(C, 7, 2, [&] { return launch_dot(x, y, n, C->partial, C->dots + slot, C->stream); });
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* smx_strerror(int s) {
+    switch (s) {
+        case SMX_OK: return "ok";
+        case SMX_EINVAL: return "invalid argument";
+        case SMX_EGEOM: return "geometry map not orientation preserving (det J <= 0)";
+        case SMX_EMAT: return "material not finite and positive";
+        case SMX_ECUDA: return "CUDA runtime error";
+        case SMX_ENONFINITE: return "non-finite value in the fields";
+        case SMX_ESTATE: return "workspace missing or too small";
+        case SMX_ENOMEM: return "host allocation failed";
+        case SMX_ESINGULAR: return "singular 1D pairing factor";
+        default: return "unknown status";
+    }
+}
+
+int smx_create(const smx_params* P, smx_ctx** out) {
+    if (!P || !out) return SMX_EINVAL;
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a) {
+        if (P->p[a] < 2 || P->p[a] > kPMax) return SMX_EINVAL;
+        if (P->nel[a] < 1 || P->nel[a] > 800) return SMX_EINVAL;
+    }
+    if (P->geometry != SMX_GEOM_IDENTITY && P->geometry != SMX_GEOM_SINE_BUMP) return SMX_EINVAL;
+    if (!std::isfinite(P->geom_amplitude)) return SMX_EINVAL;
+    int st = check_material(P->eps, P->nel);
+    if (st) return st;
+    st = check_material(P->mu, P->nel);
+    if (st) return st;
+    smx_ctx* C = new (std::nothrow) smx_ctx();
+    if (!C) return SMX_ENOMEM;
+    try {
+        for (int a = 0; a < 3; ++a) {
+            C->p[a] = P->p[a];
+            C->nel[a] = P->nel[a];
+        }
+        C->geometry = P->geometry;
+        C->amp = P->geom_amplitude;
+        for (int f = 0; f < 4; ++f) {
+            long long off = 0;
+            for (int c = 0; c < 3; ++c) {
+                for (int a = 0; a < 3; ++a) C->fld[f].c[c].n[a] = kind_dim(kFieldKinds[f][c][a], C->p[a], C->nel[a]);
+                C->fld[f].c[c].off = off;
+                off += (long long)C->fld[f].c[c].n[0] * C->fld[f].c[c].n[1] * C->fld[f].c[c].n[2];
+            }
+            C->fld[f].total = off;
+        }
+        C->N_e = C->fld[SMX_FIELD_E].total;
+        C->N_h = C->fld[SMX_FIELD_H].total;
+        // 1D factors (Sec. 4.1) and their banded LU (Sec. 4.3, Table 1 setup)
+        for (int a = 0; a < 3; ++a) {
+            const int p = C->p[a], nel = C->nel[a];
+            const std::vector<double> G = pairing_matrix(D1, P0, p, nel);
+            const std::vector<double> M = pairing_matrix(D0, P1, p, nel);
+            const int nG = kind_dim(D1, p, nel), nM = kind_dim(D0, p, nel);
+            if (!is_banded(G, nG, p - 1) || !is_banded(M, nM, p - 1)) {
+                delete C;
+                return SMX_ESINGULAR;
+            }
+            const std::vector<double>* mats[4] = {&G, &M, nullptr, nullptr};
+            const std::vector<double> Gt = transpose(G, nG), Mt = transpose(M, nM);
+            mats[2] = &Gt;
+            mats[3] = &Mt;
+            const int ns[4] = {nG, nM, nG, nM};
+            for (int w = 0; w < 4; ++w)
+                if (!band_lu(*mats[w], ns[w], p - 1, p - 1, C->fac[a][w])) {
+                    delete C;
+                    return SMX_ESINGULAR;
+                }
+        }
+        // Hodge tables: block Kronecker on the identity map with constant or block material
+        const smx_material* mats[2] = {&P->mu, &P->eps};
+        for (int h = 0; h < 2; ++h) {
+            const bool block = C->geometry == SMX_GEOM_IDENTITY && mats[h]->kind != SMX_MAT_POINTWISE;
+            C->hodge[h].mode = block ? 0 : 1;
+            st = block ? build_hodge_block(C, h, *mats[h]) : build_hodge_quad(C, h, *mats[h]);
+            if (st) {
+                delete C;
+                return st;
+            }
+        }
+        // pack the tables
+        for (int a = 0; a < 3; ++a)
+            for (int w = 0; w < 4; ++w) {
+                C->o_fac[a][w][0] = C->blob.add(C->fac[a][w].L);
+                C->o_fac[a][w][1] = C->blob.add(C->fac[a][w].U);
+                C->o_fac[a][w][2] = C->blob.add(C->fac[a][w].dinv);
+            }
+        for (int h = 0; h < 2; ++h) {
+            HodgeHost& H = C->hodge[h];
+            if (H.mode == 0) {
+                for (int a = 0; a < 3; ++a) {
+                    H.o_tf0[a] = C->blob.add(H.tf0[a]);
+                    H.o_tlen[a] = C->blob.add(H.tlen[a]);
+                    H.o_tmat[a] = C->blob.add(H.tmat[a]);
+                }
+                H.o_gamma = C->blob.add(H.gamma);
+            } else {
+                for (int a = 0; a < 3; ++a) H.o_bval[a] = C->blob.add(H.bval[a]);
+                H.o_G = C->blob.add(H.G);
+                H.G.clear();
+                H.G.shrink_to_fit();
+            }
+        }
+        C->tables_bytes = (C->blob.bytes.size() + 255) & ~size_t(255);
+        C->o_scratch = C->tables_bytes;
+        const size_t nmax = (size_t)std::max(C->N_e, C->N_h);
+        C->o_scratch2 = C->o_scratch + ((nmax * sizeof(double) + 255) & ~size_t(255));
+        C->o_partial = C->o_scratch2 + ((nmax * sizeof(double) + 255) & ~size_t(255));
+        C->o_dots = C->o_partial + ((kDotBlocks * sizeof(double) + 255) & ~size_t(255));
+        C->o_state = C->o_dots + 256;
+        C->total_bytes = C->o_state + ((2 * (size_t)(C->N_e + C->N_h) * sizeof(double) + 255) & ~size_t(255));
+    } catch (const std::bad_alloc&) {
+        delete C;
+        return SMX_ENOMEM;
+    }
+    *out = C;
+    return SMX_OK;
+}
+
+int smx_destroy(smx_ctx* C) {
+    if (C)
+        for (auto& t : C->timed) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+    delete C;
+    return SMX_OK;
+}
+
+int smx_sizes(const smx_ctx* C, int64_t* n_e, int64_t* n_h) {
+    if (!C || !n_e || !n_h) return SMX_EINVAL;
+    *n_e = C->N_e;
+    *n_h = C->N_h;
+    return SMX_OK;
+}
+
+int smx_comp_shape(const smx_ctx* C, int field, int comp, int64_t shape[3]) {
+    if (!C || !shape || field < 0 || field > 3 || comp < 0 || comp > 2) return SMX_EINVAL;
+    for (int a = 0; a < 3; ++a) shape[a] = C->fld[field].c[comp].n[a];
+    return SMX_OK;
+}
+
+int smx_workspace_bytes(const smx_ctx* C, size_t* bytes) {
+    if (!C || !bytes) return SMX_EINVAL;
+    *bytes = C->total_bytes;
+    return SMX_OK;
+}
+
+int smx_set_stream(smx_ctx* C, void* stream) {
+    if (!C) return SMX_EINVAL;
+    C->stream = static_cast<cudaStream_t>(stream);
+    return SMX_OK;
+}
+
+int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
+    if (!C || !dev) return SMX_EINVAL;
+    if (bytes < C->total_bytes || (reinterpret_cast<uintptr_t>(dev) & 255)) return SMX_ESTATE;
+    unsigned char* ws = static_cast<unsigned char*>(dev);
+    CK(cudaMemcpyAsync(ws, C->blob.bytes.data(), C->blob.bytes.size(), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    C->ws = ws;
+    C->scratch = reinterpret_cast<double*>(ws + C->o_scratch);
+    C->scratch2 = reinterpret_cast<double*>(ws + C->o_scratch2);
+    C->partial = reinterpret_cast<double*>(ws + C->o_partial);
+    C->dots = reinterpret_cast<double*>(ws + C->o_dots);
+    C->state = reinterpret_cast<double*>(ws + C->o_state);
+    // pairing sweeps
+    for (int which = 0; which < 2; ++which) {
+        const int fld = which == 0 ? SMX_FIELD_D : SMX_FIELD_B;
+        for (int a = 0; a < 3; ++a) {
+            SolveArgs& S = C->solve[which][a];
+            S.field = C->fld[fld];
+            S.axis = a;
+            for (int c = 0; c < 3; ++c) {
+                const int w = factor_index(which, c, a);
+                S.f[c].L = reinterpret_cast<const double*>(ws + C->o_fac[a][w][0]);
+                S.f[c].U = reinterpret_cast<const double*>(ws + C->o_fac[a][w][1]);
+                S.f[c].dinv = reinterpret_cast<const double*>(ws + C->o_fac[a][w][2]);
+                S.f[c].n = C->fac[a][w].n;
+            }
+        }
+    }
+    for (int h = 0; h < 2; ++h) {
+        const HodgeHost& H = C->hodge[h];
+        const int fld = kFieldOfHodge[h];
+        if (H.mode == 0) {
+            HodgeBlockArgs& A = C->hb[h];
+            A.field = C->fld[fld];
+            for (int a = 0; a < 3; ++a) {
+                A.ntile[a] = H.ntile[a];
+                A.tf0[a] = reinterpret_cast<const int*>(ws + H.o_tf0[a]);
+                A.tlen[a] = reinterpret_cast<const int*>(ws + H.o_tlen[a]);
+                A.tmat[a] = reinterpret_cast<const double*>(ws + H.o_tmat[a]);
+            }
+            for (int c = 0; c < 3; ++c)
+                for (int a = 0; a < 3; ++a) {
+                    A.kinds[c][a] = kFieldKinds[fld][c][a];
+                    A.deg[c][a] = kind_degree(A.kinds[c][a], C->p[a]);
+                }
+            A.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
+        } else {
+            HodgeQuadArgs& A = C->hq[h];
+            A.field = C->fld[fld];
+            for (int a = 0; a < 3; ++a) {
+                A.nel[a] = C->nel[a];
+                A.q[a] = H.q[a];
+                A.Qn[a] = H.Qn[a];
+                A.bval[a] = reinterpret_cast<const double*>(ws + H.o_bval[a]);
+            }
+            for (int c = 0; c < 3; ++c)
+                for (int a = 0; a < 3; ++a) {
+                    A.kinds[c][a] = kFieldKinds[fld][c][a];
+                    A.deg[c][a] = kind_degree(A.kinds[c][a], C->p[a]);
+                    A.koff[c][a] = kind_offset(A.kinds[c][a]);
+                }
+            A.G = reinterpret_cast<const double*>(ws + H.o_G);
+            A.Qtot = H.Qtot;
+        }
+    }
+    return SMX_OK;
+}
+
+#define NEED_WS(C)                      \
+    do {                                \
+        if (!(C)) return SMX_EINVAL;    \
+        if (!(C)->ws) return SMX_ESTATE; \
+    } while (0)
+
+int smx_curl_primal(smx_ctx* C, const double* e, double* b, double alpha) {
+    NEED_WS(C);
+    if (!e || !b || !std::isfinite(alpha)) return SMX_EINVAL;
+    return curl_primal_impl(C, e, b, alpha);
+}
+
+int smx_curl_dual(smx_ctx* C, const double* h, double* d, double alpha, const double* jhat, double s) {
+    NEED_WS(C);
+    if (!h || !d || !std::isfinite(alpha) || !std::isfinite(s)) return SMX_EINVAL;
+    return curl_dual_impl(C, h, d, alpha, jhat, nullptr, 0, s);
+}
+
+int smx_hodge_apply(smx_ctx* C, int field, const double* x, double* y) {
+    NEED_WS(C);
+    if (!x || !y || x == y) return SMX_EINVAL;
+    if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
+    return hodge_apply_impl(C, field == SMX_FIELD_B ? 0 : 1, x, y);
+}
+
+int smx_pairing_solve(smx_ctx* C, int which, const double* y, double* x) {
+    NEED_WS(C);
+    if (!x || !y) return SMX_EINVAL;
+    if (which != SMX_FIELD_E && which != SMX_FIELD_H) return SMX_EINVAL;
+    return solve_impl(C, which == SMX_FIELD_E ? 0 : 1, y, x);
+}
+
+int smx_hodge_star(smx_ctx* C, int field, const double* x, double* out) {
+    NEED_WS(C);
+    if (!x || !out) return SMX_EINVAL;
+    if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
+    const int h = field == SMX_FIELD_B ? 0 : 1;
+    int st = hodge_apply_impl(C, h, x, C->scratch);
+    if (st) return st;
+    return solve_impl(C, h == 0 ? 1 : 0, C->scratch, out);
+}
+
+int smx_step(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp,
+             double dt, int nsteps) {
+    NEED_WS(C);
+    if (!d || !b || !e || !h || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return SMX_EINVAL;
+    if (jhat && !amp) return SMX_EINVAL;
+    if (nsteps == 0) return SMX_OK;
+    // kick-drift-kick with the inner half kicks of b merged
+    int st = curl_primal_impl(C, e, b, -0.5 * dt);
+    if (st) return st;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((st = hodge_apply_impl(C, 0, b, C->scratch))) return st;  // M^2_{1/mu} b
+        if ((st = solve_impl(C, 1, C->scratch, h))) return st;        // h = K~_1^{-1} (.)
+        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0))) return st;
+        if ((st = hodge_apply_impl(C, 1, d, C->scratch))) return st;  // M~^2_{1/eps} d
+        if ((st = solve_impl(C, 0, C->scratch, e))) return st;        // e = K_1^{-1} (.)
+        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt))) return st;
+    }
+    return SMX_OK;
+}
+
+int smx_energy(smx_ctx* C, const double* d, const double* b, const double* e, double dt, double out[2]) {
+    NEED_WS(C);
+    if (!d || !b || !out || !std::isfinite(dt)) return SMX_EINVAL;
+    int st = hodge_apply_impl(C, 1, d, C->scratch);
+    if (st) return st;
+    st = dot_impl(C, d, C->scratch, C->N_e, 0);
+    if (st) return st;
+    st = hodge_apply_impl(C, 0, b, C->scratch);
+    if (st) return st;
+    st = dot_impl(C, b, C->scratch, C->N_h, 1);
+    if (st) return st;
+    double host[3] = {0.0, 0.0, 0.0};
+    if (e) {
+        // c = D^1 e into the second scratch vector, M c into the first
+        CK(cudaMemsetAsync(C->scratch2, 0, C->N_h * sizeof(double), C->stream));
+        if ((st = curl_primal_impl(C, e, C->scratch2, 1.0))) return st;
+        if ((st = hodge_apply_impl(C, 0, C->scratch2, C->scratch))) return st;
+        if ((st = dot_impl(C, C->scratch2, C->scratch, C->N_h, 2))) return st;
+    }
+    CK(cudaMemcpyAsync(host, C->dots, 3 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    const double Eh = 0.5 * (host[0] + host[1]);
+    out[0] = Eh;
+    out[1] = e ? Eh - dt * dt / 8.0 * host[2] : Eh;
+    if (!std::isfinite(out[0]) || !std::isfinite(out[1])) return SMX_ENONFINITE;
+    return SMX_OK;
+}
+
+int smx_step_host(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp,
+                  double dt, int nsteps) {
+    NEED_WS(C);
+    if (!d || !b || !e || !h) return SMX_EINVAL;
+    double* dd = C->state;
+    double* ed = dd + C->N_e;
+    double* bd = ed + C->N_e;
+    double* hd = bd + C->N_h;
+    const size_t se = C->N_e * sizeof(double), sh = C->N_h * sizeof(double);
+    CK(cudaMemcpyAsync(dd, d, se, cudaMemcpyHostToDevice, C->stream));
+    CK(cudaMemcpyAsync(ed, e, se, cudaMemcpyHostToDevice, C->stream));
+    CK(cudaMemcpyAsync(bd, b, sh, cudaMemcpyHostToDevice, C->stream));
+    int st = smx_step(C, dd, bd, ed, hd, jhat, amp, dt, nsteps);
+    if (st) return st;
+    CK(cudaMemcpyAsync(d, dd, se, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaMemcpyAsync(e, ed, se, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaMemcpyAsync(b, bd, sh, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaMemcpyAsync(h, hd, sh, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    return SMX_OK;
+}
+
+int smx_launch_count(const smx_ctx* C, int64_t* n) {
+    if (!C || !n) return SMX_EINVAL;
+    *n = C->launches;
+    return SMX_OK;
+}
+
+int smx_set_timing(smx_ctx* C, int enable) {
+    if (!C) return SMX_EINVAL;
+    C->timing = enable ? 1 : 0;
+    return SMX_OK;
+}
+
+int smx_kernel_times(smx_ctx* C, double* ms, int64_t* counts) {
+    if (!C || !ms || !counts) return SMX_EINVAL;
+    for (int k = 0; k < SMX_NCLASS; ++k) {
+        ms[k] = 0.0;
+        counts[k] = 0;
+    }
+    int st = SMX_OK;
+    if (!C->timed.empty() && cudaStreamSynchronize(C->stream) != cudaSuccess) st = SMX_ECUDA;
+    for (auto& t : C->timed) {
+        float el = 0.0f;
+        if (st == SMX_OK && cudaEventElapsedTime(&el, t.a, t.b) == cudaSuccess) {
+            ms[t.cls] += el;
+            counts[t.cls] += 1;
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    C->timed.clear();
+    return st;
+}
+
+int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double* bytes) {
+    if (!C || !flops || !bytes || field < 0 || field > 3) return SMX_EINVAL;
+    const double Ne = (double)C->N_e, Nh = (double)C->N_h;
+    const bool bside = (field == SMX_FIELD_B || field == SMX_FIELD_H);  // K~_1 / M^2 side
+    const double N = bside ? Nh : Ne;
+    switch (cls) {
+        case 0:  // curl_primal: b += alpha D^1 e, 3 differences + 1 FMA per output
+            if (!bside) return SMX_EINVAL;
+            *flops = 5.0 * Nh;
+            *bytes = 8.0 * (Ne + 2.0 * Nh);
+            return SMX_OK;
+        case 1:  // curl_dual (without source)
+            if (bside) return SMX_EINVAL;
+            *flops = 5.0 * Ne;
+            *bytes = 8.0 * (Nh + 2.0 * Ne);
+            return SMX_OK;
+        case 2:
+        case 3: {
+            const int h = bside ? 0 : 1;
+            const HodgeHost& H = C->hodge[h];
+            if ((cls == 2) != (H.mode == 0)) return SMX_EINVAL;
+            const int fld = kFieldOfHodge[h];
+            double f = 0.0;
+            if (H.mode == 0) {
+                // per tile and component: 2 * (sum of band widths of each 1D pass x the other extents)
+                for (int c = 0; c < 3; ++c) {
+                    std::vector<double> band_sum[3], len[3];
+                    for (int a = 0; a < 3; ++a) {
+                        const int kind = kFieldKinds[fld][c][a], d = kind_degree(kind, C->p[a]);
+                        for (int t = 0; t < H.ntile[a]; ++t) {
+                            const int L = H.tlen[a][kind * H.ntile[a] + t];
+                            double bs = 0.0;
+                            for (int i = 0; i < L; ++i) bs += std::min(L - 1, i + d) - std::max(0, i - d) + 1;
+                            band_sum[a].push_back(bs);
+                            len[a].push_back(L);
+                        }
+                    }
+                    for (int tz = 0; tz < H.ntile[2]; ++tz)
+                        for (int ty = 0; ty < H.ntile[1]; ++ty)
+                            for (int tx = 0; tx < H.ntile[0]; ++tx)
+                                f += 2.0 * (band_sum[0][tx] * len[1][ty] * len[2][tz] +
+                                            len[0][tx] * band_sum[1][ty] * len[2][tz] +
+                                            len[0][tx] * len[1][ty] * band_sum[2][tz]);
+                }
+            } else {
+                const double Qe = (double)H.q[0] * H.q[1] * H.q[2];
+                const double nel = (double)C->nel[0] * C->nel[1] * C->nel[2];
+                double per = 15.0 * Qe;
+                for (int c = 0; c < 3; ++c) {
+                    double r[3];
+                    for (int a = 0; a < 3; ++a) r[a] = kind_degree(kFieldKinds[fld][c][a], C->p[a]) + 1;
+                    per += 4.0 * (r[2] * r[1] * H.q[0] * r[0] + r[2] * H.q[1] * H.q[0] * r[1] + Qe * r[2]);
+                }
+                f = per * nel;
+            }
+            *flops = f;
+            *bytes = 16.0 * N + (H.mode == 1 ? 48.0 * (double)H.Qtot : 0.0);
+            return SMX_OK;
+        }
+        case 4:
+        case 5:
+        case 6: {  // one 1D sweep: forward 2 KL + backward 2 KL + 1 flops per entry
+            const int kl = C->p[cls - 4] - 1;
+            *flops = (4.0 * kl + 1.0) * N;
+            *bytes = 16.0 * N;
+            return SMX_OK;
+        }
+        default:
+            return SMX_EINVAL;
+    }
+}
+
+int smx_factor_matrix(const smx_ctx* C, int axis, int which, int64_t* n, double* dense_out) {
+    if (!C || !n || axis < 0 || axis > 2 || which < 0 || which > 3) return SMX_EINVAL;
+    const BandLU& f = C->fac[axis][which];
+    *n = f.n;
+    if (dense_out) {
+        const std::vector<double> A = band_lu_dense(f);
+        std::memcpy(dense_out, A.data(), A.size() * sizeof(double));
+    }
+    return SMX_OK;
+}
+
+int smx_hodge_mode(const smx_ctx* C, int field, int* mode) {
+    if (!C || !mode || (field != SMX_FIELD_B && field != SMX_FIELD_D)) return SMX_EINVAL;
+    *mode = C->hodge[field == SMX_FIELD_B ? 0 : 1].mode;
+    return SMX_OK;
+}
+
+int smx_cfl(smx_ctx* C, int iters, double tol, double* v, double* w, double* t, double* dt_max) {
+    NEED_WS(C);
+    if (!v || !w || !t || !dt_max || iters < 1 || !(tol >= 0.0)) return SMX_EINVAL;
+    std::vector<double> v0(C->N_e);
+    uint64_t state = 0x5eed5eedULL;
+    for (auto& x : v0) x = (double)(splitmix64(state) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    CK(cudaMemcpyAsync(v, v0.data(), v0.size() * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+    double lam = 0.0, lam_old = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        int st = hodge_apply_impl(C, 1, v, C->scratch);  // S = M~ v
+        if (st) return st;
+        if ((st = dot_impl(C, v, C->scratch, C->N_e, 0))) return st;  // den = v.M~v
+        if ((st = solve_impl(C, 0, C->scratch, w))) return st;        // w = K_1^{-1} M~ v
+        CK(cudaMemsetAsync(t, 0, C->N_h * sizeof(double), C->stream));
+        if ((st = curl_primal_impl(C, w, t, 1.0))) return st;        // t = D^1 w
+        if ((st = hodge_apply_impl(C, 0, t, C->scratch))) return st;  // S = M t
+        if ((st = solve_impl(C, 1, C->scratch, t))) return st;        // t = K~_1^{-1} M t
+        CK(cudaMemsetAsync(w, 0, C->N_e * sizeof(double), C->stream));
+        if ((st = curl_dual_impl(C, t, w, 1.0, nullptr, nullptr, 0, 0.0))) return st;  // w = D~^1 t = T v
+        if ((st = hodge_apply_impl(C, 1, w, C->scratch))) return st;  // S = M~ w
+        if ((st = dot_impl(C, v, C->scratch, C->N_e, 1))) return st;  // num = v.M~ T v
+        if ((st = dot_impl(C, w, C->scratch, C->N_e, 2))) return st;  // |T v|^2_M~
+        double host[3];
+        CK(cudaMemcpyAsync(host, C->dots, 3 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+        if (!std::isfinite(host[0]) || !std::isfinite(host[1]) || !(host[2] > 0.0)) return SMX_ENONFINITE;
+        lam = host[1] / host[0];
+        const double sc = 1.0 / std::sqrt(host[2]);
+        if ((st = run(C, 7, 1, [&] { return launch_scale_copy(w, v, sc, C->N_e, C->stream); }))) return st;
+        if (it > 0 && std::fabs(lam - lam_old) <= tol * std::fabs(lam)) break;
+        lam_old = lam;
+    }
+    if (!(lam > 0.0)) return SMX_ENONFINITE;
+    *dt_max = 2.0 / std::sqrt(lam);
+    return SMX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Device-visible argument blocks and kernel launchers of the leapfrog path.
+// Shared by kernels.cu (device code) and api.cu (the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace smx {
+
+constexpr int kLMax = 16;      // max local functions per tile and axis (tile <= 8 elements, p <= 6)
+constexpr int kTileMax = 8;    // max elements per Hodge tile and axis
+constexpr int kRMax = 8;       // max local functions per element and axis (p + 1 <= 7)
+constexpr int kPMax = 6;       // largest supported degree
+constexpr int kSolveLines = 32;  // lines per CTA in the pairing sweeps
+constexpr int kDotBlocks = 304;  // CTAs of the first reduction stage (2 x 152 SMs)
+
+// One component of a field: extents (x, y, z) and offset in the global vector.
+struct DevComp {
+    int n[3];
+    long long off;
+};
+struct DevField {
+    DevComp c[3];
+    long long total;
+};
+
+// Banded LU of one 1D factor (see BandLU in setup.h); device pointers.
+struct DevFactor {
+    const double* L;
+    const double* U;
+    const double* dinv;
+    int n;
+};
+
+// Per-axis sweep of a pairing solve: for each component the factor along `axis`.
+struct SolveArgs {
+    DevField field;
+    DevFactor f[3];
+    int axis;
+};
+
+// Block-Kronecker Hodge apply: M = sum_t gamma_t (Mz_t (x) My_t (x) Mx_t).
+struct HodgeBlockArgs {
+    DevField field;
+    int ntile[3];
+    int kinds[3][3];   // kinds[c][a]
+    int deg[3][3];     // degree of kinds[c][a]
+    const int* tf0[3];       // tf0[a][kind * ntile[a] + t]: first local function of tile t
+    const int* tlen[3];      // number of local functions
+    const double* tmat[3];   // (kind * ntile[a] + t) * kLMax^2: dense tile mass, row-major
+    const double* gamma;     // per tile, x fastest
+};
+
+// Quadrature Hodge apply (curved map or pointwise material).
+struct HodgeQuadArgs {
+    DevField field;
+    int nel[3];
+    int q[3];
+    int kinds[3][3];
+    int deg[3][3];
+    int koff[3][3];          // index shift of kinds[c][a] (-1 for P0)
+    const double* bval[3];   // ((kind * nel[a] + e) * q[a] + qp) * kRMax + r
+    const double* G;         // 6 arrays of Qtot: G00 G01 G02 G11 G12 G22 (weight, metric, material folded in)
+    long long Qtot;
+    int Qn[3];               // quadrature points per axis
+};
+
+// ---- launchers (kernels.cu); all enqueue on `s` and return cudaGetLastError()
+cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b,
+                               double alpha, cudaStream_t s);
+cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double* h, double* d,
+                             double alpha, const double* jhat, const double* amp, int amp_index,
+                             double s_host, cudaStream_t s);
+cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_solve_axis(const SolveArgs& a, int kl, const double* in, double* out, cudaStream_t s);
+// partial[b] of sum_i x_i y_i over kDotBlocks CTAs, then out[0] = total (device)
+cudaError_t launch_dot(const double* x, const double* y, long long n, double* partial, double* out,
+                       cudaStream_t s);
+cudaError_t launch_scale_copy(const double* x, double* y, double a, long long n, cudaStream_t s);
+
+}  // namespace smx

@@ -1,0 +1,494 @@
+// sm_103a kernels of the scheme-2 leapfrog (Kapidani & Vazquez, Sec. 3.4, Sec. 4).
+//
+// FP64 throughout.  On GB300 the FP64 pipe is the scarce resource (about
+// 1/64 of the FP32 lane rate), so every kernel here is written to issue the
+// fewest FP64 instructions per degree of freedom; index arithmetic is integer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace smx {
+
+// ------------------------------------------------------------------ curl
+// Primal incidence along axis a (Remark on incidence matrices after Table 1):
+// (d u)_m = u_m - u_{m-1}, with u_m = 0 outside [0, n_a) (the removed BC functions).
+__device__ __forceinline__ double primal_diff(const DevComp& u, const double* __restrict__ v, int i, int j,
+                                              int k, int a) {
+    const long long base = u.off + i + (long long)u.n[0] * (j + (long long)u.n[1] * k);
+    const long long stride = a == 0 ? 1LL : (a == 1 ? (long long)u.n[0] : (long long)u.n[0] * u.n[1]);
+    const int m = a == 0 ? i : (a == 1 ? j : k);
+    const double hi = (m < u.n[a]) ? __ldg(v + base) : 0.0;
+    const double lo = (m >= 1) ? __ldg(v + base - stride) : 0.0;
+    return hi - lo;
+}
+
+// Dual incidence along axis a: (d u)_m = u_{m+1} - u_m (input has one more entry along a).
+__device__ __forceinline__ double dual_diff(const DevComp& u, const double* __restrict__ v, int i, int j, int k,
+                                            int a) {
+    const long long base = u.off + i + (long long)u.n[0] * (j + (long long)u.n[1] * k);
+    const long long stride = a == 0 ? 1LL : (a == 1 ? (long long)u.n[0] : (long long)u.n[0] * u.n[1]);
+    return __ldg(v + base + stride) - __ldg(v + base);
+}
+
+__device__ __forceinline__ void decode(const DevField& F, long long idx, int& c, int& i, int& j, int& k) {
+    c = (idx >= F.c[1].off) + (idx >= F.c[2].off);
+    const long long r = idx - F.c[c].off;
+    const int nx = F.c[c].n[0], ny = F.c[c].n[1];
+    const long long t = r / nx;
+    i = static_cast<int>(r - t * nx);
+    j = static_cast<int>(t % ny);
+    k = static_cast<int>(t / ny);
+}
+
+// b += alpha * D^1 e, (curl E)_c = d_{c+1} E_{c+2} - d_{c+2} E_{c+1}  (Eq. discrete2_faraday)
+__global__ void __launch_bounds__(256) curl_primal_kernel(DevField E, DevField B, const double* __restrict__ e,
+                                                          double* __restrict__ b, double alpha) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= B.total) return;
+    int c, i, j, k;
+    decode(B, idx, c, i, j, k);
+    const int a1 = c == 2 ? 0 : c + 1, a2 = c == 0 ? 2 : c - 1;
+    const double v = primal_diff(E.c[a2], e, i, j, k, a1) - primal_diff(E.c[a1], e, i, j, k, a2);
+    b[idx] = fma(alpha, v, b[idx]);
+}
+
+// d += alpha * (D~^1 h - s jhat)  (Eq. discrete2_ampere)
+__global__ void __launch_bounds__(256) curl_dual_kernel(DevField H, DevField D, const double* __restrict__ h,
+                                                        double* __restrict__ d, double alpha,
+                                                        const double* __restrict__ jhat,
+                                                        const double* __restrict__ amp, int amp_index,
+                                                        double s_host) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= D.total) return;
+    int c, i, j, k;
+    decode(D, idx, c, i, j, k);
+    const int a1 = c == 2 ? 0 : c + 1, a2 = c == 0 ? 2 : c - 1;
+    double v = dual_diff(H.c[a2], h, i, j, k, a1) - dual_diff(H.c[a1], h, i, j, k, a2);
+    if (jhat != nullptr) {
+        const double s = amp != nullptr ? __ldg(amp + amp_index) : s_host;
+        v = fma(-s, __ldg(jhat + idx), v);
+    }
+    d[idx] = fma(alpha, v, d[idx]);
+}
+
+cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b, double alpha,
+                               cudaStream_t s) {
+    const int nt = 256;
+    const long long nb = (B.total + nt - 1) / nt;
+    if (nb > 0) curl_primal_kernel<<<static_cast<unsigned>(nb), nt, 0, s>>>(E, B, e, b, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double* h, double* d, double alpha,
+                             const double* jhat, const double* amp, int amp_index, double s_host,
+                             cudaStream_t s) {
+    const int nt = 256;
+    const long long nb = (D.total + nt - 1) / nt;
+    if (nb > 0)
+        curl_dual_kernel<<<static_cast<unsigned>(nb), nt, 0, s>>>(H, D, h, d, alpha, jhat, amp, amp_index, s_host);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Hodge: block Kronecker
+// Identity map, material constant on each tile of <= 8^3 elements: the tile's
+// contribution to the mass matrix of one 2-form component is
+//   gamma_t * (Mz_t (x) My_t (x) Mx_t)
+// with M*_t the univariate mass restricted to the tile's elements (Sec. 3.4
+// mass matrix; the Kronecker structure of the parametric integrals, Sec. 4.1).
+// One CTA per (tile, component): gather the tile's coefficients into shared
+// memory, three banded 1D passes, scatter-add (FP64 atomics) into y.
+constexpr int kHodgeThreads = 256;
+
+__global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockArgs A, const double* __restrict__ x,
+                                                                    double* __restrict__ y) {
+    extern __shared__ double sm[];
+    const int c = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int tx = tile % A.ntile[0];
+    const int tyz = tile / A.ntile[0];
+    const int ty = tyz % A.ntile[1];
+    const int tz = tyz / A.ntile[1];
+    const int tpos[3] = {tx, ty, tz};
+    int f0[3], L[3], dg[3];
+    const double* gmat[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int slot = A.kinds[c][a] * A.ntile[a] + tpos[a];
+        f0[a] = A.tf0[a][slot];
+        L[a] = A.tlen[a][slot];
+        dg[a] = A.deg[c][a];
+        gmat[a] = A.tmat[a] + (long long)slot * kLMax * kLMax;
+    }
+    const double gam = A.gamma[(tz * A.ntile[1] + ty) * A.ntile[0] + tx];
+    double* Mx = sm;
+    double* My = Mx + kLMax * kLMax;
+    double* Mz = My + kLMax * kLMax;
+    double* s0 = Mz + kLMax * kLMax;
+    const int Lx = L[0], Ly = L[1], Lz = L[2];
+    const int nloc = Lx * Ly * Lz;
+    double* s1 = s0 + nloc;
+    // tile masses; gamma folded into Mz
+    for (int t = threadIdx.x; t < kLMax * kLMax; t += blockDim.x) {
+        Mx[t] = __ldg(gmat[0] + t);
+        My[t] = __ldg(gmat[1] + t);
+        Mz[t] = gam * __ldg(gmat[2] + t);
+    }
+    const DevComp C = A.field.c[c];
+    const long long nxy = (long long)C.n[0] * C.n[1];
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+        const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
+        s0[t] = __ldg(x + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * (f0[2] + kk));
+    }
+    __syncthreads();
+    // x pass
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+        const int ii = t % Lx, row = t - ii;
+        const int lo = max(0, ii - dg[0]), hi = min(Lx - 1, ii + dg[0]);
+        double acc = 0.0;
+        for (int m = lo; m <= hi; ++m) acc = fma(Mx[ii * kLMax + m], s0[row + m], acc);
+        s1[t] = acc;
+    }
+    __syncthreads();
+    // y pass
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+        const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
+        const int lo = max(0, jj - dg[1]), hi = min(Ly - 1, jj + dg[1]);
+        double acc = 0.0;
+        for (int m = lo; m <= hi; ++m) acc = fma(My[jj * kLMax + m], s1[(kk * Ly + m) * Lx + ii], acc);
+        s0[t] = acc;
+    }
+    __syncthreads();
+    // z pass and scatter-add
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+        const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
+        const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
+        double acc = 0.0;
+        for (int m = lo; m <= hi; ++m) acc = fma(Mz[kk * kLMax + m], s0[(m * Ly + jj) * Lx + ii], acc);
+        atomicAdd(y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * (f0[2] + kk), acc);
+    }
+}
+
+cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s) {
+    const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
+    const size_t smem = (3 * kLMax * kLMax + 2 * kLMax * kLMax * kLMax) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(hodge_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    if (ntiles > 0) hodge_block_kernel<<<dim3(ntiles, 3), kHodgeThreads, smem, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Hodge: quadrature
+// General map / pointwise material: per element, interpolate the three
+// components at the q^3 Gauss points (sum factorisation), apply the 3x3
+// symmetric metric G = w gamma J^T J / det J (2-form pullback, Sec. 2.3),
+// integrate back against the same basis, scatter-add.  One CTA per element.
+constexpr int kQuadThreads = 128;
+
+__global__ void __launch_bounds__(kQuadThreads) hodge_quad_kernel(HodgeQuadArgs A, const double* __restrict__ x,
+                                                                  double* __restrict__ y) {
+    extern __shared__ double sm[];
+    const int e = blockIdx.x;
+    const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
+    const int el[3] = {ex, ey, ez};
+    const int qx = A.q[0], qy = A.q[1], qz = A.q[2];
+    const int Qe = qx * qy * qz;
+    double* U = sm;                 // 3 * Qe values at the Gauss points
+    double* T1 = U + 3 * Qe;        // scratch, <= Qe * kRMax
+    double* T2 = T1 + Qe * kRMax;   // scratch, <= Qe * kRMax
+    double* X = T2 + Qe * kRMax;    // local coefficients, <= kRMax^3
+    double* Bv = X + kRMax * kRMax * kRMax;  // 3 axes x q x kRMax
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    for (int c = 0; c < 3; ++c) {
+        const DevComp C = A.field.c[c];
+        const int rx = A.deg[c][0] + 1, ry = A.deg[c][1] + 1, rz = A.deg[c][2] + 1;
+        // basis values of this component's kinds on this element
+        for (int t = tid; t < 3 * 8 * kRMax; t += nt) {
+            const int a = t / (8 * kRMax), rem = t % (8 * kRMax), qp = rem / kRMax, r = rem % kRMax;
+            if (qp < A.q[a])
+                Bv[t] = __ldg(A.bval[a] + (((long long)A.kinds[c][a] * A.nel[a] + el[a]) * A.q[a] + qp) * kRMax + r);
+        }
+        for (int t = tid; t < rx * ry * rz; t += nt) {
+            const int r0 = t % rx, rr = t / rx, r1 = rr % ry, r2 = rr / ry;
+            const int gi = el[0] + r0 + A.koff[c][0], gj = el[1] + r1 + A.koff[c][1], gk = el[2] + r2 + A.koff[c][2];
+            double v = 0.0;
+            if (gi >= 0 && gi < C.n[0] && gj >= 0 && gj < C.n[1] && gk >= 0 && gk < C.n[2])
+                v = __ldg(x + C.off + gi + (long long)C.n[0] * (gj + (long long)C.n[1] * gk));
+            X[t] = v;
+        }
+        __syncthreads();
+        const double* Bx = Bv;
+        const double* By = Bv + 8 * kRMax;
+        const double* Bz = Bv + 16 * kRMax;
+        // T1[r2][r1][qx] = sum_r0 Bx[qx][r0] X[r2][r1][r0]
+        for (int t = tid; t < rz * ry * qx; t += nt) {
+            const int a = t % qx, rr = t / qx;
+            double acc = 0.0;
+            for (int r0 = 0; r0 < rx; ++r0) acc = fma(Bx[a * kRMax + r0], X[rr * rx + r0], acc);
+            T1[t] = acc;
+        }
+        __syncthreads();
+        // T2[r2][qy][qx] = sum_r1 By[qy][r1] T1[r2][r1][qx]
+        for (int t = tid; t < rz * qy * qx; t += nt) {
+            const int a = t % qx, rr = t / qx, b = rr % qy, r2 = rr / qy;
+            double acc = 0.0;
+            for (int r1 = 0; r1 < ry; ++r1) acc = fma(By[b * kRMax + r1], T1[(r2 * ry + r1) * qx + a], acc);
+            T2[t] = acc;
+        }
+        __syncthreads();
+        // U_c[qz][qy][qx] = sum_r2 Bz[qz][r2] T2[r2][qy][qx]
+        for (int t = tid; t < Qe; t += nt) {
+            const int ab = t % (qx * qy), g = t / (qx * qy);
+            double acc = 0.0;
+            for (int r2 = 0; r2 < rz; ++r2) acc = fma(Bz[g * kRMax + r2], T2[r2 * qx * qy + ab], acc);
+            U[c * Qe + t] = acc;
+        }
+        __syncthreads();
+    }
+    // metric at each Gauss point
+    for (int t = tid; t < Qe; t += nt) {
+        const int a = t % qx, rr = t / qx, b = rr % qy, g = rr / qy;
+        const long long qi = ((long long)(ez * qz + g) * A.Qn[1] + (ey * qy + b)) * A.Qn[0] + (ex * qx + a);
+        const double g00 = __ldg(A.G + qi), g01 = __ldg(A.G + A.Qtot + qi), g02 = __ldg(A.G + 2 * A.Qtot + qi);
+        const double g11 = __ldg(A.G + 3 * A.Qtot + qi), g12 = __ldg(A.G + 4 * A.Qtot + qi);
+        const double g22 = __ldg(A.G + 5 * A.Qtot + qi);
+        const double u0 = U[t], u1 = U[Qe + t], u2 = U[2 * Qe + t];
+        U[t] = g00 * u0 + g01 * u1 + g02 * u2;
+        U[Qe + t] = g01 * u0 + g11 * u1 + g12 * u2;
+        U[2 * Qe + t] = g02 * u0 + g12 * u1 + g22 * u2;
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+        const DevComp C = A.field.c[c];
+        const int rx = A.deg[c][0] + 1, ry = A.deg[c][1] + 1, rz = A.deg[c][2] + 1;
+        for (int t = tid; t < 3 * 8 * kRMax; t += nt) {
+            const int a = t / (8 * kRMax), rem = t % (8 * kRMax), qp = rem / kRMax, r = rem % kRMax;
+            if (qp < A.q[a])
+                Bv[t] = __ldg(A.bval[a] + (((long long)A.kinds[c][a] * A.nel[a] + el[a]) * A.q[a] + qp) * kRMax + r);
+        }
+        __syncthreads();
+        const double* Bx = Bv;
+        const double* By = Bv + 8 * kRMax;
+        const double* Bz = Bv + 16 * kRMax;
+        // T2[r2][qy][qx] = sum_qz Bz[qz][r2] V[qz][qy][qx]
+        for (int t = tid; t < rz * qy * qx; t += nt) {
+            const int ab = t % (qx * qy), r2 = t / (qx * qy);
+            double acc = 0.0;
+            for (int g = 0; g < qz; ++g) acc = fma(Bz[g * kRMax + r2], U[c * Qe + g * qx * qy + ab], acc);
+            T2[t] = acc;
+        }
+        __syncthreads();
+        // T1[r2][r1][qx] = sum_qy By[qy][r1] T2[r2][qy][qx]
+        for (int t = tid; t < rz * ry * qx; t += nt) {
+            const int a = t % qx, rr = t / qx, r1 = rr % ry, r2 = rr / ry;
+            double acc = 0.0;
+            for (int b = 0; b < qy; ++b) acc = fma(By[b * kRMax + r1], T2[(r2 * qy + b) * qx + a], acc);
+            T1[t] = acc;
+        }
+        __syncthreads();
+        // Y[r2][r1][r0] = sum_qx Bx[qx][r0] T1[r2][r1][qx], scatter-add
+        for (int t = tid; t < rx * ry * rz; t += nt) {
+            const int r0 = t % rx, rr = t / rx, r1 = rr % ry, r2 = rr / ry;
+            const int gi = el[0] + r0 + A.koff[c][0], gj = el[1] + r1 + A.koff[c][1], gk = el[2] + r2 + A.koff[c][2];
+            if (gi >= 0 && gi < C.n[0] && gj >= 0 && gj < C.n[1] && gk >= 0 && gk < C.n[2]) {
+                double acc = 0.0;
+                for (int a = 0; a < qx; ++a) acc = fma(Bx[a * kRMax + r0], T1[rr * qx + a], acc);
+                atomicAdd(y + C.off + gi + (long long)C.n[0] * (gj + (long long)C.n[1] * gk), acc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y, cudaStream_t s) {
+    const int nel = a.nel[0] * a.nel[1] * a.nel[2];
+    const int Qe = a.q[0] * a.q[1] * a.q[2];
+    const size_t smem = (3 * Qe + 2 * Qe * kRMax + kRMax * kRMax * kRMax + 3 * 8 * kRMax) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(hodge_quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    if (nel > 0) hodge_quad_kernel<<<nel, kQuadThreads, smem, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pairing solve sweeps
+// x = A^{-1} y along every line of one axis (Sec. 4.2: Eq. kroninverse and
+// the vec identity turn the Kronecker solve into independent 1D solves).
+// A = L U without pivoting: forward z_m = y_m - sum_k L(m,m-k) z_{m-k},
+// backward x_m = z_m / U(m,m) - sum_k U'(m,m+k) x_{m+k} with U' = U / diag.
+// A CTA stages kSolveLines lines in shared memory (coalesced loads), each
+// thread solves one line with a register window of the last KL values.
+template <int KL>
+__global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, const double* __restrict__ in,
+                                                                 double* __restrict__ out) {
+    extern __shared__ double sm[];
+    const int c = blockIdx.y;
+    const DevComp C = A.field.c[c];
+    const int axis = A.axis;
+    const int n = C.n[axis];
+    const long long ncomp = (long long)C.n[0] * C.n[1] * C.n[2];
+    const long long nlines = ncomp / n;
+    const long long l0 = (long long)blockIdx.x * kSolveLines;
+    if (l0 >= nlines) return;
+    const int nl = (int)min((long long)kSolveLines, nlines - l0);
+    const DevFactor F = A.f[c];
+    double* fL = sm;
+    double* fU = fL + n * KL;
+    double* fD = fU + n * KL;
+    double* S = fD + n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < n * KL; t += nt) {
+        fL[t] = __ldg(F.L + t);
+        fU[t] = __ldg(F.U + t);
+    }
+    for (int t = tid; t < n; t += nt) fD[t] = __ldg(F.dinv + t);
+    // layout: x lines as [line][m] with odd leading dimension, y/z lines as [m][line]
+    const int ldl = n | 1;
+    const long long nx = C.n[0], nxy = (long long)C.n[0] * C.n[1];
+    if (axis == 0) {
+        const double* src = in + C.off + l0 * n;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int line = g / n, m = g - line * n;
+            S[line * ldl + m] = __ldg(src + g);
+        }
+    } else if (tid < nl) {
+        const long long l = l0 + tid;
+        const long long base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        const long long stride = axis == 1 ? nx : nxy;
+        for (int m = 0; m < n; ++m) S[m * kSolveLines + tid] = __ldg(in + C.off + base + m * stride);
+    }
+    __syncthreads();
+    if (tid < nl) {
+        const int sL = axis == 0 ? ldl : 1;
+        const int sM = axis == 0 ? 1 : kSolveLines;
+        double* row = S + tid * sL;
+        double w[KL];
+#pragma unroll
+        for (int k = 0; k < KL; ++k) w[k] = 0.0;
+        for (int m = 0; m < n; ++m) {  // forward, unit lower L
+            double z = row[m * sM];
+#pragma unroll
+            for (int k = KL - 1; k >= 0; --k) z = fma(-fL[m * KL + k], w[k], z);
+#pragma unroll
+            for (int k = KL - 1; k > 0; --k) w[k] = w[k - 1];
+            w[0] = z;
+            row[m * sM] = z;
+        }
+#pragma unroll
+        for (int k = 0; k < KL; ++k) w[k] = 0.0;
+        for (int m = n - 1; m >= 0; --m) {  // backward, U scaled by its diagonal
+            double v = row[m * sM] * fD[m];
+#pragma unroll
+            for (int k = KL - 1; k >= 0; --k) v = fma(-fU[m * KL + k], w[k], v);
+#pragma unroll
+            for (int k = KL - 1; k > 0; --k) w[k] = w[k - 1];
+            w[0] = v;
+            row[m * sM] = v;
+        }
+    }
+    __syncthreads();
+    if (axis == 0) {
+        double* dst = out + C.off + l0 * n;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int line = g / n, m = g - line * n;
+            dst[g] = S[line * ldl + m];
+        }
+    } else if (tid < nl) {
+        const long long l = l0 + tid;
+        const long long base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        const long long stride = axis == 1 ? nx : nxy;
+        for (int m = 0; m < n; ++m) out[C.off + base + m * stride] = S[m * kSolveLines + tid];
+    }
+}
+
+template <int KL>
+static cudaError_t launch_solve_t(const SolveArgs& a, const double* in, double* out, cudaStream_t s) {
+    long long maxlines = 0;
+    int maxn = 0;
+    for (int c = 0; c < 3; ++c) {
+        const long long nc = (long long)a.field.c[c].n[0] * a.field.c[c].n[1] * a.field.c[c].n[2];
+        const int n = a.field.c[c].n[a.axis];
+        if (n > 0) maxlines = std::max(maxlines, nc / n);
+        maxn = std::max(maxn, n);
+    }
+    const size_t smem = ((size_t)(2 * KL + 1) * maxn + (size_t)(maxn | 1) * kSolveLines + 8) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(solve_axis_kernel<KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr = true;
+    }
+    const long long nb = (maxlines + kSolveLines - 1) / kSolveLines;
+    if (nb > 0) solve_axis_kernel<KL><<<dim3((unsigned)nb, 3), kSolveLines, smem, s>>>(a, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_axis(const SolveArgs& a, int kl, const double* in, double* out, cudaStream_t s) {
+    switch (kl) {
+        case 1: return launch_solve_t<1>(a, in, out, s);
+        case 2: return launch_solve_t<2>(a, in, out, s);
+        case 3: return launch_solve_t<3>(a, in, out, s);
+        case 4: return launch_solve_t<4>(a, in, out, s);
+        case 5: return launch_solve_t<5>(a, in, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+constexpr int kDotThreads = 256;
+
+__global__ void __launch_bounds__(kDotThreads) dot_partial_kernel(const double* __restrict__ x,
+                                                                  const double* __restrict__ y, long long n,
+                                                                  double* __restrict__ partial) {
+    __shared__ double red[kDotThreads];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc = fma(__ldg(x + i), __ldg(y + i), acc);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kDotThreads) dot_final_kernel(const double* __restrict__ partial, int np,
+                                                                double* __restrict__ out) {
+    __shared__ double red[kDotThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+cudaError_t launch_dot(const double* x, const double* y, long long n, double* partial, double* out,
+                       cudaStream_t s) {
+    dot_partial_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(x, y, n, partial);
+    dot_final_kernel<<<1, kDotThreads, 0, s>>>(partial, kDotBlocks, out);
+    return cudaGetLastError();
+}
+
+__global__ void scale_copy_kernel(const double* __restrict__ x, double* __restrict__ y, double a, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = a * x[i];
+}
+
+cudaError_t launch_scale_copy(const double* x, double* y, double a, long long n, cudaStream_t s) {
+    const long long nb = (n + 255) / 256;
+    if (nb > 0) scale_copy_kernel<<<(unsigned)nb, 256, 0, s>>>(x, y, a, n);
+    return cudaGetLastError();
+}
+
+}  // namespace smx

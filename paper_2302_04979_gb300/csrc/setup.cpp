@@ -1,0 +1,206 @@
+// Host-side FP64 setup: univariate bases, Gauss rules, pairing matrices and
+// their banded LU, element masses.  See setup.h for the conventions.
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace smx {
+
+// Component kinds (x, y, z) per field, Sec. 2.3 / Sec. 4.1:
+//   E (X^1_{h,0}): E_c has P1 along axis c, P0 along the others;
+//   B (X^2_{h,0}): B_c has P0 along axis c, P1 along the others;
+//   H (X~^1):      H_c has D1 along axis c, D0 along the others;
+//   D (X~^2):      D_c has D0 along axis c, D1 along the others.
+const int kFieldKinds[4][3][3] = {
+    {{P1, P0, P0}, {P0, P1, P0}, {P0, P0, P1}},
+    {{P0, P1, P1}, {P1, P0, P1}, {P1, P1, P0}},
+    {{D1, D0, D0}, {D0, D1, D0}, {D0, D0, D1}},
+    {{D0, D1, D1}, {D1, D0, D1}, {D1, D1, D0}},
+};
+
+int kind_degree(int kind, int p) {
+    switch (kind) {
+        case P0: return p;
+        case P1: return p - 1;
+        case D0: return p - 1;
+        default: return p - 2;
+    }
+}
+
+int kind_dim(int kind, int p, int nel) {
+    const int n = nel + p;
+    return (kind == P0 || kind == D1) ? n - 2 : n - 1;
+}
+
+int kind_offset(int kind) { return kind == P0 ? -1 : 0; }
+
+static bool kind_is_cs(int kind) { return kind == P1 || kind == D1; }
+
+// Knot i of the open uniform knot vector of degree d: d+1 zeros, k/nel, d+1 ones.
+static double knot(int d, int nel, int i) {
+    const int k = i - d;
+    if (k <= 0) return 0.0;
+    if (k >= nel) return 1.0;
+    return static_cast<double>(k) / nel;
+}
+
+void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (q + 0.5));  // guess for the (i+1)-th largest root
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            // P_q(z) and P_{q-1}(z) by the three-term recurrence
+            double p0 = 1.0, p1 = z;
+            if (q == 1) p1 = z;
+            for (int k = 2; k <= q; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pq = (q == 1) ? z : p1;
+            const double pqm1 = (q == 1) ? 1.0 : p0;
+            dp = q * (z * pq - pqm1) / (z * z - 1.0);
+            const double dz = pq / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // recompute the derivative at the converged root
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= q; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double pq = (q == 1) ? z : p1, pqm1 = (q == 1) ? 1.0 : p0;
+        dp = q * (z * pq - pqm1) / (z * z - 1.0);
+        // map [-1,1] -> [0,1]; roots come out descending in z, so ascending in (1-z)/2 order is reversed
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2/((1-z^2) P'^2)) * 1/2
+    }
+}
+
+void local_basis(int kind, int p, int nel, int e, double x, double* out) {
+    const int d = kind_degree(kind, p);
+    const int s = d + e;  // knot span: knot(s) <= x < knot(s+1)
+    double left[16], right[16];
+    out[0] = 1.0;
+    for (int j = 1; j <= d; ++j) {
+        left[j] = x - knot(d, nel, s + 1 - j);
+        right[j] = knot(d, nel, s + j) - x;
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            const double tmp = out[r] / (right[r + 1] + left[j - r]);
+            out[r] = saved + right[r + 1] * tmp;
+            saved = left[j - r] * tmp;
+        }
+        out[j] = saved;
+    }
+    if (kind_is_cs(kind)) {
+        for (int r = 0; r <= d; ++r) {
+            const int i = e + r;  // full index
+            out[r] *= (d + 1) / (knot(d, nel, i + d + 1) - knot(d, nel, i));
+        }
+    }
+}
+
+std::vector<double> pairing_matrix(int row_kind, int col_kind, int p, int nel) {
+    const int nr = kind_dim(row_kind, p, nel), nc = kind_dim(col_kind, p, nel);
+    const int dr = kind_degree(row_kind, p), dc = kind_degree(col_kind, p);
+    const int q = p + 1;
+    std::vector<double> gx, gw;
+    gauss_legendre01(q, gx, gw);
+    std::vector<double> A(static_cast<size_t>(nr) * nc, 0.0);
+    double vr[16], vc[16];
+    for (int e = 0; e < nel; ++e) {
+        for (int k = 0; k < q; ++k) {
+            const double x = (e + gx[k]) / nel, w = gw[k] / nel;
+            local_basis(row_kind, p, nel, e, x, vr);
+            local_basis(col_kind, p, nel, e, x, vc);
+            for (int a = 0; a <= dr; ++a) {
+                const int i = e + a + kind_offset(row_kind);
+                if (i < 0 || i >= nr) continue;
+                for (int b = 0; b <= dc; ++b) {
+                    const int j = e + b + kind_offset(col_kind);
+                    if (j < 0 || j >= nc) continue;
+                    A[static_cast<size_t>(i) * nc + j] += w * vr[a] * vc[b];
+                }
+            }
+        }
+    }
+    return A;
+}
+
+bool band_lu(const std::vector<double>& A0, int n, int kl, int ku, BandLU& out) {
+    std::vector<double> A(A0);
+    double amax = 0.0;
+    for (double v : A) amax = std::max(amax, std::fabs(v));
+    // Doolittle elimination without pivoting, restricted to the band
+    for (int k = 0; k < n; ++k) {
+        const double piv = A[static_cast<size_t>(k) * n + k];
+        if (!(std::fabs(piv) > 1e-12 * amax)) return false;
+        for (int i = k + 1; i <= std::min(n - 1, k + kl); ++i) {
+            const double l = A[static_cast<size_t>(i) * n + k] / piv;
+            A[static_cast<size_t>(i) * n + k] = l;
+            for (int j = k + 1; j <= std::min(n - 1, k + ku); ++j)
+                A[static_cast<size_t>(i) * n + j] -= l * A[static_cast<size_t>(k) * n + j];
+        }
+    }
+    out.n = n;
+    out.kl = kl;
+    out.ku = ku;
+    out.L.assign(static_cast<size_t>(n) * std::max(kl, 1), 0.0);
+    out.U.assign(static_cast<size_t>(n) * std::max(ku, 1), 0.0);
+    out.dinv.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double dii = A[static_cast<size_t>(i) * n + i];
+        out.dinv[i] = 1.0 / dii;
+        for (int k = 1; k <= kl; ++k)
+            if (i - k >= 0) out.L[static_cast<size_t>(i) * kl + k - 1] = A[static_cast<size_t>(i) * n + i - k];
+        for (int k = 1; k <= ku; ++k)
+            if (i + k < n) out.U[static_cast<size_t>(i) * ku + k - 1] = A[static_cast<size_t>(i) * n + i + k] / dii;
+    }
+    return true;
+}
+
+std::vector<double> band_lu_dense(const BandLU& f) {
+    const int n = f.n;
+    std::vector<double> L(static_cast<size_t>(n) * n, 0.0), U(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        L[static_cast<size_t>(i) * n + i] = 1.0;
+        for (int k = 1; k <= f.kl; ++k)
+            if (i - k >= 0) L[static_cast<size_t>(i) * n + i - k] = f.L[static_cast<size_t>(i) * f.kl + k - 1];
+        const double dii = 1.0 / f.dinv[i];
+        U[static_cast<size_t>(i) * n + i] = dii;
+        for (int k = 1; k <= f.ku; ++k)
+            if (i + k < n) U[static_cast<size_t>(i) * n + i + k] = f.U[static_cast<size_t>(i) * f.ku + k - 1] * dii;
+    }
+    std::vector<double> A(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double l = L[static_cast<size_t>(i) * n + k];
+            if (l == 0.0) continue;
+            for (int j = 0; j < n; ++j) A[static_cast<size_t>(i) * n + j] += l * U[static_cast<size_t>(k) * n + j];
+        }
+    return A;
+}
+
+std::vector<double> element_mass(int kind, int p, int nel, int e) {
+    const int d = kind_degree(kind, p), m = d + 1, q = p + 1;
+    std::vector<double> gx, gw;
+    gauss_legendre01(q, gx, gw);
+    std::vector<double> Me(static_cast<size_t>(m) * m, 0.0);
+    double v[16];
+    for (int k = 0; k < q; ++k) {
+        const double x = (e + gx[k]) / nel, w = gw[k] / nel;
+        local_basis(kind, p, nel, e, x, v);
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) Me[a * m + b] += w * v[a] * v[b];
+    }
+    return Me;
+}
+
+}  // namespace smx

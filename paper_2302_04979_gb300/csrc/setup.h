@@ -1,0 +1,55 @@
+// Host-side FP64 setup of the spline geometric leapfrog (not timed).
+//
+// Univariate spaces (Sec. 2.3 and the basis choice of Sec. 4.1): on each axis
+// with degree p and nel uniform elements, n = nel + p,
+//   kind P0: primal S_p(Xi) B-splines, first and last removed (BC)   dim n-2
+//   kind P1: primal S_{p-1}(Xi') Curry-Schoenberg                     dim n-1
+//   kind D0: dual   S_{p-1}(Xi') B-splines                            dim n-1
+//   kind D1: dual   S_{p-2}(Xi'') Curry-Schoenberg                    dim n-2
+// On element e every kind of degree d has the d+1 functions e..e+d of its
+// full (open-knot) basis; P0 shifts that index by -1 and drops 0 and n-1.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace smx {
+
+enum Kind { P0 = 0, P1 = 1, D0 = 2, D1 = 3 };
+
+// Space kinds along (x, y, z) of component c of each field (E, B, H, D).
+extern const int kFieldKinds[4][3][3];
+
+int kind_degree(int kind, int p);
+int kind_dim(int kind, int p, int nel);
+// index shift from the full basis numbering to the stored numbering (-1 for P0)
+int kind_offset(int kind);
+
+// Gauss-Legendre rule on [0,1] by Newton iteration on the Legendre recurrence.
+void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>& w);
+
+// Values of the d+1 basis functions of one kind that live on element e, at a
+// point x inside that element (full-basis numbering e..e+d; CS scaling applied).
+void local_basis(int kind, int p, int nel, int e, double x, double* out);
+
+// Dense univariate pairing matrix int phi_i psi_j (row kind, column kind), row-major.
+std::vector<double> pairing_matrix(int row_kind, int col_kind, int p, int nel);
+
+// Banded LU without pivoting: A = L U, L unit lower with kl sub-diagonals, U
+// upper with ku super-diagonals.  Returns false on a pivot below
+// tol * max|A| (the factor is then unusable).
+struct BandLU {
+    int n = 0, kl = 0, ku = 0;
+    std::vector<double> L;     // L[i*kl + k-1] = L(i, i-k), k = 1..kl
+    std::vector<double> U;     // U[i*ku + k-1] = U(i, i+k) / U(i,i), k = 1..ku
+    std::vector<double> dinv;  // 1 / U(i,i)
+};
+bool band_lu(const std::vector<double>& A, int n, int kl, int ku, BandLU& out);
+// Rebuild the dense matrix L * U (row-major) from a factor.
+std::vector<double> band_lu_dense(const BandLU& f);
+
+// Element mass matrix of one kind on element e: (d+1) x (d+1), row-major,
+// int_e phi_i phi_j with q = p+1 Gauss points.
+std::vector<double> element_mass(int kind, int p, int nel, int e);
+
+}  // namespace smx

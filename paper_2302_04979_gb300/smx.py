@@ -1,0 +1,276 @@
+"""Thin Python binding of the C ABI in include/smx.h (argument marshalling only).
+
+Every computation runs in libsmx.so's CUDA kernels; this module converts
+torch tensors to device pointers and checks status codes.  If the library is
+missing it raises: there is no CPU fallback.
+
+Names follow the C ABI: ``create``, ``sizes``, ``curl_primal``, ``curl_dual``,
+``hodge_apply``, ``pairing_solve``, ``hodge_star``, ``step``, ``energy``, ``cfl``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsmx.so")
+
+# ---- constants mirrored from include/smx.h
+OK, EINVAL, EGEOM, EMAT, ECUDA, ENONFINITE, ESTATE, ENOMEM, ESINGULAR = 0, -1, -2, -3, -4, -5, -6, -7, -8
+GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
+MAT_CONST, MAT_BLOCKS, MAT_POINTWISE = 0, 1, 2
+FIELD_E, FIELD_B, FIELD_H, FIELD_D = 0, 1, 2, 3
+
+MATERIAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("value", ctypes.c_double), ("blocks", ctypes.c_int * 3),
+                ("block_values", ctypes.POINTER(ctypes.c_double)), ("fn", MATERIAL_FN),
+                ("user", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int * 3), ("nel", ctypes.c_int * 3), ("geometry", ctypes.c_int),
+                ("geom_amplitude", ctypes.c_double), ("eps", Material), ("mu", Material)]
+
+
+class SmxError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, _lib().smx_strerror(status).decode(), status))
+
+
+_LIB = None
+
+_SIGS = {
+    "smx_create": [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)],
+    "smx_destroy": [ctypes.c_void_p],
+    "smx_sizes": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "smx_comp_shape": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
+    "smx_workspace_bytes": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+    "smx_bind_workspace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "smx_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
+    "smx_curl_primal": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
+    "smx_curl_dual": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                      ctypes.c_double],
+    "smx_hodge_apply": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_pairing_solve": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_hodge_star": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_step": [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int],
+    "smx_energy": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                   ctypes.POINTER(ctypes.c_double)],
+    "smx_cfl": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.POINTER(ctypes.c_double)],
+    "smx_factor_matrix": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                          ctypes.c_void_p],
+    "smx_hodge_mode": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "smx_step_host": [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int],
+    "smx_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
+    "smx_set_timing": [ctypes.c_void_p, ctypes.c_int],
+    "smx_kernel_times": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "smx_kernel_work": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_double)],
+}
+
+NCLASS = 8
+KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
+                  "reduction")
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsmx.so not built: run __graft_entry__.build() (no CPU fallback exists)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.smx_strerror.argtypes = [ctypes.c_int]
+        lib.smx_strerror.restype = ctypes.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def library():
+    return _lib()
+
+
+def _check(st, what):
+    if st != OK:
+        raise SmxError(st, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def material(spec):
+    """Build an smx_material from a number, ('blocks', array (b_z, b_y, b_x)) or a callable f(x, y, z).
+
+    Returns (Material, keepalive) -- keep the second object alive while the context is created.
+    """
+    m = Material()
+    keep = []
+    if callable(spec):
+        def cb(n, xyz, out, user):
+            pts = np.ctypeslib.as_array(xyz, shape=(n, 3))
+            res = np.ctypeslib.as_array(out, shape=(n,))
+            res[:] = spec(pts[:, 0], pts[:, 1], pts[:, 2])
+        fn = MATERIAL_FN(cb)
+        keep.append(fn)
+        m.kind, m.fn = MAT_POINTWISE, fn
+    elif isinstance(spec, tuple) and spec[0] == "blocks":
+        vals = np.ascontiguousarray(spec[1], dtype=np.float64)
+        keep.append(vals)
+        bz, by, bx = vals.shape
+        m.kind = MAT_BLOCKS
+        m.blocks[0], m.blocks[1], m.blocks[2] = bx, by, bz
+        m.block_values = vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    else:
+        m.kind, m.value = MAT_CONST, float(spec)
+    return m, keep
+
+
+def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0):
+    P = Params()
+    p = np.broadcast_to(np.asarray(p, dtype=int), (3,))
+    nel = np.broadcast_to(np.asarray(nel, dtype=int), (3,))
+    for a in range(3):
+        P.p[a], P.nel[a] = int(p[a]), int(nel[a])
+    P.geometry = {"identity": GEOM_IDENTITY, "sine_bump": GEOM_SINE_BUMP}[geometry]
+    P.geom_amplitude = float(amplitude)
+    P.eps, k1 = material(eps)
+    P.mu, k2 = material(mu)
+    return P, k1 + k2
+
+
+class Context:
+    """Owns an smx_ctx; the device workspace is a torch tensor bound by ``bind``."""
+
+    def __init__(self, p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0):
+        lib = _lib()
+        P, keep = make_params(p, nel, geometry, amplitude, eps, mu)
+        h = ctypes.c_void_p()
+        _check(lib.smx_create(ctypes.byref(P), ctypes.byref(h)), "smx_create")
+        del keep
+        self.h = h
+        ne, nh = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.smx_sizes(h, ctypes.byref(ne), ctypes.byref(nh)), "smx_sizes")
+        self.N_e, self.N_h = ne.value, nh.value
+        self.workspace = None
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _LIB is not None:
+            _LIB.smx_destroy(self.h)
+            self.h = None
+
+    def comp_shape(self, field, comp):
+        s = (ctypes.c_int64 * 3)()
+        _check(_lib().smx_comp_shape(self.h, field, comp, s), "smx_comp_shape")
+        return tuple(s)
+
+    def workspace_bytes(self):
+        n = ctypes.c_size_t()
+        _check(_lib().smx_workspace_bytes(self.h, ctypes.byref(n)), "smx_workspace_bytes")
+        return n.value
+
+    def bind(self, device="cuda"):
+        import torch
+        nbytes = self.workspace_bytes()
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        ptr = ws.data_ptr()
+        aligned = (ptr + 255) & ~255
+        _check(_lib().smx_bind_workspace(self.h, ctypes.c_void_p(aligned), nbytes), "smx_bind_workspace")
+        self.workspace = ws
+        return self
+
+    def set_stream(self, stream):
+        _check(_lib().smx_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)),
+               "smx_set_stream")
+
+    def factor_matrix(self, axis, which):
+        n = ctypes.c_int64()
+        _check(_lib().smx_factor_matrix(self.h, axis, which, ctypes.byref(n), None), "smx_factor_matrix")
+        out = np.zeros((n.value, n.value))
+        _check(_lib().smx_factor_matrix(self.h, axis, which, ctypes.byref(n), out.ctypes.data_as(ctypes.c_void_p)),
+               "smx_factor_matrix")
+        return out
+
+    def hodge_mode(self, field):
+        m = ctypes.c_int()
+        _check(_lib().smx_hodge_mode(self.h, field, ctypes.byref(m)), "smx_hodge_mode")
+        return m.value
+
+    # ---- hot-path stages
+    def curl_primal(self, e, b, alpha):
+        _check(_lib().smx_curl_primal(self.h, _ptr(e), _ptr(b), float(alpha)), "smx_curl_primal")
+
+    def curl_dual(self, h, d, alpha, jhat=None, s=0.0):
+        _check(_lib().smx_curl_dual(self.h, _ptr(h), _ptr(d), float(alpha), _ptr(jhat), float(s)), "smx_curl_dual")
+
+    def hodge_apply(self, field, x, y):
+        _check(_lib().smx_hodge_apply(self.h, field, _ptr(x), _ptr(y)), "smx_hodge_apply")
+
+    def pairing_solve(self, which, y, x):
+        _check(_lib().smx_pairing_solve(self.h, which, _ptr(y), _ptr(x)), "smx_pairing_solve")
+
+    def hodge_star(self, field, x, out):
+        _check(_lib().smx_hodge_star(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star")
+
+    def step(self, d, b, e, h, dt, nsteps, jhat=None, amp=None):
+        _check(_lib().smx_step(self.h, _ptr(d), _ptr(b), _ptr(e), _ptr(h), _ptr(jhat), _ptr(amp), float(dt),
+                               int(nsteps)), "smx_step")
+
+    def step_host(self, d, b, e, h, dt, nsteps, jhat=None, amp=None):
+        """Leapfrog on host (CPU, ideally pinned) float64 tensors; copies in and out inside the call."""
+        for t in (d, b, e, h):
+            if t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
+                raise ValueError("expected contiguous float64 host tensors")
+        _check(_lib().smx_step_host(self.h, *[ctypes.c_void_p(t.data_ptr()) for t in (d, b, e, h)], _ptr(jhat),
+                                    _ptr(amp), float(dt), int(nsteps)), "smx_step_host")
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        _check(_lib().smx_launch_count(self.h, ctypes.byref(n)), "smx_launch_count")
+        return n.value
+
+    def set_timing(self, on):
+        _check(_lib().smx_set_timing(self.h, 1 if on else 0), "smx_set_timing")
+
+    def kernel_times(self):
+        """{class: (milliseconds, launches)} of the launches bracketed since timing was switched on."""
+        ms = (ctypes.c_double * NCLASS)()
+        cnt = (ctypes.c_int64 * NCLASS)()
+        _check(_lib().smx_kernel_times(self.h, ms, cnt), "smx_kernel_times")
+        return {KERNEL_CLASSES[k]: (ms[k], cnt[k]) for k in range(NCLASS)}
+
+    def kernel_work(self, cls, field):
+        """(FP64 flops, minimal bytes) of one launch of kernel class cls writing field."""
+        f, b = ctypes.c_double(), ctypes.c_double()
+        _check(_lib().smx_kernel_work(self.h, KERNEL_CLASSES.index(cls) if isinstance(cls, str) else cls, field,
+                                      ctypes.byref(f), ctypes.byref(b)), "smx_kernel_work")
+        return f.value, b.value
+
+    def energy(self, d, b, e=None, dt=0.0):
+        out = (ctypes.c_double * 2)()
+        _check(_lib().smx_energy(self.h, _ptr(d), _ptr(b), _ptr(e), float(dt), out), "smx_energy")
+        return out[0], out[1]
+
+    def cfl(self, iters=500, tol=1e-12):
+        import torch
+        dev = self.workspace.device
+        v = torch.empty(self.N_e, dtype=torch.float64, device=dev)
+        w = torch.empty_like(v)
+        t = torch.empty(self.N_h, dtype=torch.float64, device=dev)
+        out = ctypes.c_double()
+        _check(_lib().smx_cfl(self.h, int(iters), float(tol), _ptr(v), _ptr(w), _ptr(t), ctypes.byref(out)),
+               "smx_cfl")
+        return out.value

@@ -1,0 +1,79 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+Holds none of the method's arithmetic: only counter-based random numbers
+(splitmix64, Steele, Lea & Flood 2014) and the input recipes of the
+benchmark configurations (material fields, source waveform).  The oracle and
+the CUDA path receive the same arrays from here.
+"""
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed, n, stream=0):
+    """n outputs of splitmix64 with state seed + (stream << 40) advanced by the golden gamma per draw."""
+    with np.errstate(over="ignore"):
+        base = np.uint64(seed) + (np.uint64(stream) << np.uint64(40)) * _GOLDEN
+        z = base + np.arange(1, n + 1, dtype=np.uint64) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed, n, lo=0.0, hi=1.0, stream=0):
+    u = (splitmix64(seed, n, stream) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return lo + (hi - lo) * u
+
+
+def normal(seed, n, stream=0):
+    """Standard normals by Box-Muller from two uniform streams."""
+    u1 = uniform(seed, n, stream=2 * stream + 1)
+    u2 = uniform(seed, n, stream=2 * stream + 2)
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def block_material(seed, blocks=(8, 8, 8), lo=1.0, hi=9.0):
+    """Piecewise-constant material on a block grid: array (b_z, b_y, b_x), uniform in [lo, hi)."""
+    bx, by, bz = blocks
+    return uniform(seed, bx * by * bz, lo, hi, stream=7).reshape(bz, by, bx)
+
+
+class GaussianBumps:
+    """eps(x) = 1 + 3 (1 - prod_k (1 - a_k exp(-|x - c_k|^2 / (2 s_k^2)))), values in [1, 4).
+
+    8 bumps with centres in [0,1]^3, widths in [0.05, 0.2], amplitudes in [0.5, 1].
+    """
+
+    def __init__(self, seed, nbumps=8):
+        self.c = uniform(seed, 3 * nbumps, 0.0, 1.0, stream=11).reshape(nbumps, 3)
+        self.s = uniform(seed, nbumps, 0.05, 0.2, stream=12)
+        self.a = uniform(seed, nbumps, 0.5, 1.0, stream=13)
+
+    def __call__(self, x, y, z):
+        x, y, z = np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64), np.asarray(z, dtype=np.float64)
+        prod = np.ones(np.broadcast(x, y, z).shape)
+        for k in range(len(self.s)):
+            r2 = (x - self.c[k, 0]) ** 2 + (y - self.c[k, 1]) ** 2 + (z - self.c[k, 2]) ** 2
+            prod = prod * (1.0 - self.a[k] * np.exp(-r2 / (2.0 * self.s[k] ** 2)))
+        return 1.0 + 3.0 * (1.0 - prod)
+
+
+def pulse_centre(seed):
+    return uniform(seed, 3, 0.3, 0.7, stream=21)
+
+
+def pulse_profile(centre, width=0.05):
+    """Spatial profile of the current J = z-hat g(x) s(t): a Gaussian of the given width."""
+    def J(x, y, z):
+        r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
+        g = np.exp(-r2 / (2.0 * width ** 2))
+        return np.array([0.0 * g, 0.0 * g, g])
+    return J
+
+
+def source_amplitudes(dt, nsteps, f0=1.0, tau=0.25, t0=0.75):
+    """s(t_n + dt/2) for the Gaussian-modulated carrier s(t) = sin(2 pi f0 t) exp(-(t - t0)^2 / (2 tau^2))."""
+    t = (np.arange(nsteps) + 0.5) * dt
+    return np.sin(2.0 * np.pi * f0 * t) * np.exp(-((t - t0) ** 2) / (2.0 * tau ** 2))

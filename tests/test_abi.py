@@ -1,0 +1,91 @@
+"""CPU tests of the C ABI: the library loads, exports every symbol include/smx.h
+declares, and its host-side setup (DoF numbering, univariate pairing factors,
+argument checks) agrees with the oracle.  No device work is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import forms3d, splines
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def smx():
+    from paper_2302_04979_gb300 import build, smx as mod
+    if not os.path.exists(mod.LIB_PATH):
+        build.build()
+    return mod
+
+
+def test_exports_every_declared_symbol(smx):
+    header = open(os.path.join(ROOT, "include", "smx.h")).read()
+    declared = set(re.findall(r"^\s*(?:const\s+char\s*\*|int)\s+(smx_\w+)\s*\(", header, re.M))
+    assert len(declared) >= 18
+    lib = smx.library()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+FIELDS = {"E": 0, "B": 1, "H": 2, "D": 3}
+
+
+@pytest.mark.parametrize("p,nel", [((2, 2, 2), (8, 8, 8)), ((3, 4, 2), (5, 3, 7)), ((4, 4, 4), (1, 2, 3))])
+def test_numbering_matches_oracle(smx, p, nel):
+    ctx = smx.Context(p, nel)
+    assert ctx.N_e == forms3d.field_size("E", p, nel) == forms3d.field_size("D", p, nel)
+    assert ctx.N_h == forms3d.field_size("B", p, nel) == forms3d.field_size("H", p, nel)
+    for f, fi in FIELDS.items():
+        for c in range(3):
+            nx, ny, nz = ctx.comp_shape(fi, c)
+            assert (nz, ny, nx) == forms3d.comp_shape(f, c, p, nel)
+
+
+@pytest.mark.parametrize("p,nel", [(2, 1), (2, 7), (3, 4), (4, 9), (5, 3), (6, 2)])
+def test_pairing_factors_match_oracle(smx, p, nel):
+    ctx = smx.Context(p, nel)
+    G, M = splines.G_hat(p, nel), splines.M_hat(p, nel)
+    for axis in range(3):
+        np.testing.assert_allclose(ctx.factor_matrix(axis, 0), G, atol=1e-14)
+        np.testing.assert_allclose(ctx.factor_matrix(axis, 1), M, atol=1e-14)
+        np.testing.assert_allclose(ctx.factor_matrix(axis, 2), G.T, atol=1e-14)
+        np.testing.assert_allclose(ctx.factor_matrix(axis, 3), M.T, atol=1e-14)
+
+
+def test_hodge_mode_selection(smx):
+    assert smx.Context(3, 4).hodge_mode(smx.FIELD_D) == 0
+    assert smx.Context(3, 8, eps=("blocks", np.ones((2, 2, 2)))).hodge_mode(smx.FIELD_D) == 0
+    ctx = smx.Context(3, 4, geometry="sine_bump")
+    assert ctx.hodge_mode(smx.FIELD_D) == 1 and ctx.hodge_mode(smx.FIELD_B) == 1
+    ctx = smx.Context(3, 4, eps=lambda x, y, z: 1.0 + x)
+    assert ctx.hodge_mode(smx.FIELD_D) == 1 and ctx.hodge_mode(smx.FIELD_B) == 0
+
+
+def test_argument_errors(smx):
+    def status(**kw):
+        try:
+            smx.Context(**kw)
+            return smx.OK
+        except smx.SmxError as e:
+            return e.status
+    assert status(p=1, nel=4) == smx.EINVAL
+    assert status(p=3, nel=0) == smx.EINVAL
+    assert status(p=3, nel=4, eps=-1.0) == smx.EMAT
+    assert status(p=3, nel=4, mu=float("nan")) == smx.EMAT
+    assert status(p=3, nel=6, eps=("blocks", np.ones((4, 4, 4)))) == smx.EINVAL  # 4 does not divide 6
+    assert status(p=3, nel=4, eps=("blocks", -np.ones((2, 2, 2)))) == smx.EMAT
+    assert status(p=3, nel=4, geometry="sine_bump", amplitude=0.5) == smx.EGEOM  # det J <= 0 somewhere
+    assert status(p=3, nel=4, geometry="sine_bump", eps=lambda x, y, z: 0.0 * x) == smx.EMAT
+
+
+def test_calls_without_workspace_are_rejected(smx):
+    ctx = smx.Context(2, 2)
+    lib = smx.library()
+    assert lib.smx_hodge_apply(ctx.h, smx.FIELD_B, ctypes.c_void_p(8), ctypes.c_void_p(16)) == smx.ESTATE
+    assert lib.smx_step(ctx.h, *([ctypes.c_void_p(8)] * 4), None, None, 0.1, 1) == smx.ESTATE
+    assert lib.smx_bind_workspace(ctx.h, ctypes.c_void_p(256), 16) == smx.ESTATE
+    assert lib.smx_bind_workspace(ctx.h, None, 1 << 30) == smx.EINVAL
+    assert lib.smx_strerror(smx.EGEOM).startswith(b"geometry")
