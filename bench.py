@@ -225,12 +225,14 @@ def run_ours(args, rank, world, local):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = ctx.launch_count()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_region")
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
         ctx.step(d, b, e, h, dt, 1)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     launches = ctx.launch_count() - launches0
