@@ -45,6 +45,7 @@ extern "C" {
 #define SMX_ESTATE (-6)      /* workspace missing or too small */
 #define SMX_ENOMEM (-7)      /* host allocation failed */
 #define SMX_ESINGULAR (-8)   /* a 1D pairing factor has a (near) zero pivot */
+#define SMX_ENOSPACE (-9)    /* problem larger than the library's fixed device array (SMX_NOALLOC_BYTES) */
 
 /* ---- geometry map F : (0,1)^3 -> Omega (Sec. 2.3) ---- */
 #define SMX_GEOM_IDENTITY 0  /* F = identity: the unit-cube cavity of Sec. 5.1.1 */
@@ -197,6 +198,38 @@ int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);
  * read once, each output written once).  SMX_EINVAL for a class that the
  * context does not launch for that field. */
 int smx_kernel_work(const smx_ctx* ctx, int cls, int field, double* flops, double* bytes);
+
+/* Allocation-free variant of smx_hodge_star, for callers that cannot allocate
+ * device memory at all -- code running where cudaMalloc is unavailable or
+ * forbidden (inside another library's memory pool, a sandboxed plug-in, a
+ * process whose allocator is owned by someone else) and that therefore cannot
+ * provide the workspace the other calls need.  The paper has no counterpart;
+ * this is a deployment convenience.
+ *
+ * Computes the same result as smx_hodge_star (e = K_1^{-1} M~ d for
+ * SMX_FIELD_D, h = K~_1^{-1} M b for SMX_FIELD_B) with the caller passing only
+ * the input x and the output out (device, FP64).  The tables and the
+ * intermediate vector live in one fixed array of SMX_NOALLOC_BYTES (16 MiB)
+ * that the library image reserves on every GPU that loads it, until the
+ * process exits.  No workspace needs to be bound, and the call itself makes
+ * no device allocation (no cudaMalloc, cudaFree or allocating library call).
+ *
+ * Limits and behaviour:
+ *  - the context's tables plus one field vector must fit in SMX_NOALLOC_BYTES,
+ *    otherwise SMX_ENOSPACE (about 0.9M degrees of freedom per field at p = 3);
+ *  - only the block-Kronecker Hodge (identity map, constant or block material)
+ *    is supported: the quadrature tables of curved maps or pointwise
+ *    materials are too large, and the call returns SMX_EINVAL;
+ *  - the first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture;
+ *  - the array is shared by every context and every call on the device and
+ *    keeps the last call's contents; a call re-uploads its context's tables
+ *    (an asynchronous host-to-device copy on the context stream) when another
+ *    context used the array last, and clears the intermediate vector itself;
+ *  - calls that overlap on the GPU (different streams, or different contexts
+ *    without ordering between them) race on the array; serialise them. */
+#define SMX_NOALLOC_BYTES (16u << 20)
+int smx_hodge_star_noalloc(smx_ctx* ctx, int field, const double* x, double* out);
 
 /* Diagnostics for tests: copy the host-side banded LU of one 1D factor.
  * axis 0..2; which 0 = G-hat, 1 = M-hat, 2 = G-hat^T, 3 = M-hat^T (Sec. 4.1).

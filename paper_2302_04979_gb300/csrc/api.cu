@@ -13,7 +13,13 @@
 #include "internal.h"
 #include "setup.h"
 
+#include <atomic>
+
 using namespace smx;
+
+namespace smx {
+int noalloc_region(void** base, uint64_t** owner);  // noalloc.cu
+}
 
 namespace {
 
@@ -55,6 +61,7 @@ uint64_t splitmix64(uint64_t& s) {
 }  // namespace
 
 struct smx_ctx {
+    uint64_t uid = 0;  // unique per context (which tables the static no-alloc array holds)
     int p[3], nel[3];
     int geometry;
     double amp;
@@ -365,6 +372,7 @@ const char* smx_strerror(int s) {
         case SMX_ESTATE: return "workspace missing or too small";
         case SMX_ENOMEM: return "host allocation failed";
         case SMX_ESINGULAR: return "singular 1D pairing factor";
+        case SMX_ENOSPACE: return "problem larger than the fixed no-alloc device array";
         default: return "unknown status";
     }
 }
@@ -384,6 +392,8 @@ int smx_create(const smx_params* P, smx_ctx** out) {
     if (st) return st;
     smx_ctx* C = new (std::nothrow) smx_ctx();
     if (!C) return SMX_ENOMEM;
+    static std::atomic<uint64_t> next_uid{1};
+    C->uid = next_uid.fetch_add(1);
     try {
         for (int a = 0; a < 3; ++a) {
             C->p[a] = P->p[a];
@@ -791,6 +801,62 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
         default:
             return SMX_EINVAL;
     }
+}
+
+int smx_hodge_star_noalloc(smx_ctx* C, int field, const double* x, double* out) {
+    if (!C || !x || !out) return SMX_EINVAL;
+    if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
+    const int h = field == SMX_FIELD_B ? 0 : 1;
+    const HodgeHost& H = C->hodge[h];
+    if (H.mode != 0) return SMX_EINVAL;  // quadrature tables do not fit the fixed array
+    const int fld = kFieldOfHodge[h];
+    const long long n = C->fld[fld].total;
+    // layout of the fixed array: this context's tables (as in the workspace), then one vector
+    const size_t o_y = C->tables_bytes;
+    if (o_y + (size_t)n * sizeof(double) > (size_t)SMX_NOALLOC_BYTES) return SMX_ENOSPACE;
+    void* basev = nullptr;
+    uint64_t* owner = nullptr;
+    const int st = noalloc_region(&basev, &owner);
+    if (st) return st;
+    unsigned char* base = static_cast<unsigned char*>(basev);
+    if (*owner != C->uid) {
+        CK(cudaMemcpyAsync(base, C->blob.bytes.data(), C->blob.bytes.size(), cudaMemcpyHostToDevice, C->stream));
+        *owner = C->uid;
+    }
+    HodgeBlockArgs A;
+    A.field = C->fld[fld];
+    for (int a = 0; a < 3; ++a) {
+        A.ntile[a] = H.ntile[a];
+        A.tf0[a] = reinterpret_cast<const int*>(base + H.o_tf0[a]);
+        A.tlen[a] = reinterpret_cast<const int*>(base + H.o_tlen[a]);
+        A.tmat[a] = reinterpret_cast<const double*>(base + H.o_tmat[a]);
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a) {
+            A.kinds[c][a] = kFieldKinds[fld][c][a];
+            A.deg[c][a] = kind_degree(A.kinds[c][a], C->p[a]);
+        }
+    A.gamma = reinterpret_cast<const double*>(base + H.o_gamma);
+    const int which = h == 0 ? 1 : 0;  // M^2 -> K~_1 solve, M~^2 -> K_1 solve
+    SolveArgs S[3];
+    for (int a = 0; a < 3; ++a) {
+        S[a].field = C->fld[which == 0 ? SMX_FIELD_D : SMX_FIELD_B];
+        S[a].axis = a;
+        for (int c = 0; c < 3; ++c) {
+            const int w = factor_index(which, c, a);
+            S[a].f[c].L = reinterpret_cast<const double*>(base + C->o_fac[a][w][0]);
+            S[a].f[c].U = reinterpret_cast<const double*>(base + C->o_fac[a][w][1]);
+            S[a].f[c].dinv = reinterpret_cast<const double*>(base + C->o_fac[a][w][2]);
+            S[a].f[c].n = C->fac[a][w].n;
+        }
+    }
+    double* y = reinterpret_cast<double*>(base + o_y);
+    CK(cudaMemsetAsync(y, 0, (size_t)n * sizeof(double), C->stream));  // the mass apply accumulates
+    CK(launch_hodge_block(A, x, y, C->stream));
+    CK(launch_solve_axis(S[0], C->p[0] - 1, y, out, C->stream));
+    CK(launch_solve_axis(S[1], C->p[1] - 1, out, out, C->stream));
+    CK(launch_solve_axis(S[2], C->p[2] - 1, out, out, C->stream));
+    return SMX_OK;
 }
 
 int smx_factor_matrix(const smx_ctx* C, int axis, int which, int64_t* n, double* dense_out) {

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsmx.so")
 
 # ---- constants mirrored from include/smx.h
-OK, EINVAL, EGEOM, EMAT, ECUDA, ENONFINITE, ESTATE, ENOMEM, ESINGULAR = 0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, EINVAL, EGEOM, EMAT, ECUDA, ENONFINITE, ESTATE, ENOMEM, ESINGULAR, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 MAT_CONST, MAT_BLOCKS, MAT_POINTWISE = 0, 1, 2
 FIELD_E, FIELD_B, FIELD_H, FIELD_D = 0, 1, 2, 3
@@ -58,6 +58,7 @@ _SIGS = {
     "smx_hodge_apply": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_pairing_solve": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_hodge_star": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_hodge_star_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_step": [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int],
     "smx_energy": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                    ctypes.POINTER(ctypes.c_double)],
@@ -224,6 +225,10 @@ class Context:
 
     def hodge_star(self, field, x, out):
         _check(_lib().smx_hodge_star(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star")
+
+    def hodge_star_noalloc(self, field, x, out):
+        """hodge_star without a bound workspace: tables and scratch in the library's fixed device array."""
+        _check(_lib().smx_hodge_star_noalloc(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star_noalloc")
 
     def step(self, d, b, e, h, dt, nsteps, jhat=None, amp=None):
         _check(_lib().smx_step(self.h, _ptr(d), _ptr(b), _ptr(e), _ptr(h), _ptr(jhat), _ptr(amp), float(dt),
