@@ -27,6 +27,7 @@ struct HodgeHost {
     int mode = 0;  // 0 block Kronecker, 1 quadrature
     // block mode
     int ntile[3] = {0, 0, 0};
+    int max_nloc = 0;
     std::vector<int> tf0[3], tlen[3];
     std::vector<double> tmat[3];
     std::vector<double> gamma;
@@ -186,7 +187,15 @@ int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
             }
         }
     }
-    (void)field;
+    H.max_nloc = 0;
+    for (int c = 0; c < 3; ++c) {
+        int lmax[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+            const int kind = kFieldKinds[field][c][a];
+            for (int t = 0; t < H.ntile[a]; ++t) lmax[a] = std::max(lmax[a], H.tlen[a][kind * H.ntile[a] + t]);
+        }
+        H.max_nloc = std::max(H.max_nloc, lmax[0] * lmax[1] * lmax[2]);
+    }
     H.gamma.assign((size_t)H.ntile[0] * H.ntile[1] * H.ntile[2], 0.0);
     for (int tz = 0; tz < H.ntile[2]; ++tz)
         for (int ty = 0; ty < H.ntile[1]; ++ty)
@@ -564,6 +573,7 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                     A.deg[c][a] = kind_degree(A.kinds[c][a], C->p[a]);
                 }
             A.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
+            A.max_nloc = H.max_nloc;
         } else {
             HodgeQuadArgs& A = C->hq[h];
             A.field = C->fld[fld];
@@ -837,6 +847,7 @@ int smx_hodge_star_noalloc(smx_ctx* C, int field, const double* x, double* out) 
             A.deg[c][a] = kind_degree(A.kinds[c][a], C->p[a]);
         }
     A.gamma = reinterpret_cast<const double*>(base + H.o_gamma);
+    A.max_nloc = H.max_nloc;
     const int which = h == 0 ? 1 : 0;  // M^2 -> K~_1 solve, M~^2 -> K_1 solve
     SolveArgs S[3];
     for (int a = 0; a < 3; ++a) {

@@ -49,6 +49,7 @@ struct HodgeBlockArgs {
     const int* tlen[3];      // number of local functions
     const double* tmat[3];   // (kind * ntile[a] + t) * kLMax^2: dense tile mass, row-major
     const double* gamma;     // per tile, x fastest
+    int max_nloc;            // largest Lx*Ly*Lz over tiles and components (sizes shared memory)
 };
 
 // Quadrature Hodge apply (curved map or pointwise material).

@@ -12,83 +12,79 @@
 namespace smx {
 
 // ------------------------------------------------------------------ curl
-// Primal incidence along axis a (Remark on incidence matrices after Table 1):
-// (d u)_m = u_m - u_{m-1}, with u_m = 0 outside [0, n_a) (the removed BC functions).
-__device__ __forceinline__ double primal_diff(const DevComp& u, const double* __restrict__ v, int i, int j,
-                                              int k, int a) {
-    const long long base = u.off + i + (long long)u.n[0] * (j + (long long)u.n[1] * k);
-    const long long stride = a == 0 ? 1LL : (a == 1 ? (long long)u.n[0] : (long long)u.n[0] * u.n[1]);
-    const int m = a == 0 ? i : (a == 1 ? j : k);
-    const double hi = (m < u.n[a]) ? __ldg(v + base) : 0.0;
-    const double lo = (m >= 1) ? __ldg(v + base - stride) : 0.0;
+// Incidence along axis a (Remark on incidence matrices after Table 1):
+//   primal (d u)_m = u_m - u_{m-1}, u_m = 0 outside [0, n_a) (removed BC functions);
+//   dual   (d u)_m = u_{m+1} - u_m (the input has one more entry along a).
+// (curl u)_c = d_{c+1} u_{c+2} - d_{c+2} u_{c+1}.  One thread per output
+// coefficient on a 3D grid (x, y, component * z); the component is a
+// template parameter so every extent and stride is a compile-time field.
+template <int A, bool DUAL>
+__device__ __forceinline__ double incidence(const DevComp& u, const double* __restrict__ v, int i, int j, int k) {
+    const int idx = i + u.n[0] * (j + u.n[1] * k);
+    const int stride = A == 0 ? 1 : (A == 1 ? u.n[0] : u.n[0] * u.n[1]);
+    const double* p = v + u.off + idx;
+    if (DUAL) return __ldg(p + stride) - __ldg(p);
+    const int m = A == 0 ? i : (A == 1 ? j : k);
+    const double hi = (m < u.n[A]) ? __ldg(p) : 0.0;
+    const double lo = (m >= 1) ? __ldg(p - stride) : 0.0;
     return hi - lo;
 }
 
-// Dual incidence along axis a: (d u)_m = u_{m+1} - u_m (input has one more entry along a).
-__device__ __forceinline__ double dual_diff(const DevComp& u, const double* __restrict__ v, int i, int j, int k,
-                                            int a) {
-    const long long base = u.off + i + (long long)u.n[0] * (j + (long long)u.n[1] * k);
-    const long long stride = a == 0 ? 1LL : (a == 1 ? (long long)u.n[0] : (long long)u.n[0] * u.n[1]);
-    return __ldg(v + base + stride) - __ldg(v + base);
-}
-
-__device__ __forceinline__ void decode(const DevField& F, long long idx, int& c, int& i, int& j, int& k) {
-    c = (idx >= F.c[1].off) + (idx >= F.c[2].off);
-    const long long r = idx - F.c[c].off;
-    const int nx = F.c[c].n[0], ny = F.c[c].n[1];
-    const long long t = r / nx;
-    i = static_cast<int>(r - t * nx);
-    j = static_cast<int>(t % ny);
-    k = static_cast<int>(t / ny);
-}
-
-// b += alpha * D^1 e, (curl E)_c = d_{c+1} E_{c+2} - d_{c+2} E_{c+1}  (Eq. discrete2_faraday)
-__global__ void __launch_bounds__(256) curl_primal_kernel(DevField E, DevField B, const double* __restrict__ e,
-                                                          double* __restrict__ b, double alpha) {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= B.total) return;
-    int c, i, j, k;
-    decode(B, idx, c, i, j, k);
-    const int a1 = c == 2 ? 0 : c + 1, a2 = c == 0 ? 2 : c - 1;
-    const double v = primal_diff(E.c[a2], e, i, j, k, a1) - primal_diff(E.c[a1], e, i, j, k, a2);
-    b[idx] = fma(alpha, v, b[idx]);
-}
-
-// d += alpha * (D~^1 h - s jhat)  (Eq. discrete2_ampere)
-__global__ void __launch_bounds__(256) curl_dual_kernel(DevField H, DevField D, const double* __restrict__ h,
-                                                        double* __restrict__ d, double alpha,
-                                                        const double* __restrict__ jhat,
-                                                        const double* __restrict__ amp, int amp_index,
-                                                        double s_host) {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= D.total) return;
-    int c, i, j, k;
-    decode(D, idx, c, i, j, k);
-    const int a1 = c == 2 ? 0 : c + 1, a2 = c == 0 ? 2 : c - 1;
-    double v = dual_diff(H.c[a2], h, i, j, k, a1) - dual_diff(H.c[a1], h, i, j, k, a2);
-    if (jhat != nullptr) {
+template <int C, bool DUAL>
+__device__ __forceinline__ void curl_comp(const DevField& IN, const DevField& OUT, const double* __restrict__ in,
+                                          double* __restrict__ out, double alpha, const double* __restrict__ jhat,
+                                          const double* __restrict__ amp, int amp_index, double s_host, int i, int j,
+                                          int k) {
+    constexpr int a1 = (C + 1) % 3, a2 = (C + 2) % 3;
+    const DevComp& O = OUT.c[C];
+    if (i >= O.n[0] || j >= O.n[1] || k >= O.n[2]) return;
+    double v = incidence<a1, DUAL>(IN.c[a2], in, i, j, k) - incidence<a2, DUAL>(IN.c[a1], in, i, j, k);
+    const long long g = O.off + i + O.n[0] * (j + O.n[1] * k);
+    if (DUAL && jhat != nullptr) {
         const double s = amp != nullptr ? __ldg(amp + amp_index) : s_host;
-        v = fma(-s, __ldg(jhat + idx), v);
+        v = fma(-s, __ldg(jhat + g), v);
     }
-    d[idx] = fma(alpha, v, d[idx]);
+    out[g] = fma(alpha, v, out[g]);
+}
+
+template <bool DUAL>
+__global__ void __launch_bounds__(128) curl_kernel(DevField IN, DevField OUT, const double* __restrict__ in,
+                                                   double* __restrict__ out, double alpha,
+                                                   const double* __restrict__ jhat, const double* __restrict__ amp,
+                                                   int amp_index, double s_host, int nzmax) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int c = blockIdx.z / nzmax;
+    const int k = blockIdx.z - c * nzmax;
+    if (c == 0)
+        curl_comp<0, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
+    else if (c == 1)
+        curl_comp<1, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
+    else
+        curl_comp<2, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
+}
+
+template <bool DUAL>
+static cudaError_t launch_curl(const DevField& IN, const DevField& OUT, const double* in, double* out, double alpha,
+                               const double* jhat, const double* amp, int amp_index, double s_host, cudaStream_t s) {
+    int nmax[3] = {0, 0, 0};
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a) nmax[a] = std::max(nmax[a], OUT.c[c].n[a]);
+    if (OUT.total == 0) return cudaSuccess;
+    const dim3 grid((nmax[0] + 127) / 128, nmax[1], 3 * nmax[2]);
+    curl_kernel<DUAL><<<grid, 128, 0, s>>>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, nmax[2]);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b, double alpha,
                                cudaStream_t s) {
-    const int nt = 256;
-    const long long nb = (B.total + nt - 1) / nt;
-    if (nb > 0) curl_primal_kernel<<<static_cast<unsigned>(nb), nt, 0, s>>>(E, B, e, b, alpha);
-    return cudaGetLastError();
+    return launch_curl<false>(E, B, e, b, alpha, nullptr, nullptr, 0, 0.0, s);
 }
 
 cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double* h, double* d, double alpha,
                              const double* jhat, const double* amp, int amp_index, double s_host,
                              cudaStream_t s) {
-    const int nt = 256;
-    const long long nb = (D.total + nt - 1) / nt;
-    if (nb > 0)
-        curl_dual_kernel<<<static_cast<unsigned>(nb), nt, 0, s>>>(H, D, h, d, alpha, jhat, amp, amp_index, s_host);
-    return cudaGetLastError();
+    return launch_curl<true>(H, D, h, d, alpha, jhat, amp, amp_index, s_host, s);
 }
 
 // ------------------------------------------------------------------ Hodge: block Kronecker
@@ -172,10 +168,11 @@ __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockAr
 
 cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s) {
     const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
-    const size_t smem = (3 * kLMax * kLMax + 2 * kLMax * kLMax * kLMax) * sizeof(double);
+    const size_t smem = (3 * kLMax * kLMax + 2 * (size_t)a.max_nloc) * sizeof(double);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(hodge_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(hodge_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((3 * kLMax * kLMax + 2 * kLMax * kLMax * kLMax) * sizeof(double)));
         attr = true;
     }
     if (ntiles > 0) hodge_block_kernel<<<dim3(ntiles, 3), kHodgeThreads, smem, s>>>(a, x, y);
@@ -323,8 +320,16 @@ cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y
 // the vec identity turn the Kronecker solve into independent 1D solves).
 // A = L U without pivoting: forward z_m = y_m - sum_k L(m,m-k) z_{m-k},
 // backward x_m = z_m / U(m,m) - sum_k U'(m,m+k) x_{m+k} with U' = U / diag.
-// A CTA stages kSolveLines lines in shared memory (coalesced loads), each
-// thread solves one line with a register window of the last KL values.
+// A CTA stages kSolveLines lines in shared memory with asynchronous copies
+// (every load of the chunk in flight at once), each thread then solves one
+// line with a register window of the last KL values, and the chunk is
+// written back with coalesced stores.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int KL>
 __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, const double* __restrict__ in,
                                                                  double* __restrict__ out) {
@@ -333,11 +338,11 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
     const int n = C.n[axis];
-    const long long ncomp = (long long)C.n[0] * C.n[1] * C.n[2];
-    const long long nlines = ncomp / n;
-    const long long l0 = (long long)blockIdx.x * kSolveLines;
+    const int ncomp = C.n[0] * C.n[1] * C.n[2];
+    const int nlines = ncomp / n;
+    const int l0 = blockIdx.x * kSolveLines;
     if (l0 >= nlines) return;
-    const int nl = (int)min((long long)kSolveLines, nlines - l0);
+    const int nl = min(kSolveLines, nlines - l0);
     const DevFactor F = A.f[c];
     double* fL = sm;
     double* fU = fL + n * KL;
@@ -345,25 +350,27 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
     double* S = fD + n;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = tid; t < n * KL; t += nt) {
-        fL[t] = __ldg(F.L + t);
-        fU[t] = __ldg(F.U + t);
+        cp_async8(fL + t, F.L + t);
+        cp_async8(fU + t, F.U + t);
     }
-    for (int t = tid; t < n; t += nt) fD[t] = __ldg(F.dinv + t);
+    for (int t = tid; t < n; t += nt) cp_async8(fD + t, F.dinv + t);
     // layout: x lines as [line][m] with odd leading dimension, y/z lines as [m][line]
     const int ldl = n | 1;
-    const long long nx = C.n[0], nxy = (long long)C.n[0] * C.n[1];
+    const int nx = C.n[0], nxy = C.n[0] * C.n[1];
+    const double* src = in + C.off;
     if (axis == 0) {
-        const double* src = in + C.off + l0 * n;
+        const double* chunk = src + (long long)l0 * n;
         for (int g = tid; g < nl * n; g += nt) {
             const int line = g / n, m = g - line * n;
-            S[line * ldl + m] = __ldg(src + g);
+            cp_async8(S + line * ldl + m, chunk + g);
         }
     } else if (tid < nl) {
-        const long long l = l0 + tid;
-        const long long base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-        const long long stride = axis == 1 ? nx : nxy;
-        for (int m = 0; m < n; ++m) S[m * kSolveLines + tid] = __ldg(in + C.off + base + m * stride);
+        const int l = l0 + tid;
+        const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        const int stride = axis == 1 ? nx : nxy;
+        for (int m = 0; m < n; ++m) cp_async8(S + m * kSolveLines + tid, src + base + m * stride);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (tid < nl) {
         const int sL = axis == 0 ? ldl : 1;
@@ -372,6 +379,7 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
         double w[KL];
 #pragma unroll
         for (int k = 0; k < KL; ++k) w[k] = 0.0;
+#pragma unroll 2
         for (int m = 0; m < n; ++m) {  // forward, unit lower L
             double z = row[m * sM];
 #pragma unroll
@@ -383,6 +391,7 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
         }
 #pragma unroll
         for (int k = 0; k < KL; ++k) w[k] = 0.0;
+#pragma unroll 2
         for (int m = n - 1; m >= 0; --m) {  // backward, U scaled by its diagonal
             double v = row[m * sM] * fD[m];
 #pragma unroll
@@ -394,17 +403,19 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
         }
     }
     __syncthreads();
+    double* dst = out + C.off;
     if (axis == 0) {
-        double* dst = out + C.off + l0 * n;
+        double* chunk = dst + (long long)l0 * n;
         for (int g = tid; g < nl * n; g += nt) {
             const int line = g / n, m = g - line * n;
-            dst[g] = S[line * ldl + m];
+            chunk[g] = S[line * ldl + m];
         }
     } else if (tid < nl) {
-        const long long l = l0 + tid;
-        const long long base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-        const long long stride = axis == 1 ? nx : nxy;
-        for (int m = 0; m < n; ++m) out[C.off + base + m * stride] = S[m * kSolveLines + tid];
+        const int l = l0 + tid;
+        const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        const int stride = axis == 1 ? nx : nxy;
+#pragma unroll 4
+        for (int m = 0; m < n; ++m) dst[base + m * stride] = S[m * kSolveLines + tid];
     }
 }
 
