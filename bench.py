@@ -182,6 +182,87 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+HBM_PEAK_GBS = 6793.1   # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+
+
+def kernel_table(ctx, smx, ktimes):
+    """Per-kernel-class launches, time, share and algorithmic work per launch."""
+    mode = {smx.FIELD_B: ctx.hodge_mode(smx.FIELD_B), smx.FIELD_D: ctx.hodge_mode(smx.FIELD_D)}
+    sol = [f for f, m in ((smx.FIELD_H, mode[smx.FIELD_B]), (smx.FIELD_E, mode[smx.FIELD_D])) if m != 2]
+    sep = [f for f, m in ((smx.FIELD_H, mode[smx.FIELD_B]), (smx.FIELD_E, mode[smx.FIELD_D])) if m == 2]
+    both = [smx.FIELD_H, smx.FIELD_E]
+    fields = {"curl_primal": [smx.FIELD_B], "curl_dual": [smx.FIELD_D],
+              "hodge_block": [f for f in (smx.FIELD_B, smx.FIELD_D) if mode[f] == 0],
+              "hodge_quad": [f for f in (smx.FIELD_B, smx.FIELD_D) if mode[f] == 1],
+              "solve_x": sol, "solve_y": sol, "solve_z": sol,
+              "mass_solve_x": sep, "mass_solve_y": sep, "mass_solve_z": sep,
+              "curl_primal_f32": [smx.FIELD_B], "curl_dual_f32": [smx.FIELD_D],
+              "hodge_block_f32": [f for f in (smx.FIELD_B, smx.FIELD_D) if mode[f] == 0],
+              "line_f32_x": both, "line_f32_y": both, "line_f32_z": both}
+    kern = {}
+    for name, (ms, cnt) in ktimes.items():
+        if cnt == 0 or name not in fields:
+            continue
+        works = []
+        for f in fields[name]:
+            try:
+                works.append(ctx.kernel_work(name, f))
+            except smx.SmxError:
+                pass
+        if not works:
+            continue
+        fl = sum(w[0] for w in works) / len(works)
+        by = sum(w[1] for w in works) / len(works)
+        avg_ms = ms / cnt
+        kern[name] = {"launches": cnt, "total_ms": ms, "avg_us": 1e3 * avg_ms,
+                      "fp64_tflops": fl / (avg_ms * 1e-3) / 1e12, "gbs": by / (avg_ms * 1e-3) / 1e9,
+                      "flops_per_launch": fl, "bytes_per_launch": by}
+    total_k = sum(v["total_ms"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["total_ms"] / total_k if total_k else None
+    return kern
+
+
+def time_steps(ctx, state, dt, steps, flush, stream, world):
+    """K single steps, L2 flushed before each, CUDA events on the launching stream; (sum ms, launches)."""
+    import torch
+    d, b, e, h = state
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    launches0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_region")
+    for k in range(steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        ctx.step(d, b, e, h, dt, 1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    return sum(s.elapsed_time(t) for s, t in zip(starts, ends)), ctx.launch_count() - launches0
+
+
+def steady_and_kernels(ctx, smx, state, dt, steps, flush, stream):
+    """Steady state (K steps in one call) and per-kernel event times over K flushed single steps."""
+    import torch
+    d, b, e, h = state
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.step(d, b, e, h, dt, steps)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    for k in range(steps):
+        flush.fill_(float(k))
+        ctx.step(d, b, e, h, dt, 1)
+    kt = ctx.kernel_times()
+    ctx.set_timing(False)
+    return s0.elapsed_time(s1), kernel_table(ctx, smx, kt)
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2302_04979_gb300 import smx, synth
@@ -196,17 +277,17 @@ def run_ours(args, rank, world, local):
     ctx.set_stream(stream)
     ne, nh = ctx.N_e, ctx.N_h
     dof = ne + nh
-    d = torch.as_tensor(synth.uniform(SEED + 1 + 17 * rank, ne, -1.0, 1.0)).to(dev)
-    b = torch.zeros(nh, dtype=torch.float64, device=dev)
-    ctx.curl_primal(torch.as_tensor(synth.uniform(SEED + 2 + 17 * rank, ne, -1.0, 1.0)).to(dev), b, 1.0)
-    e = torch.empty(ne, dtype=torch.float64, device=dev)
-    h = torch.zeros(nh, dtype=torch.float64, device=dev)
-    ctx.hodge_star(smx.FIELD_D, d, e)
+    d0 = torch.as_tensor(synth.uniform(SEED + 1 + 17 * rank, ne, -1.0, 1.0)).to(dev)
+    b0 = torch.zeros(nh, dtype=torch.float64, device=dev)
+    ctx.curl_primal(torch.as_tensor(synth.uniform(SEED + 2 + 17 * rank, ne, -1.0, 1.0)).to(dev), b0, 1.0)
+    e0 = torch.empty(ne, dtype=torch.float64, device=dev)
+    ctx.hodge_star(smx.FIELD_D, d0, e0)
     dt = 0.5 * ctx.cfl(iters=400, tol=1e-8)
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device=dev)
+    state = (d0.clone(), b0.clone(), e0.clone(), torch.zeros(nh, dtype=torch.float64, device=dev))
 
     for _ in range(args.warmup):
-        ctx.step(d, b, e, h, dt, 1)
+        ctx.step(*state, dt, 1)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -220,48 +301,30 @@ def run_ours(args, rank, world, local):
     sampler.start()
     time.sleep(0.3)
 
-    # ---- timed region: K steps, L2 flushed before each, CUDA events on the launching stream
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches0 = ctx.launch_count()
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("timed_region")
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        starts[k].record(stream)
-        ctx.step(d, b, e, h, dt, 1)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    if world > 1:
-        dist.barrier()
-    launches = ctx.launch_count() - launches0
-    step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-    total_ms = reduce_max(sum(step_ms), world)
+    # ---- FP64 form: timed region
+    total_ms, launches = time_steps(ctx, state, dt, args.steps, flush, stream, world)
+    total_ms = reduce_max(total_ms, world)
     value = reduce_sum(dof * args.steps, world) / (total_ms * 1e-3)
+    steady_ms, kern = steady_and_kernels(ctx, smx, state, dt, args.steps, flush, stream)
+    steady_ms = reduce_max(steady_ms, world)
 
-    # ---- steady state: the same K steps back to back in one call (state stays in L2)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    ctx.step(d, b, e, h, dt, args.steps)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    steady_ms = reduce_max(s0.elapsed_time(s1), world)
-
-    # ---- per-kernel times (events around each launch), same flushed per-step pattern
-    ctx.set_timing(True)
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ctx.step(d, b, e, h, dt, 1)
-    ktimes = ctx.kernel_times()
-    ctx.set_timing(False)
+    # ---- mixed form on the same workload and protocol (FP32 operators, FP64 state)
+    mctx = smx.Context(P, NEL, eps=eps, mu=1.0, precision="mixed").bind(dev)
+    mctx.set_stream(stream)
+    mstate = (d0.clone(), b0.clone(), e0.clone(), torch.zeros(nh, dtype=torch.float64, device=dev))
+    for _ in range(args.warmup):
+        mctx.step(*mstate, dt, 1)
+    m_ms, m_launches = time_steps(mctx, mstate, dt, args.steps, flush, stream, world)
+    m_ms = reduce_max(m_ms, world)
+    m_steady, mkern = steady_and_kernels(mctx, smx, mstate, dt, args.steps, flush, stream)
+    m_steady = reduce_max(m_steady, world)
     clocks = sampler.stop()
 
     # ---- end to end through the host-buffer C call (copies inside the timed region)
-    hd = d.cpu().pin_memory()
-    hb = b.cpu().pin_memory()
-    he = e.cpu().pin_memory()
-    hh = h.cpu().pin_memory()
+    hd = state[0].cpu().pin_memory()
+    hb = state[1].cpu().pin_memory()
+    he = state[2].cpu().pin_memory()
+    hh = state[3].cpu().pin_memory()
     ctx.step_host(hd, hb, he, hh, dt, 1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -271,34 +334,16 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": 8 * (2 * ne + nh), "d2h_bytes_per_step": 8 * (2 * ne + 2 * nh),
            "call": "smx_step_host (pinned host d, b, e in; d, b, e, h out; nsteps=1 per call)"}
 
-    # ---- roofline of the dominant kernel (largest total time)
-    fields = {"curl_primal": [smx.FIELD_B], "curl_dual": [smx.FIELD_D], "hodge_block": [smx.FIELD_B, smx.FIELD_D],
-              "hodge_quad": [smx.FIELD_B, smx.FIELD_D], "solve_x": [smx.FIELD_H, smx.FIELD_E],
-              "solve_y": [smx.FIELD_H, smx.FIELD_E], "solve_z": [smx.FIELD_H, smx.FIELD_E]}
-    kern = {}
-    for name, (ms, cnt) in ktimes.items():
-        if cnt == 0 or name not in fields:
-            continue
-        works = []
-        for f in fields[name]:
-            try:
-                works.append(ctx.kernel_work(name, f))
-            except smx.SmxError:
-                pass
-        fl = sum(w[0] for w in works) / len(works)
-        by = sum(w[1] for w in works) / len(works)
-        avg_ms = ms / cnt
-        kern[name] = {"launches": cnt, "total_ms": ms, "avg_us": 1e3 * avg_ms,
-                      "fp64_tflops": fl / (avg_ms * 1e-3) / 1e12, "gbs": by / (avg_ms * 1e-3) / 1e9,
-                      "flops_per_launch": fl, "bytes_per_launch": by}
-    total_k = sum(v["total_ms"] for v in kern.values())
-    for v in kern.values():
-        v["share"] = v["total_ms"] / total_k if total_k else None
+    # ---- roofline of the dominant kernel: FP64 form is bound by the FP64 pipe
     dom = max(kern, key=lambda n: kern[n]["total_ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kern[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": kern[dom]["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+            "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json; "
+                           "our FMA probe measured 1.19)",
             "hbm_gbs": kern[dom]["gbs"]}
+    mdom = max(mkern, key=lambda n: mkern[n]["total_ms"])
+    mroof = {"kernel": mdom, "bound": "hbm", "achieved": mkern[mdom]["gbs"], "peak": HBM_PEAK_GBS, "unit": "GB/s",
+             "frac": mkern[mdom]["gbs"] / HBM_PEAK_GBS, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
     out = None
     if rank == 0:
@@ -309,7 +354,13 @@ def run_ours(args, rank, world, local):
                "roofline": roof, "kernels": kern,
                "steady_state": {"value": reduce_sum(dof * args.steps, world) / (steady_ms * 1e-3),
                                 "ms_per_step": steady_ms / args.steps,
-                                "note": "K steps in one smx_step call, no L2 flush (state L2-resident)"}}
+                                "note": "K steps in one smx_step call, no L2 flush (state L2-resident)"},
+               "mixed": {"value": reduce_sum(dof * args.steps, world) / (m_ms * 1e-3), "unit": UNIT,
+                         "ms_per_step": m_ms / args.steps, "dtype": "f32 operators (split coefficients), f64 state",
+                         "gpu_launches": m_launches, "roofline": mroof, "kernels": mkern,
+                         "speedup_vs_fp64": total_ms / m_ms,
+                         "steady_state": {"value": reduce_sum(dof * args.steps, world) / (m_steady * 1e-3),
+                                          "ms_per_step": m_steady / args.steps}}}
     return out
 
 

@@ -82,7 +82,20 @@ typedef struct {
     double geom_amplitude; /* SMX_GEOM_SINE_BUMP amplitude a; |a| < 1/(3 pi) keeps det J_F > 0 */
     smx_material eps;      /* permittivity: weights M~^2_{1/eps} (Eq. discrete2_hodge_eps) */
     smx_material mu;       /* permeability: weights M^2_{1/mu} (Eq. discrete2_hodge_mu) */
+    int precision;         /* SMX_FP64 or SMX_MIXED: arithmetic of smx_step / smx_step_host */
 } smx_params;
+
+/* ---- precision of the leapfrog step ----
+ * SMX_FP64: every operation in FP64.
+ * SMX_MIXED: the stepped state d, b and its updates stay FP64 (one FP64 FMA
+ * per coefficient per half step); the curl differences, the Hodge mass apply
+ * and the pairing sweeps run in FP32 with operator coefficients stored as
+ * FP32 (hi, lo) pairs (hi + lo = the FP64 value to about 2^-48), so only the
+ * data is rounded to FP32.  Supported for the identity map with constant or
+ * block material (SMX_EINVAL otherwise).  Only smx_step / smx_step_host
+ * change; every other call stays FP64. */
+#define SMX_FP64 0
+#define SMX_MIXED 1
 
 typedef struct smx_ctx smx_ctx;
 
@@ -183,9 +196,12 @@ int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
  * events on the context stream; smx_kernel_times synchronises, adds up the
  * bracketed durations per kernel class and clears them:
  *   0 curl_primal, 1 curl_dual, 2 hodge_block, 3 hodge_quad,
- *   4 solve along x, 5 solve along y, 6 solve along z, 7 reductions.
- * ms[8] receives milliseconds, counts[8] launches per class. */
-#define SMX_NCLASS 8
+ *   4 solve along x, 5 solve along y, 6 solve along z, 7 reductions,
+ *   8/9/10 fused mass + solve along x/y/z (separable Hodge star),
+ *   11 curl_primal and 12 curl_dual of the mixed step (FP32 differences),
+ *   13 FP32 block Hodge, 14/15/16 FP32 line passes along x/y/z, 17 casts.
+ * ms[SMX_NCLASS] receives milliseconds, counts[SMX_NCLASS] launches per class. */
+#define SMX_NCLASS 18
 int smx_launch_count(const smx_ctx* ctx, int64_t* n);
 int smx_set_timing(smx_ctx* ctx, int enable);
 int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);
@@ -237,8 +253,12 @@ int smx_hodge_star_noalloc(smx_ctx* ctx, int field, const double* x, double* out
  * stored L and U, so tests can compare it with the definition. */
 int smx_factor_matrix(const smx_ctx* ctx, int axis, int which, int64_t* n, double* dense_out);
 
-/* Which Hodge kernel a field uses: 0 = block Kronecker (identity map with
- * block-constant material), 1 = quadrature (curved map or pointwise material). */
+/* Which Hodge kernels a field uses: 0 = block-Kronecker mass apply (identity
+ * map, block-constant material) followed by the pairing sweeps; 1 = quadrature
+ * mass apply (curved map or pointwise material) followed by the sweeps; 2 =
+ * constant material on the identity map: the mass is one Kronecker product and
+ * the Hodge star runs as three fused mass + solve line passes (the plain mass
+ * apply still uses the block kernel). */
 int smx_hodge_mode(const smx_ctx* ctx, int field, int* mode);
 
 #ifdef __cplusplus

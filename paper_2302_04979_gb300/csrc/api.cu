@@ -25,6 +25,11 @@ namespace {
 
 struct HodgeHost {
     int mode = 0;  // 0 block Kronecker, 1 quadrature
+    // identity map and constant material: the mass is one Kronecker product of
+    // 1D masses, lmass[a][kind] (n x (2 deg + 1) band rows, material folded into axis x)
+    bool separable = false;
+    std::vector<double> lmass[3][4];
+    size_t o_lmass[3][4];
     // block mode
     int ntile[3] = {0, 0, 0};
     int max_nloc = 0;
@@ -79,6 +84,7 @@ struct smx_ctx {
     SolveArgs solve[2][3];  // [K1, Kt1][axis]
     HodgeBlockArgs hb[2];
     HodgeQuadArgs hq[2];
+    MassSolveArgs ms[2][3];  // separable Hodge star: [field][axis]
     double* scratch = nullptr;
     double* scratch2 = nullptr;
     double* state = nullptr;  // d, e (N_e each), b, h (N_h each) for smx_step_host
@@ -92,6 +98,14 @@ struct smx_ctx {
     std::vector<Timed> timed;
     double* partial = nullptr;
     double* dots = nullptr;
+    // mixed precision: FP32 (hi, lo) tables, FP32 intermediates e32, h32, y32
+    int precision = SMX_FP64;
+    size_t o_fac32[3][4][3];
+    size_t o_tmat32[2][3], o_lmass32[2][3][4];
+    size_t o_e32 = 0, o_h32 = 0, o_y32 = 0;
+    float *e32 = nullptr, *h32 = nullptr, *y32 = nullptr;
+    HodgeBlockF32Args hb32[2];
+    LineF32Args ln32[2][3];  // [field][axis]: plain pairing sweeps (block Hodge) or fused mass + solve (separable)
 };
 
 namespace {
@@ -212,6 +226,35 @@ int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
     return SMX_OK;
 }
 
+// Global univariate masses of every space kind as band rows (half-bandwidth =
+// the kind's degree), gamma folded into the x axis: M = gamma Mz (x) My (x) Mx.
+void build_separable(smx_ctx* C, int h, double gamma) {
+    HodgeHost& H = C->hodge[h];
+    H.separable = true;
+    for (int a = 0; a < 3; ++a) {
+        const int p = C->p[a], nel = C->nel[a];
+        for (int kind = 0; kind < 4; ++kind) {
+            const int d = kind_degree(kind, p), off = kind_offset(kind), dim = kind_dim(kind, p, nel);
+            const int W = 2 * d + 1;
+            std::vector<double>& R = H.lmass[a][kind];
+            R.assign((size_t)dim * W, 0.0);
+            const double scale = a == 0 ? gamma : 1.0;
+            for (int e = 0; e < nel; ++e) {
+                const std::vector<double> Me = element_mass(kind, p, nel, e);
+                for (int r = 0; r <= d; ++r) {
+                    const int i = e + r + off;
+                    if (i < 0 || i >= dim) continue;
+                    for (int s = 0; s <= d; ++s) {
+                        const int j = e + s + off;
+                        if (j < 0 || j >= dim) continue;
+                        R[(size_t)i * W + (j - i + d)] += scale * Me[r * (d + 1) + s];
+                    }
+                }
+            }
+        }
+    }
+}
+
 int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
     HodgeHost& H = C->hodge[h];
     std::vector<double> gx[3], gw[3];
@@ -284,6 +327,17 @@ int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
         H.G[5 * Q + qi] = s * JtJ[2][2];
     }
     return SMX_OK;
+}
+
+// FP64 values as FP32 (hi, lo) pairs: hi = fl32(v), lo = fl32(v - hi); hi + lo = v to about 2^-48 relative.
+std::vector<float> split_pairs(const std::vector<double>& v) {
+    std::vector<float> out(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float hi = static_cast<float>(v[i]);
+        out[2 * i] = hi;
+        out[2 * i + 1] = static_cast<float>(v[i] - static_cast<double>(hi));
+    }
+    return out;
 }
 
 std::vector<double> transpose(const std::vector<double>& A, int n) {
@@ -364,6 +418,70 @@ int solve_impl(smx_ctx* C, int which, const double* y, double* x) {
 
 int dot_impl(smx_ctx* C, const double* x, const double* y, long long n, int slot) {
     return run(C, 7, 2, [&] { return launch_dot(x, y, n, C->partial, C->dots + slot, C->stream); });
+}
+
+// ---- mixed precision: FP32 operators on the FP64 state
+// FP32 Hodge star from the FP64 2-form x into out (h = 0: h32 = K~_1^{-1} M^2 b;
+// h = 1: e32 = K_1^{-1} M~^2 d), same algorithms as the FP64 path.
+int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out) {
+    int st;
+    if (C->hodge[h].separable) {
+        st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, true, x, nullptr, out, C->stream); });
+        if (st) return st;
+        st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, true, nullptr, out, out, C->stream); });
+        if (st) return st;
+        return run(C, 16, 1,
+                   [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, true, nullptr, out, out, C->stream); });
+    }
+    const long long n = C->fld[kFieldOfHodge[h]].total;
+    CK(cudaMemsetAsync(C->y32, 0, (size_t)n * sizeof(float), C->stream));
+    st = run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->y32, C->stream); });
+    if (st) return st;
+    st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, false, nullptr, C->y32, out, C->stream); });
+    if (st) return st;
+    st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, false, nullptr, out, out, C->stream); });
+    if (st) return st;
+    return run(C, 16, 1, [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, false, nullptr, out, out, C->stream); });
+}
+
+int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp, double dt,
+               int nsteps) {
+    const DevField &FE = C->fld[SMX_FIELD_E], &FB = C->fld[SMX_FIELD_B], &FH = C->fld[SMX_FIELD_H],
+                   &FD = C->fld[SMX_FIELD_D];
+    int st = run(C, 17, 1, [&] { return launch_cast_d2f(e, C->e32, C->N_e, C->stream); });
+    if (st) return st;
+    st = run(C, 11, 1, [&] { return launch_curl_f32(false, FE, FB, C->e32, b, -0.5 * dt, nullptr, nullptr, 0, 0.0, C->stream); });
+    if (st) return st;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((st = hodge_star_f32_impl(C, 0, b, C->h32))) return st;
+        st = run(C, 12, 1, [&] { return launch_curl_f32(true, FH, FD, C->h32, d, dt, jhat, amp, n, 0.0, C->stream); });
+        if (st) return st;
+        if ((st = hodge_star_f32_impl(C, 1, d, C->e32))) return st;
+        const double alpha = (n + 1 == nsteps) ? -0.5 * dt : -dt;
+        st = run(C, 11, 1, [&] { return launch_curl_f32(false, FE, FB, C->e32, b, alpha, nullptr, nullptr, 0, 0.0, C->stream); });
+        if (st) return st;
+    }
+    st = run(C, 17, 1, [&] { return launch_cast_f2d(C->e32, e, C->N_e, C->stream); });
+    if (st) return st;
+    return run(C, 17, 1, [&] { return launch_cast_f2d(C->h32, h, C->N_h, C->stream); });
+}
+
+// One discrete Hodge star of scheme 2 (Eq. discrete2_hodge_mu for h = 0,
+// Eq. discrete2_hodge_eps for h = 1): three fused mass+solve line passes when
+// the field's mass is a single Kronecker product, else mass apply into the
+// scratch vector followed by the three pairing sweeps.
+int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out) {
+    const int which = h == 0 ? 1 : 0;
+    if (C->hodge[h].separable) {
+        int st = run(C, 8, 1, [&] { return launch_mass_solve_axis(C->ms[h][0], C->p[0] - 1, x, out, C->stream); });
+        if (st) return st;
+        st = run(C, 9, 1, [&] { return launch_mass_solve_axis(C->ms[h][1], C->p[1] - 1, out, out, C->stream); });
+        if (st) return st;
+        return run(C, 10, 1, [&] { return launch_mass_solve_axis(C->ms[h][2], C->p[2] - 1, out, out, C->stream); });
+    }
+    const int st = hodge_apply_impl(C, h, x, C->scratch);
+    if (st) return st;
+    return solve_impl(C, which, C->scratch, out);
 }
 
 }  // namespace
@@ -452,6 +570,16 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                 delete C;
                 return st;
             }
+            if (block && mats[h]->kind == SMX_MAT_CONST) build_separable(C, h, 1.0 / mats[h]->value);
+        }
+        if (P->precision != SMX_FP64 && P->precision != SMX_MIXED) {
+            delete C;
+            return SMX_EINVAL;
+        }
+        C->precision = P->precision;
+        if (C->precision == SMX_MIXED && (C->hodge[0].mode != 0 || C->hodge[1].mode != 0)) {
+            delete C;  // the FP32 operators cover the block-Kronecker Hodge only
+            return SMX_EINVAL;
         }
         // pack the tables
         for (int a = 0; a < 3; ++a)
@@ -469,11 +597,31 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                     H.o_tmat[a] = C->blob.add(H.tmat[a]);
                 }
                 H.o_gamma = C->blob.add(H.gamma);
+                if (H.separable)
+                    for (int a = 0; a < 3; ++a)
+                        for (int kind = 0; kind < 4; ++kind) H.o_lmass[a][kind] = C->blob.add(H.lmass[a][kind]);
             } else {
                 for (int a = 0; a < 3; ++a) H.o_bval[a] = C->blob.add(H.bval[a]);
                 H.o_G = C->blob.add(H.G);
                 H.G.clear();
                 H.G.shrink_to_fit();
+            }
+        }
+        if (C->precision == SMX_MIXED) {
+            // FP32 (hi, lo) copies of every operator table of the mixed step
+            for (int a = 0; a < 3; ++a)
+                for (int w = 0; w < 4; ++w) {
+                    C->o_fac32[a][w][0] = C->blob.add(split_pairs(C->fac[a][w].L));
+                    C->o_fac32[a][w][1] = C->blob.add(split_pairs(C->fac[a][w].U));
+                    C->o_fac32[a][w][2] = C->blob.add(split_pairs(C->fac[a][w].dinv));
+                }
+            for (int h = 0; h < 2; ++h) {
+                HodgeHost& H = C->hodge[h];
+                for (int a = 0; a < 3; ++a) C->o_tmat32[h][a] = C->blob.add(split_pairs(H.tmat[a]));
+                if (H.separable)
+                    for (int a = 0; a < 3; ++a)
+                        for (int kind = 0; kind < 4; ++kind)
+                            C->o_lmass32[h][a][kind] = C->blob.add(split_pairs(H.lmass[a][kind]));
             }
         }
         C->tables_bytes = (C->blob.bytes.size() + 255) & ~size_t(255);
@@ -484,6 +632,13 @@ int smx_create(const smx_params* P, smx_ctx** out) {
         C->o_dots = C->o_partial + ((kDotBlocks * sizeof(double) + 255) & ~size_t(255));
         C->o_state = C->o_dots + 256;
         C->total_bytes = C->o_state + ((2 * (size_t)(C->N_e + C->N_h) * sizeof(double) + 255) & ~size_t(255));
+        if (C->precision == SMX_MIXED) {
+            auto f32 = [](long long n) { return ((size_t)n * sizeof(float) + 255) & ~size_t(255); };
+            C->o_e32 = C->total_bytes;
+            C->o_h32 = C->o_e32 + f32(C->N_e);
+            C->o_y32 = C->o_h32 + f32(C->N_h);
+            C->total_bytes = C->o_y32 + f32((long long)nmax);
+        }
     } catch (const std::bad_alloc&) {
         delete C;
         return SMX_ENOMEM;
@@ -574,6 +729,20 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                 }
             A.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
             A.max_nloc = H.max_nloc;
+            if (H.separable) {
+                const int which = h == 0 ? 1 : 0;  // M^2 pairs with K~_1, M~^2 with K_1
+                for (int a = 0; a < 3; ++a) {
+                    MassSolveArgs& M = C->ms[h][a];
+                    M.field = C->fld[fld];
+                    M.axis = a;
+                    for (int c = 0; c < 3; ++c) {
+                        const int kind = kFieldKinds[fld][c][a];
+                        M.f[c] = C->solve[which][a].f[c];
+                        M.mass[c] = reinterpret_cast<const double*>(ws + H.o_lmass[a][kind]);
+                        M.deg[c] = kind_degree(kind, C->p[a]);
+                    }
+                }
+            }
         } else {
             HodgeQuadArgs& A = C->hq[h];
             A.field = C->fld[fld];
@@ -591,6 +760,44 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                 }
             A.G = reinterpret_cast<const double*>(ws + H.o_G);
             A.Qtot = H.Qtot;
+        }
+    }
+    if (C->precision == SMX_MIXED) {
+        C->e32 = reinterpret_cast<float*>(ws + C->o_e32);
+        C->h32 = reinterpret_cast<float*>(ws + C->o_h32);
+        C->y32 = reinterpret_cast<float*>(ws + C->o_y32);
+        for (int h = 0; h < 2; ++h) {
+            const HodgeHost& H = C->hodge[h];
+            const int fld = kFieldOfHodge[h];
+            const int which = h == 0 ? 1 : 0;  // M^2 pairs with K~_1, M~^2 with K_1
+            HodgeBlockF32Args& B = C->hb32[h];
+            B.field = C->fld[fld];
+            for (int a = 0; a < 3; ++a) {
+                B.ntile[a] = H.ntile[a];
+                B.tf0[a] = reinterpret_cast<const int*>(ws + H.o_tf0[a]);
+                B.tlen[a] = reinterpret_cast<const int*>(ws + H.o_tlen[a]);
+                B.tmat[a] = reinterpret_cast<const float2*>(ws + C->o_tmat32[h][a]);
+            }
+            for (int c = 0; c < 3; ++c)
+                for (int a = 0; a < 3; ++a) {
+                    B.kinds[c][a] = kFieldKinds[fld][c][a];
+                    B.deg[c][a] = kind_degree(B.kinds[c][a], C->p[a]);
+                }
+            B.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
+            B.max_nloc = H.max_nloc;
+            for (int a = 0; a < 3; ++a) {
+                LineF32Args& Lg = C->ln32[h][a];
+                Lg.field = C->fld[fld];
+                Lg.axis = a;
+                for (int c = 0; c < 3; ++c) {
+                    const int w = factor_index(which, c, a), kind = kFieldKinds[fld][c][a];
+                    Lg.L[c] = reinterpret_cast<const float2*>(ws + C->o_fac32[a][w][0]);
+                    Lg.U[c] = reinterpret_cast<const float2*>(ws + C->o_fac32[a][w][1]);
+                    Lg.dinv[c] = reinterpret_cast<const float2*>(ws + C->o_fac32[a][w][2]);
+                    Lg.mass[c] = H.separable ? reinterpret_cast<const float2*>(ws + C->o_lmass32[h][a][kind]) : nullptr;
+                    Lg.deg[c] = kind_degree(kind, C->p[a]);
+                }
+            }
         }
     }
     return SMX_OK;
@@ -632,10 +839,7 @@ int smx_hodge_star(smx_ctx* C, int field, const double* x, double* out) {
     NEED_WS(C);
     if (!x || !out) return SMX_EINVAL;
     if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
-    const int h = field == SMX_FIELD_B ? 0 : 1;
-    int st = hodge_apply_impl(C, h, x, C->scratch);
-    if (st) return st;
-    return solve_impl(C, h == 0 ? 1 : 0, C->scratch, out);
+    return hodge_star_impl(C, field == SMX_FIELD_B ? 0 : 1, x, out);
 }
 
 int smx_step(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp,
@@ -644,15 +848,14 @@ int smx_step(smx_ctx* C, double* d, double* b, double* e, double* h, const doubl
     if (!d || !b || !e || !h || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return SMX_EINVAL;
     if (jhat && !amp) return SMX_EINVAL;
     if (nsteps == 0) return SMX_OK;
+    if (C->precision == SMX_MIXED) return step_mixed(C, d, b, e, h, jhat, amp, dt, nsteps);
     // kick-drift-kick with the inner half kicks of b merged
     int st = curl_primal_impl(C, e, b, -0.5 * dt);
     if (st) return st;
     for (int n = 0; n < nsteps; ++n) {
-        if ((st = hodge_apply_impl(C, 0, b, C->scratch))) return st;  // M^2_{1/mu} b
-        if ((st = solve_impl(C, 1, C->scratch, h))) return st;        // h = K~_1^{-1} (.)
+        if ((st = hodge_star_impl(C, 0, b, h))) return st;  // h = K~_1^{-1} M^2_{1/mu} b
         if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0))) return st;
-        if ((st = hodge_apply_impl(C, 1, d, C->scratch))) return st;  // M~^2_{1/eps} d
-        if ((st = solve_impl(C, 0, C->scratch, e))) return st;        // e = K_1^{-1} (.)
+        if ((st = hodge_star_impl(C, 1, d, e))) return st;  // e = K_1^{-1} M~^2_{1/eps} d
         if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt))) return st;
     }
     return SMX_OK;
@@ -808,6 +1011,52 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
             *bytes = 16.0 * N;
             return SMX_OK;
         }
+        case 8:
+        case 9:
+        case 10: {  // fused mass + solve sweep: 2 (2 deg + 1) + 4 KL + 1 flops per entry
+            const int h = bside ? 0 : 1;
+            if (!C->hodge[h].separable) return SMX_EINVAL;
+            const int a = cls - 8, kl = C->p[a] - 1, fld = kFieldOfHodge[h];
+            double f = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const DevComp& K = C->fld[fld].c[c];
+                const double nc = (double)K.n[0] * K.n[1] * K.n[2];
+                const int d = kind_degree(kFieldKinds[fld][c][a], C->p[a]);
+                f += nc * (2.0 * (2 * d + 1) + 4.0 * kl + 1.0);
+            }
+            *flops = f;
+            *bytes = 16.0 * N;
+            return SMX_OK;
+        }
+        // mixed step: the method's flops as above (split products not counted twice);
+        // bytes with FP32 intermediates and the FP64 state
+        case 11:
+        case 12: {
+            const int st = smx_kernel_work(C, cls - 11, field, flops, bytes);
+            if (st) return st;
+            *bytes = cls == 11 ? 4.0 * Ne + 16.0 * Nh : 4.0 * Nh + 16.0 * Ne;
+            return SMX_OK;
+        }
+        case 13: {
+            const int st = smx_kernel_work(C, 2, field, flops, bytes);
+            if (st) return st;
+            *bytes = 12.0 * N;
+            return SMX_OK;
+        }
+        case 14:
+        case 15:
+        case 16: {
+            const int h = bside ? 0 : 1, a = cls - 14;
+            const bool sep = C->hodge[h].separable;
+            const int st = smx_kernel_work(C, sep ? 8 + a : 4 + a, field, flops, bytes);
+            if (st) return st;
+            *bytes = (sep && a == 0 ? 12.0 : 8.0) * N;
+            return SMX_OK;
+        }
+        case 17:
+            *flops = 0.0;
+            *bytes = 12.0 * N;
+            return SMX_OK;
         default:
             return SMX_EINVAL;
     }
@@ -883,7 +1132,8 @@ int smx_factor_matrix(const smx_ctx* C, int axis, int which, int64_t* n, double*
 
 int smx_hodge_mode(const smx_ctx* C, int field, int* mode) {
     if (!C || !mode || (field != SMX_FIELD_B && field != SMX_FIELD_D)) return SMX_EINVAL;
-    *mode = C->hodge[field == SMX_FIELD_B ? 0 : 1].mode;
+    const HodgeHost& H = C->hodge[field == SMX_FIELD_B ? 0 : 1];
+    *mode = H.separable ? 2 : H.mode;
     return SMX_OK;
 }
 

@@ -39,6 +39,17 @@ struct SolveArgs {
     int axis;
 };
 
+// Fused line pass of a separable Hodge star: x = A^{-1} (M y) along one axis,
+// M the univariate mass of the component's space along that axis (banded,
+// half-bandwidth = the space's degree), A the pairing factor.
+struct MassSolveArgs {
+    DevField field;
+    DevFactor f[3];
+    const double* mass[3];   // per component: n x (2 deg + 1) band rows, zero padded
+    int deg[3];              // per component: mass half-bandwidth
+    int axis;
+};
+
 // Block-Kronecker Hodge apply: M = sum_t gamma_t (Mz_t (x) My_t (x) Mx_t).
 struct HodgeBlockArgs {
     DevField field;
@@ -66,6 +77,39 @@ struct HodgeQuadArgs {
     int Qn[3];               // quadrature points per axis
 };
 
+// ---- FP32 operators of the mixed-precision step (kernels_f32.cu): split (hi, lo) coefficients
+struct HodgeBlockF32Args {
+    DevField field;
+    int ntile[3];
+    int kinds[3][3];
+    int deg[3][3];
+    const int* tf0[3];
+    const int* tlen[3];
+    const float2* tmat[3];
+    const double* gamma;
+    int max_nloc;
+};
+
+struct LineF32Args {
+    DevField field;
+    const float2* L[3];     // per component: n x KL
+    const float2* U[3];     // per component: n x KL (divided by the diagonal)
+    const float2* dinv[3];  // per component: n
+    const float2* mass[3];  // per component: n x (2 deg + 1) band rows (fused separable star only)
+    int deg[3];
+    int axis;
+};
+
+cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
+                            double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
+                            cudaStream_t s);
+cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
+cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
+cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, float* y,
+                                   cudaStream_t s);
+cudaError_t launch_line_f32(const LineF32Args& a, int kl, bool mass, const double* in64, const float* in32, float* out,
+                            cudaStream_t s);
+
 // ---- launchers (kernels.cu); all enqueue on `s` and return cudaGetLastError()
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b,
                                double alpha, cudaStream_t s);
@@ -75,6 +119,7 @@ cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double*
 cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_solve_axis(const SolveArgs& a, int kl, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_mass_solve_axis(const MassSolveArgs& a, int kl, const double* in, double* out, cudaStream_t s);
 // partial[b] of sum_i x_i y_i over kDotBlocks CTAs, then out[0] = total (device)
 cudaError_t launch_dot(const double* x, const double* y, long long n, double* partial, double* out,
                        cudaStream_t s);

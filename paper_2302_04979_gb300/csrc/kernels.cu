@@ -330,6 +330,49 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Line recurrences.  The FP64 pipe of GB300 has a latency of about 64 cycles,
+// so each recurrence keeps exactly one FMA per entry on its dependency chain
+// (the one with the previous value), reads and writes distinct arrays so the
+// compiler can hoist the next entries' loads above the current store, and is
+// unrolled so off-chain FMAs of later entries overlap the chain.
+template <int KL>
+__device__ __forceinline__ void lu_forward(const double* __restrict__ y, double* __restrict__ z, int s, int n,
+                                           const double* __restrict__ fL) {
+    double w[KL];
+#pragma unroll
+    for (int k = 0; k < KL; ++k) w[k] = 0.0;
+#pragma unroll 4
+    for (int m = 0; m < n; ++m) {  // z_m = y_m - sum_k L(m, m-k) z_{m-k}
+        double u = y[m * s];
+#pragma unroll
+        for (int k = KL - 1; k >= 1; --k) u = fma(-fL[m * KL + k], w[k], u);
+        const double zm = fma(-fL[m * KL], w[0], u);
+#pragma unroll
+        for (int k = KL - 1; k > 0; --k) w[k] = w[k - 1];
+        w[0] = zm;
+        z[m * s] = zm;
+    }
+}
+
+template <int KL>
+__device__ __forceinline__ void lu_backward(const double* __restrict__ z, double* __restrict__ x, int s, int n,
+                                            const double* __restrict__ fU, const double* __restrict__ fD) {
+    double w[KL];
+#pragma unroll
+    for (int k = 0; k < KL; ++k) w[k] = 0.0;
+#pragma unroll 4
+    for (int m = n - 1; m >= 0; --m) {  // x_m = z_m / U(m,m) - sum_k U'(m, m+k) x_{m+k}
+        double u = z[m * s] * fD[m];
+#pragma unroll
+        for (int k = KL - 1; k >= 1; --k) u = fma(-fU[m * KL + k], w[k], u);
+        const double xm = fma(-fU[m * KL], w[0], u);
+#pragma unroll
+        for (int k = KL - 1; k > 0; --k) w[k] = w[k - 1];
+        w[0] = xm;
+        x[m * s] = xm;
+    }
+}
+
 template <int KL>
 __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, const double* __restrict__ in,
                                                                  double* __restrict__ out) {
@@ -375,32 +418,9 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
     if (tid < nl) {
         const int sL = axis == 0 ? ldl : 1;
         const int sM = axis == 0 ? 1 : kSolveLines;
-        double* row = S + tid * sL;
-        double w[KL];
-#pragma unroll
-        for (int k = 0; k < KL; ++k) w[k] = 0.0;
-#pragma unroll 2
-        for (int m = 0; m < n; ++m) {  // forward, unit lower L
-            double z = row[m * sM];
-#pragma unroll
-            for (int k = KL - 1; k >= 0; --k) z = fma(-fL[m * KL + k], w[k], z);
-#pragma unroll
-            for (int k = KL - 1; k > 0; --k) w[k] = w[k - 1];
-            w[0] = z;
-            row[m * sM] = z;
-        }
-#pragma unroll
-        for (int k = 0; k < KL; ++k) w[k] = 0.0;
-#pragma unroll 2
-        for (int m = n - 1; m >= 0; --m) {  // backward, U scaled by its diagonal
-            double v = row[m * sM] * fD[m];
-#pragma unroll
-            for (int k = KL - 1; k >= 0; --k) v = fma(-fU[m * KL + k], w[k], v);
-#pragma unroll
-            for (int k = KL - 1; k > 0; --k) w[k] = w[k - 1];
-            w[0] = v;
-            row[m * sM] = v;
-        }
+        double* S2 = S + kSolveLines * ldl;
+        lu_forward<KL>(S + tid * sL, S2 + tid * sL, sM, n, fL);
+        lu_backward<KL>(S2 + tid * sL, S + tid * sL, sM, n, fU, fD);
     }
     __syncthreads();
     double* dst = out + C.off;
@@ -429,7 +449,7 @@ static cudaError_t launch_solve_t(const SolveArgs& a, const double* in, double* 
         if (n > 0) maxlines = std::max(maxlines, nc / n);
         maxn = std::max(maxn, n);
     }
-    const size_t smem = ((size_t)(2 * KL + 1) * maxn + (size_t)(maxn | 1) * kSolveLines + 8) * sizeof(double);
+    const size_t smem = ((size_t)(2 * KL + 1) * maxn + 2 * (size_t)(maxn | 1) * kSolveLines + 8) * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(solve_axis_kernel<KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -447,6 +467,168 @@ cudaError_t launch_solve_axis(const SolveArgs& a, int kl, const double* in, doub
         case 3: return launch_solve_t<3>(a, in, out, s);
         case 4: return launch_solve_t<4>(a, in, out, s);
         case 5: return launch_solve_t<5>(a, in, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------ separable Hodge star
+// Identity map and constant material: M = gamma (M_z (x) M_y (x) M_x) and the
+// pairing block is C = A_z (x) A_y (x) A_x (Eq. tensor_K / tensor_Ktilde), so
+// the Hodge star C^{-1} M = (A_z^{-1} M_z) (x) (A_y^{-1} M_y) (x) (A_x^{-1} M_x)
+// (gamma folded into one axis' mass).  Each pass applies the banded mass and
+// then the banded LU solve to every line of one axis, in shared memory.
+// t_m = sum_q M(m, m-D+q) y_{m-D+q} on a line padded with D zeros at both ends.
+template <int D>
+__device__ __forceinline__ void mass_line(const double* __restrict__ ypad, double* __restrict__ t, int s, int n,
+                                          const double* __restrict__ fM) {
+    constexpr int W = 2 * D + 1;
+    int m = 0;
+    for (; m + 3 < n; m += 4) {  // four independent accumulations in flight
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            a0 = fma(fM[m * W + q], ypad[(m + q) * s], a0);
+            a1 = fma(fM[(m + 1) * W + q], ypad[(m + 1 + q) * s], a1);
+            a2 = fma(fM[(m + 2) * W + q], ypad[(m + 2 + q) * s], a2);
+            a3 = fma(fM[(m + 3) * W + q], ypad[(m + 3 + q) * s], a3);
+        }
+        t[m * s] = a0;
+        t[(m + 1) * s] = a1;
+        t[(m + 2) * s] = a2;
+        t[(m + 3) * s] = a3;
+    }
+    for (; m < n; ++m) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc = fma(fM[m * W + q], ypad[(m + q) * s], acc);
+        t[m * s] = acc;
+    }
+}
+
+template <int KL, int D>
+__device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, const double* __restrict__ in,
+                                                double* __restrict__ out, double* sm) {
+    const int c = blockIdx.y;
+    const DevComp C = A.field.c[c];
+    const int axis = A.axis;
+    const int n = C.n[axis];
+    const int nlines = C.n[0] * C.n[1] * C.n[2] / n;
+    const int l0 = blockIdx.x * kSolveLines;
+    if (l0 >= nlines) return;
+    const int nl = min(kSolveLines, nlines - l0);
+    const DevFactor F = A.f[c];
+    constexpr int W = 2 * D + 1;
+    double* fL = sm;
+    double* fU = fL + n * KL;
+    double* fD = fU + n * KL;
+    double* fM = fD + n;              // n x W mass band rows
+    double* Sin = fM + n * W;         // input lines, padded with D zeros at both ends
+    const int np = n + 2 * D;
+    const int ldin = np | 1, ldout = n | 1;
+    double* Sout = Sin + kSolveLines * ldin;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const double* Mg = A.mass[c];
+    for (int t = tid; t < n * KL; t += nt) {
+        cp_async8(fL + t, F.L + t);
+        cp_async8(fU + t, F.U + t);
+    }
+    for (int t = tid; t < n; t += nt) cp_async8(fD + t, F.dinv + t);
+    for (int t = tid; t < n * W; t += nt) cp_async8(fM + t, Mg + t);
+    // x lines: [line][m + D] (leading dimension ldin); y/z lines: [m + D][line]
+    const int sL = axis == 0 ? ldin : 1;
+    const int sM = axis == 0 ? 1 : kSolveLines;
+    if constexpr (D > 0) {
+        for (int t = tid; t < kSolveLines * D; t += nt) {  // zero pads
+            const int line = t / D, q = t - line * D;
+            Sin[line * sL + q * sM] = 0.0;
+            Sin[line * sL + (n + D + q) * sM] = 0.0;
+        }
+    }
+    const int nx = C.n[0], nxy = C.n[0] * C.n[1];
+    const double* src = in + C.off;
+    if (axis == 0) {
+        const double* chunk = src + (long long)l0 * n;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int line = g / n, m = g - line * n;
+            cp_async8(Sin + line * ldin + D + m, chunk + g);
+        }
+    } else if (tid < nl) {
+        const int l = l0 + tid;
+        const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        const int stride = axis == 1 ? nx : nxy;
+        for (int m = 0; m < n; ++m) cp_async8(Sin + (D + m) * kSolveLines + tid, src + base + m * stride);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int oL = axis == 0 ? ldout : 1;
+    if (tid < nl) {
+        // t = M y: independent banded dot products, no recurrence
+        mass_line<D>(Sin + tid * sL, Sout + tid * oL, sM, n, fM);
+        // forward t -> z (z reuses the input line), backward z -> x
+        lu_forward<KL>(Sout + tid * oL, Sin + tid * sL, sM, n, fL);
+        lu_backward<KL>(Sin + tid * sL, Sout + tid * oL, sM, n, fU, fD);
+    }
+    __syncthreads();
+    double* dst = out + C.off;
+    if (axis == 0) {
+        double* chunk = dst + (long long)l0 * n;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int line = g / n, m = g - line * n;
+            chunk[g] = Sout[line * ldout + m];
+        }
+    } else if (tid < nl) {
+        const int l = l0 + tid;
+        const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        const int stride = axis == 1 ? nx : nxy;
+#pragma unroll 4
+        for (int m = 0; m < n; ++m) dst[base + m * stride] = Sout[m * kSolveLines + tid];
+    }
+}
+
+template <int KL>
+__global__ void __launch_bounds__(kSolveLines) mass_solve_axis_kernel(MassSolveArgs A, const double* __restrict__ in,
+                                                                      double* __restrict__ out) {
+    extern __shared__ double sm[];
+    const int d = A.deg[blockIdx.y];
+    if (d == KL - 1) {
+        if constexpr (KL >= 1) mass_solve_body<KL, (KL >= 1 ? KL - 1 : 0)>(A, in, out, sm);
+    } else if (d == KL) {
+        mass_solve_body<KL, KL>(A, in, out, sm);
+    } else {
+        mass_solve_body<KL, KL + 1>(A, in, out, sm);
+    }
+}
+
+template <int KL>
+static cudaError_t launch_mass_solve_t(const MassSolveArgs& a, const double* in, double* out, cudaStream_t s) {
+    long long maxlines = 0;
+    int maxn = 0;
+    for (int c = 0; c < 3; ++c) {
+        const long long nc = (long long)a.field.c[c].n[0] * a.field.c[c].n[1] * a.field.c[c].n[2];
+        const int n = a.field.c[c].n[a.axis];
+        if (n > 0) maxlines = std::max(maxlines, nc / n);
+        maxn = std::max(maxn, n);
+    }
+    const int D = KL + 1, W = 2 * D + 1;
+    const size_t smem = ((size_t)(2 * KL + 1 + W) * maxn + (size_t)((maxn + 2 * D) | 1) * kSolveLines +
+                         (size_t)(maxn | 1) * kSolveLines + 8) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mass_solve_axis_kernel<KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr = true;
+    }
+    const long long nb = (maxlines + kSolveLines - 1) / kSolveLines;
+    if (nb > 0) mass_solve_axis_kernel<KL><<<dim3((unsigned)nb, 3), kSolveLines, smem, s>>>(a, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_solve_axis(const MassSolveArgs& a, int kl, const double* in, double* out, cudaStream_t s) {
+    switch (kl) {
+        case 1: return launch_mass_solve_t<1>(a, in, out, s);
+        case 2: return launch_mass_solve_t<2>(a, in, out, s);
+        case 3: return launch_mass_solve_t<3>(a, in, out, s);
+        case 4: return launch_mass_solve_t<4>(a, in, out, s);
+        case 5: return launch_mass_solve_t<5>(a, in, out, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -33,7 +33,8 @@ class Material(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int * 3), ("nel", ctypes.c_int * 3), ("geometry", ctypes.c_int),
-                ("geom_amplitude", ctypes.c_double), ("eps", Material), ("mu", Material)]
+                ("geom_amplitude", ctypes.c_double), ("eps", Material), ("mu", Material),
+                ("precision", ctypes.c_int)]
 
 
 class SmxError(RuntimeError):
@@ -75,9 +76,11 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)],
 }
 
-NCLASS = 8
+NCLASS = 18
 KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
-                  "reduction")
+                  "reduction", "mass_solve_x", "mass_solve_y", "mass_solve_z",
+                  "curl_primal_f32", "curl_dual_f32", "hodge_block_f32", "line_f32_x", "line_f32_y", "line_f32_z",
+                  "cast")
 
 
 def _lib():
@@ -140,7 +143,10 @@ def material(spec):
     return m, keep
 
 
-def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0):
+FP64, MIXED = 0, 1
+
+
+def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64"):
     P = Params()
     p = np.broadcast_to(np.asarray(p, dtype=int), (3,))
     nel = np.broadcast_to(np.asarray(nel, dtype=int), (3,))
@@ -150,15 +156,16 @@ def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0):
     P.geom_amplitude = float(amplitude)
     P.eps, k1 = material(eps)
     P.mu, k2 = material(mu)
+    P.precision = {"fp64": FP64, "mixed": MIXED}[precision]
     return P, k1 + k2
 
 
 class Context:
     """Owns an smx_ctx; the device workspace is a torch tensor bound by ``bind``."""
 
-    def __init__(self, p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0):
+    def __init__(self, p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64"):
         lib = _lib()
-        P, keep = make_params(p, nel, geometry, amplitude, eps, mu)
+        P, keep = make_params(p, nel, geometry, amplitude, eps, mu, precision)
         h = ctypes.c_void_p()
         _check(lib.smx_create(ctypes.byref(P), ctypes.byref(h)), "smx_create")
         del keep

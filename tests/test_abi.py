@@ -56,12 +56,12 @@ def test_pairing_factors_match_oracle(smx, p, nel):
 
 
 def test_hodge_mode_selection(smx):
-    assert smx.Context(3, 4).hodge_mode(smx.FIELD_D) == 0
+    assert smx.Context(3, 4).hodge_mode(smx.FIELD_D) == 2          # constant: separable Kronecker star
     assert smx.Context(3, 8, eps=("blocks", np.ones((2, 2, 2)))).hodge_mode(smx.FIELD_D) == 0
     ctx = smx.Context(3, 4, geometry="sine_bump")
     assert ctx.hodge_mode(smx.FIELD_D) == 1 and ctx.hodge_mode(smx.FIELD_B) == 1
     ctx = smx.Context(3, 4, eps=lambda x, y, z: 1.0 + x)
-    assert ctx.hodge_mode(smx.FIELD_D) == 1 and ctx.hodge_mode(smx.FIELD_B) == 0
+    assert ctx.hodge_mode(smx.FIELD_D) == 1 and ctx.hodge_mode(smx.FIELD_B) == 2
 
 
 def test_argument_errors(smx):

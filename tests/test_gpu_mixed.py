@@ -1,0 +1,95 @@
+"""Mixed-precision leapfrog (FP32 operators, FP64 state) against the FP64 oracle.
+
+The contract for this form is a relative L2 error of at most 1e-5 per field
+against the FP64 oracle after the stated step count, with the drift of the
+conserved energy W stated.  The errors measured here are printed (pytest -s)
+and asserted against that bound.
+"""
+import numpy as np
+import pytest
+
+from oracle import maxwell as mx
+from paper_2302_04979_gb300 import synth
+from tests.gpu_util import rel_l2, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "cube_p2_te111": dict(p=2, nel=8, steps=100, init="te111"),
+    "p3_blocks_ragged": dict(p=3, nel=(12, 9, 10), eps=("blocks", synth.block_material(3, (3, 3, 2), 1.0, 9.0)),
+                             mu=1.5, steps=60, init="random"),
+    "p4_aniso_elementwise": dict(p=(4, 3, 2), nel=(10, 7, 9), eps=2.0,
+                                 mu=("blocks", synth.block_material(4, (10, 7, 9), 1.0, 4.0)), steps=40,
+                                 init="random"),
+}
+
+
+def _setup(case):
+    S = mx.Scheme2(case["p"], case["nel"], eps=case.get("eps", 1.0), mu=case.get("mu", 1.0))
+    if case["init"] == "te111":
+        d = S.project_2form("D", mx.te111_E(0.0))
+        b = np.zeros(S.N_h)
+    else:
+        d = synth.uniform(70, S.N_e, -1.0, 1.0)
+        b = S.D1 @ synth.uniform(71, S.N_e, -1.0, 1.0)
+    e = S.e_from_d(d)
+    dt = 0.5 * S.cfl(tol=1e-8)[0]
+    return S, d, b, e, dt
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_against_oracle(name):
+    import torch
+    from paper_2302_04979_gb300 import smx
+    case = CASES[name]
+    S, d, b, e, dt = _setup(case)
+    n = case["steps"]
+    ref = S.step(d, b, e, dt, n)
+    ctx = smx.Context(case["p"], case["nel"], eps=case.get("eps", 1.0), mu=case.get("mu", 1.0),
+                      precision="mixed").bind()
+    dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
+    hd = torch.zeros(S.N_h, dtype=torch.float64, device="cuda")
+    ctx.step(dd, bd, ed, hd, dt, n)
+    errs = [rel_l2(to_host(g), w) for g, w in zip((dd, bd, ed, hd), ref)]
+    W0 = S.energy(d, b, e, dt)[1]
+    W1 = S.energy(to_host(dd), to_host(bd), to_host(ed), dt)[1]
+    print("\n%s mixed after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W drift %.2e"
+          % (name, n, *errs, abs(W1 - W0) / W0))
+    assert max(errs) < 1e-5
+    assert abs(W1 - W0) / W0 < 1e-5
+
+
+def test_mixed_rejects_unsupported():
+    from paper_2302_04979_gb300 import smx
+    with pytest.raises(smx.SmxError):
+        smx.Context(3, 4, geometry="sine_bump", precision="mixed")
+    with pytest.raises(smx.SmxError):
+        smx.Context(3, 4, eps=lambda x, y, z: 1.0 + x, precision="mixed")
+
+
+@pytest.mark.slow
+def test_mixed_64cube_against_oracle():
+    """The benchmark workload: 2 steps against the oracle, then W drift over 1000 GPU steps."""
+    import torch
+    from paper_2302_04979_gb300 import smx
+    eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
+    S = mx.Scheme2(3, 64, eps=eps)
+    d = synth.uniform(2303, S.N_e, -1.0, 1.0)
+    b = S.D1 @ synth.uniform(2304, S.N_e, -1.0, 1.0)
+    e = S.e_from_d(d)
+    dt = 2e-3
+    ref = S.step(d, b, e, dt, 2)
+    ctx = smx.Context(3, 64, eps=eps, precision="mixed").bind()
+    dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
+    hd = torch.zeros(S.N_h, dtype=torch.float64, device="cuda")
+    ctx.step(dd, bd, ed, hd, dt, 2)
+    errs = [rel_l2(to_host(g), w) for g, w in zip((dd, bd, ed, hd), ref)]
+    print("\n64^3 mixed after 2 steps: rel L2 d %.2e b %.2e e %.2e h %.2e" % tuple(errs))
+    assert max(errs) < 1e-5
+    ctx64 = smx.Context(3, 64, eps=eps).bind()   # FP64 energy of the mixed trajectory
+    W0 = ctx64.energy(to_dev(d), to_dev(b), to_dev(e), dt)[1]
+    dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
+    ctx.step(dd, bd, ed, hd, dt, 1000)
+    W1 = ctx64.energy(dd, bd, ed, dt)[1]
+    print("64^3 mixed: W drift over 1000 steps %.2e" % (abs(W1 - W0) / W0))
+    assert abs(W1 - W0) / W0 < 1e-4
