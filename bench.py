@@ -273,7 +273,8 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     eps = ("blocks", synth.block_material(SEED, EPS_BLOCKS, 1.0, 9.0))
     ctx = smx.Context(P, NEL, eps=eps, mu=1.0).bind(dev)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)   # non-default: smx_step replays a captured CUDA graph
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream)
     ne, nh = ctx.N_e, ctx.N_h
     dof = ne + nh

@@ -130,6 +130,14 @@ int smx_bind_workspace(smx_ctx* ctx, void* device_ptr, size_t bytes);
  * legacy default stream). */
 int smx_set_stream(smx_ctx* ctx, void* stream);
 
+/* CUDA graphs for smx_step (default on): the first call with a given set of
+ * (d, b, e, h, jhat, amp) pointers, dt and nsteps is captured into a graph,
+ * later identical calls replay it with one launch.  Only the last call is
+ * cached; a different argument set recaptures.  Eager launches are used when
+ * per-kernel timing is on or the stream is the legacy default stream (NULL),
+ * which cannot be captured.  enable = 0 always launches eagerly. */
+int smx_set_graphs(smx_ctx* ctx, int enable);
+
 /* b += alpha * D^1 e: primal curl by the +-1 incidence matrix (Eq. discrete2_faraday,
  * Remark on incidence matrices after Table 1).  e: N_e, b: N_h, device, no aliasing. */
 int smx_curl_primal(smx_ctx* ctx, const double* e, double* b, double alpha);

@@ -57,6 +57,14 @@ struct Blob {
     }
 };
 
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double dt = 0.0;
+    int nsteps = 0;
+    long long kernels = 0;  // kernel nodes per replay
+};
+
 uint64_t splitmix64(uint64_t& s) {
     uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -106,6 +114,12 @@ struct smx_ctx {
     float *e32 = nullptr, *h32 = nullptr, *y32 = nullptr;
     HodgeBlockF32Args hb32[2];
     LineF32Args ln32[2][3];  // [field][axis]: plain pairing sweeps (block Hodge) or fused mass + solve (separable)
+    // captured CUDA graph of the last smx_step call, keyed by its pointers, dt and nsteps
+    int use_graphs = 1;
+    GraphCache graph;
+    bool use_mode = false;   // dense mode products instead of line recurrences (every line length <= kModeMaxN)
+    size_t o_mode32[2][3][3];
+    ModeF32Args md32[2][3];  // [field][axis]
 };
 
 namespace {
@@ -329,6 +343,42 @@ int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
     return SMX_OK;
 }
 
+// Dense A^{-1} (row-major) from a banded LU, column by column.
+std::vector<double> dense_inverse(const BandLU& f) {
+    const int n = f.n;
+    std::vector<double> inv((size_t)n * n, 0.0), col(n);
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+        for (int m = 0; m < n; ++m)
+            for (int k = 1; k <= f.kl; ++k)
+                if (m - k >= 0) col[m] -= f.L[(size_t)m * f.kl + k - 1] * col[m - k];
+        for (int m = n - 1; m >= 0; --m) {
+            double v = col[m] * f.dinv[m];
+            for (int k = 1; k <= f.ku; ++k)
+                if (m + k < n) v -= f.U[(size_t)m * f.ku + k - 1] * col[m + k];
+            col[m] = v;
+        }
+        for (int i = 0; i < n; ++i) inv[(size_t)i * n + j] = col[i];
+    }
+    return inv;
+}
+
+// Dense (n x n) product of a dense matrix with a banded one given as band rows (half-bandwidth d).
+std::vector<double> dense_times_band(const std::vector<double>& A, const std::vector<double>& rows, int n, int d) {
+    const int W = 2 * d + 1;
+    std::vector<double> out((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double a = A[(size_t)i * n + k];
+            if (a == 0.0) continue;
+            for (int q = 0; q < W; ++q) {
+                const int j = k - d + q;
+                if (j >= 0 && j < n) out[(size_t)i * n + j] += a * rows[(size_t)k * W + q];
+            }
+        }
+    return out;
+}
+
 // FP64 values as FP32 (hi, lo) pairs: hi = fl32(v), lo = fl32(v - hi); hi + lo = v to about 2^-48 relative.
 std::vector<float> split_pairs(const std::vector<double>& v) {
     std::vector<float> out(2 * v.size());
@@ -425,6 +475,24 @@ int dot_impl(smx_ctx* C, const double* x, const double* y, long long n, int slot
 // h = 1: e32 = K_1^{-1} M~^2 d), same algorithms as the FP64 path.
 int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out) {
     int st;
+    if (C->use_mode) {
+        // dense mode products: A^{-1} M per axis (separable) or block mass + A^{-1} per axis
+        const double* x64 = x;
+        const float* x32 = nullptr;
+        if (!C->hodge[h].separable) {
+            const long long n = C->fld[kFieldOfHodge[h]].total;
+            CK(cudaMemsetAsync(C->y32, 0, (size_t)n * sizeof(float), C->stream));
+            st = run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->y32, C->stream); });
+            if (st) return st;
+            x64 = nullptr;
+            x32 = C->y32;
+        }
+        st = run(C, 14, 1, [&] { return launch_mode_f32(C->md32[h][0], x64, x32, out, C->stream); });
+        if (st) return st;
+        st = run(C, 15, 1, [&] { return launch_mode_f32(C->md32[h][1], nullptr, out, out, C->stream); });
+        if (st) return st;
+        return run(C, 16, 1, [&] { return launch_mode_f32(C->md32[h][2], nullptr, out, out, C->stream); });
+    }
     if (C->hodge[h].separable) {
         st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, true, x, nullptr, out, C->stream); });
         if (st) return st;
@@ -464,6 +532,23 @@ int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
     st = run(C, 17, 1, [&] { return launch_cast_f2d(C->e32, e, C->N_e, C->stream); });
     if (st) return st;
     return run(C, 17, 1, [&] { return launch_cast_f2d(C->h32, h, C->N_h, C->stream); });
+}
+
+int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out);
+
+// nsteps kick-drift-kick steps enqueued kernel by kernel (the inner half kicks of b merged).
+int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp, double dt,
+               int nsteps) {
+    if (C->precision == SMX_MIXED) return step_mixed(C, d, b, e, h, jhat, amp, dt, nsteps);
+    int st = curl_primal_impl(C, e, b, -0.5 * dt);
+    if (st) return st;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((st = hodge_star_impl(C, 0, b, h))) return st;  // h = K~_1^{-1} M^2_{1/mu} b
+        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0))) return st;
+        if ((st = hodge_star_impl(C, 1, d, e))) return st;  // e = K_1^{-1} M~^2_{1/eps} d
+        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt))) return st;
+    }
+    return SMX_OK;
 }
 
 // One discrete Hodge star of scheme 2 (Eq. discrete2_hodge_mu for h = 0,
@@ -623,6 +708,28 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                         for (int kind = 0; kind < 4; ++kind)
                             C->o_lmass32[h][a][kind] = C->blob.add(split_pairs(H.lmass[a][kind]));
             }
+            // dense line operators for the mode-product sweeps: A^{-1}, or A^{-1} M (separable star)
+            C->use_mode = true;
+            for (int a = 0; a < 3; ++a)
+                if (kind_dim(P0, C->p[a], C->nel[a]) + 1 > kModeMaxN) C->use_mode = false;
+            if (C->use_mode) {
+                std::vector<double> inv[3][4];
+                for (int a = 0; a < 3; ++a)
+                    for (int w = 0; w < 4; ++w) inv[a][w] = dense_inverse(C->fac[a][w]);
+                for (int h = 0; h < 2; ++h) {
+                    const HodgeHost& H = C->hodge[h];
+                    const int fld = kFieldOfHodge[h], which = h == 0 ? 1 : 0;
+                    for (int a = 0; a < 3; ++a)
+                        for (int c = 0; c < 3; ++c) {
+                            const int w = factor_index(which, c, a), kind = kFieldKinds[fld][c][a];
+                            const int n = C->fac[a][w].n;
+                            const std::vector<double> B =
+                                H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
+                                            : inv[a][w];
+                            C->o_mode32[h][a][c] = C->blob.add(split_pairs(B));
+                        }
+                }
+            }
         }
         C->tables_bytes = (C->blob.bytes.size() + 255) & ~size_t(255);
         C->o_scratch = C->tables_bytes;
@@ -648,11 +755,13 @@ int smx_create(const smx_params* P, smx_ctx** out) {
 }
 
 int smx_destroy(smx_ctx* C) {
-    if (C)
+    if (C) {
         for (auto& t : C->timed) {
             cudaEventDestroy(t.a);
             cudaEventDestroy(t.b);
         }
+        if (C->graph.exec) cudaGraphExecDestroy(C->graph.exec);
+    }
     delete C;
     return SMX_OK;
 }
@@ -689,6 +798,10 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
     CK(cudaMemcpyAsync(ws, C->blob.bytes.data(), C->blob.bytes.size(), cudaMemcpyHostToDevice, C->stream));
     CK(cudaStreamSynchronize(C->stream));
     C->ws = ws;
+    if (C->graph.exec) {  // a captured step refers to the previous workspace
+        cudaGraphExecDestroy(C->graph.exec);
+        C->graph.exec = nullptr;
+    }
     C->scratch = reinterpret_cast<double*>(ws + C->o_scratch);
     C->scratch2 = reinterpret_cast<double*>(ws + C->o_scratch2);
     C->partial = reinterpret_cast<double*>(ws + C->o_partial);
@@ -786,6 +899,13 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
             B.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
             B.max_nloc = H.max_nloc;
             for (int a = 0; a < 3; ++a) {
+                ModeF32Args& Md = C->md32[h][a];
+                Md.field = C->fld[fld];
+                Md.axis = a;
+                for (int c = 0; c < 3; ++c)
+                    Md.B[c] = C->use_mode ? reinterpret_cast<const float2*>(ws + C->o_mode32[h][a][c]) : nullptr;
+            }
+            for (int a = 0; a < 3; ++a) {
                 LineF32Args& Lg = C->ln32[h][a];
                 Lg.field = C->fld[fld];
                 Lg.axis = a;
@@ -848,16 +968,50 @@ int smx_step(smx_ctx* C, double* d, double* b, double* e, double* h, const doubl
     if (!d || !b || !e || !h || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return SMX_EINVAL;
     if (jhat && !amp) return SMX_EINVAL;
     if (nsteps == 0) return SMX_OK;
-    if (C->precision == SMX_MIXED) return step_mixed(C, d, b, e, h, jhat, amp, dt, nsteps);
-    // kick-drift-kick with the inner half kicks of b merged
-    int st = curl_primal_impl(C, e, b, -0.5 * dt);
-    if (st) return st;
-    for (int n = 0; n < nsteps; ++n) {
-        if ((st = hodge_star_impl(C, 0, b, h))) return st;  // h = K~_1^{-1} M^2_{1/mu} b
-        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0))) return st;
-        if ((st = hodge_star_impl(C, 1, d, e))) return st;  // e = K_1^{-1} M~^2_{1/eps} d
-        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt))) return st;
+    // Replay a captured CUDA graph of the whole call: one launch instead of about
+    // ten per step.  Eager launches when per-kernel timing is on or the stream is
+    // the legacy default stream (which cannot be captured).
+    if (C->timing || C->stream == nullptr || !C->use_graphs) return step_eager(C, d, b, e, h, jhat, amp, dt, nsteps);
+    GraphCache& G = C->graph;
+    const void* key[6] = {d, b, e, h, jhat, amp};
+    bool hit = G.exec != nullptr && G.dt == dt && G.nsteps == nsteps;
+    for (int i = 0; i < 6 && hit; ++i) hit = G.key[i] == key[i];
+    if (!hit) {
+        if (G.exec) {
+            cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+        }
+        const long long before = C->launches;
+        CK(cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal));
+        const int st = step_eager(C, d, b, e, h, jhat, amp, dt, nsteps);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(C->stream, &graph);
+        if (st || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            C->launches = before;
+            return st ? st : SMX_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            G.exec = nullptr;
+            C->launches = before;
+            return SMX_ECUDA;
+        }
+        G.kernels = C->launches - before;
+        C->launches = before;
+        G.dt = dt;
+        G.nsteps = nsteps;
+        for (int i = 0; i < 6; ++i) G.key[i] = key[i];
     }
+    CK(cudaGraphLaunch(G.exec, C->stream));
+    C->launches += G.kernels;
+    return SMX_OK;
+}
+
+int smx_set_graphs(smx_ctx* C, int enable) {
+    if (!C) return SMX_EINVAL;
+    C->use_graphs = enable ? 1 : 0;
     return SMX_OK;
 }
 
@@ -1050,6 +1204,13 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
             const bool sep = C->hodge[h].separable;
             const int st = smx_kernel_work(C, sep ? 8 + a : 4 + a, field, flops, bytes);
             if (st) return st;
+            if (C->use_mode) {  // dense mode product: 2 n flops per entry
+                const DevField& F = C->fld[kFieldOfHodge[h]];
+                double f = 0.0;
+                for (int c = 0; c < 3; ++c)
+                    f += 2.0 * F.c[c].n[a] * ((double)F.c[c].n[0] * F.c[c].n[1] * F.c[c].n[2]);
+                *flops = f;
+            }
             *bytes = (sep && a == 0 ? 12.0 : 8.0) * N;
             return SMX_OK;
         }

@@ -100,6 +100,15 @@ struct LineF32Args {
     int axis;
 };
 
+// Dense mode product along one axis: every line x of component c becomes B[c] x.
+struct ModeF32Args {
+    DevField field;
+    const float2* B[3];  // per component: n x n, row-major, (hi, lo) pairs
+    int axis;
+};
+constexpr int kModeMaxN = 80;  // largest line length the mode-product kernel handles
+
+cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const float* in32, float* out, cudaStream_t s);
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
                             cudaStream_t s);

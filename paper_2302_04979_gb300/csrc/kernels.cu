@@ -7,84 +7,21 @@
 
 #include <algorithm>
 
+#include "curl.cuh"
 #include "internal.h"
 
 namespace smx {
 
-// ------------------------------------------------------------------ curl
-// Incidence along axis a (Remark on incidence matrices after Table 1):
-//   primal (d u)_m = u_m - u_{m-1}, u_m = 0 outside [0, n_a) (removed BC functions);
-//   dual   (d u)_m = u_{m+1} - u_m (the input has one more entry along a).
-// (curl u)_c = d_{c+1} u_{c+2} - d_{c+2} u_{c+1}.  One thread per output
-// coefficient on a 3D grid (x, y, component * z); the component is a
-// template parameter so every extent and stride is a compile-time field.
-template <int A, bool DUAL>
-__device__ __forceinline__ double incidence(const DevComp& u, const double* __restrict__ v, int i, int j, int k) {
-    const int idx = i + u.n[0] * (j + u.n[1] * k);
-    const int stride = A == 0 ? 1 : (A == 1 ? u.n[0] : u.n[0] * u.n[1]);
-    const double* p = v + u.off + idx;
-    if (DUAL) return __ldg(p + stride) - __ldg(p);
-    const int m = A == 0 ? i : (A == 1 ? j : k);
-    const double hi = (m < u.n[A]) ? __ldg(p) : 0.0;
-    const double lo = (m >= 1) ? __ldg(p - stride) : 0.0;
-    return hi - lo;
-}
-
-template <int C, bool DUAL>
-__device__ __forceinline__ void curl_comp(const DevField& IN, const DevField& OUT, const double* __restrict__ in,
-                                          double* __restrict__ out, double alpha, const double* __restrict__ jhat,
-                                          const double* __restrict__ amp, int amp_index, double s_host, int i, int j,
-                                          int k) {
-    constexpr int a1 = (C + 1) % 3, a2 = (C + 2) % 3;
-    const DevComp& O = OUT.c[C];
-    if (i >= O.n[0] || j >= O.n[1] || k >= O.n[2]) return;
-    double v = incidence<a1, DUAL>(IN.c[a2], in, i, j, k) - incidence<a2, DUAL>(IN.c[a1], in, i, j, k);
-    const long long g = O.off + i + O.n[0] * (j + O.n[1] * k);
-    if (DUAL && jhat != nullptr) {
-        const double s = amp != nullptr ? __ldg(amp + amp_index) : s_host;
-        v = fma(-s, __ldg(jhat + g), v);
-    }
-    out[g] = fma(alpha, v, out[g]);
-}
-
-template <bool DUAL>
-__global__ void __launch_bounds__(128) curl_kernel(DevField IN, DevField OUT, const double* __restrict__ in,
-                                                   double* __restrict__ out, double alpha,
-                                                   const double* __restrict__ jhat, const double* __restrict__ amp,
-                                                   int amp_index, double s_host, int nzmax) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const int c = blockIdx.z / nzmax;
-    const int k = blockIdx.z - c * nzmax;
-    if (c == 0)
-        curl_comp<0, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
-    else if (c == 1)
-        curl_comp<1, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
-    else
-        curl_comp<2, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
-}
-
-template <bool DUAL>
-static cudaError_t launch_curl(const DevField& IN, const DevField& OUT, const double* in, double* out, double alpha,
-                               const double* jhat, const double* amp, int amp_index, double s_host, cudaStream_t s) {
-    int nmax[3] = {0, 0, 0};
-    for (int c = 0; c < 3; ++c)
-        for (int a = 0; a < 3; ++a) nmax[a] = std::max(nmax[a], OUT.c[c].n[a]);
-    if (OUT.total == 0) return cudaSuccess;
-    const dim3 grid((nmax[0] + 127) / 128, nmax[1], 3 * nmax[2]);
-    curl_kernel<DUAL><<<grid, 128, 0, s>>>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, nmax[2]);
-    return cudaGetLastError();
-}
-
+// ------------------------------------------------------------------ curl (see curl.cuh)
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b, double alpha,
                                cudaStream_t s) {
-    return launch_curl<false>(E, B, e, b, alpha, nullptr, nullptr, 0, 0.0, s);
+    return launch_curl_t<false, double>(E, B, e, b, alpha, nullptr, nullptr, 0, 0.0, s);
 }
 
 cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double* h, double* d, double alpha,
                              const double* jhat, const double* amp, int amp_index, double s_host,
                              cudaStream_t s) {
-    return launch_curl<true>(H, D, h, d, alpha, jhat, amp, amp_index, s_host, s);
+    return launch_curl_t<true, double>(H, D, h, d, alpha, jhat, amp, amp_index, s_host, s);
 }
 
 // ------------------------------------------------------------------ Hodge: block Kronecker

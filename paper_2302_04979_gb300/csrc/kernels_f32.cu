@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "curl.cuh"
 #include "internal.h"
 
 namespace smx {
@@ -33,68 +34,12 @@ __device__ __forceinline__ float to_f(T v) {
     return static_cast<float>(v);
 }
 
-// ------------------------------------------------------------------ curl (FP32 differences, FP64 state)
-template <int A, bool DUAL>
-__device__ __forceinline__ float incidence_f(const DevComp& u, const float* __restrict__ v, int i, int j, int k) {
-    const int idx = i + u.n[0] * (j + u.n[1] * k);
-    const int stride = A == 0 ? 1 : (A == 1 ? u.n[0] : u.n[0] * u.n[1]);
-    const float* p = v + u.off + idx;
-    if (DUAL) return __ldg(p + stride) - __ldg(p);
-    const int m = A == 0 ? i : (A == 1 ? j : k);
-    const float hi = (m < u.n[A]) ? __ldg(p) : 0.0f;
-    const float lo = (m >= 1) ? __ldg(p - stride) : 0.0f;
-    return hi - lo;
-}
-
-template <int C, bool DUAL>
-__device__ __forceinline__ void curl_comp_f(const DevField& IN, const DevField& OUT, const float* __restrict__ in,
-                                            double* __restrict__ out, double alpha, const double* __restrict__ jhat,
-                                            const double* __restrict__ amp, int amp_index, double s_host, int i, int j,
-                                            int k) {
-    constexpr int a1 = (C + 1) % 3, a2 = (C + 2) % 3;
-    const DevComp& O = OUT.c[C];
-    if (i >= O.n[0] || j >= O.n[1] || k >= O.n[2]) return;
-    const float vf = incidence_f<a1, DUAL>(IN.c[a2], in, i, j, k) - incidence_f<a2, DUAL>(IN.c[a1], in, i, j, k);
-    double v = static_cast<double>(vf);
-    const long long g = O.off + i + O.n[0] * (j + O.n[1] * k);
-    if (DUAL && jhat != nullptr) {
-        const double s = amp != nullptr ? __ldg(amp + amp_index) : s_host;
-        v = fma(-s, __ldg(jhat + g), v);
-    }
-    out[g] = fma(alpha, v, out[g]);
-}
-
-template <bool DUAL>
-__global__ void __launch_bounds__(128) curl_f32_kernel(DevField IN, DevField OUT, const float* __restrict__ in,
-                                                       double* __restrict__ out, double alpha,
-                                                       const double* __restrict__ jhat,
-                                                       const double* __restrict__ amp, int amp_index, double s_host,
-                                                       int nzmax) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const int c = blockIdx.z / nzmax;
-    const int k = blockIdx.z - c * nzmax;
-    if (c == 0)
-        curl_comp_f<0, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
-    else if (c == 1)
-        curl_comp_f<1, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
-    else
-        curl_comp_f<2, DUAL>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, i, j, k);
-}
-
+// ------------------------------------------------------------------ curl (FP32 differences, FP64 state; curl.cuh)
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
                             cudaStream_t s) {
-    int nmax[3] = {0, 0, 0};
-    for (int c = 0; c < 3; ++c)
-        for (int a = 0; a < 3; ++a) nmax[a] = std::max(nmax[a], OUT.c[c].n[a]);
-    if (OUT.total == 0) return cudaSuccess;
-    const dim3 grid((nmax[0] + 127) / 128, nmax[1], 3 * nmax[2]);
-    if (dual)
-        curl_f32_kernel<true><<<grid, 128, 0, s>>>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, nmax[2]);
-    else
-        curl_f32_kernel<false><<<grid, 128, 0, s>>>(IN, OUT, in, out, alpha, nullptr, nullptr, 0, 0.0, nmax[2]);
-    return cudaGetLastError();
+    if (dual) return launch_curl_t<true, float>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, s);
+    return launch_curl_t<false, float>(IN, OUT, in, out, alpha, nullptr, nullptr, 0, 0.0, s);
 }
 
 // ------------------------------------------------------------------ casts
@@ -119,6 +64,8 @@ cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t
 // Same algorithm as the FP64 block kernel (one CTA per tile and component,
 // three banded passes in shared memory, atomics to scatter) with split FP32
 // tile masses.  The input may be the FP64 state (converted on load).
+// Threads (ii, jj) = (threadIdx.x, threadIdx.y) cover the tile's x-y face
+// (L <= 16 per axis) and march along z, so no index is divided at run time.
 template <class TIN>
 __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args A, const TIN* __restrict__ x,
                                                               float* __restrict__ y) {
@@ -148,7 +95,8 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     const int Lx = L[0], Ly = L[1], Lz = L[2];
     const int nloc = Lx * Ly * Lz;
     float* s1 = s0 + nloc;
-    for (int t = threadIdx.x; t < kLMax * kLMax; t += blockDim.x) {
+    const int flat = threadIdx.y * 16 + threadIdx.x;
+    for (int t = flat; t < kLMax * kLMax; t += 256) {
         Mx[t] = gmat[0][t];
         My[t] = gmat[1][t];
         // gamma folded into z in FP64, then split again
@@ -159,33 +107,41 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     }
     const DevComp C = A.field.c[c];
     const long long nxy = (long long)C.n[0] * C.n[1];
-    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-        const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
-        s0[t] = to_f(__ldg(x + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * (f0[2] + kk)));
-    }
+    const int ii = threadIdx.x, jj = threadIdx.y;
+    const bool act = ii < Lx && jj < Ly;
+    const TIN* xcol = x + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
+    if (act)
+        for (int kk = 0; kk < Lz; ++kk) s0[(kk * Ly + jj) * Lx + ii] = to_f(__ldg(xcol + nxy * kk));
     __syncthreads();
-    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-        const int ii = t % Lx, row = t - ii;
+    if (act) {  // x pass
         const int lo = max(0, ii - dg[0]), hi = min(Lx - 1, ii + dg[0]);
-        float acc = 0.0f;
-        for (int m = lo; m <= hi; ++m) acc = fma2(Mx[ii * kLMax + m], s0[row + m], acc);
-        s1[t] = acc;
+        for (int kk = 0; kk < Lz; ++kk) {
+            const float* row = s0 + (kk * Ly + jj) * Lx;
+            float acc = 0.0f;
+            for (int m = lo; m <= hi; ++m) acc = fma2(Mx[ii * kLMax + m], row[m], acc);
+            s1[(kk * Ly + jj) * Lx + ii] = acc;
+        }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-        const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
+    if (act) {  // y pass
         const int lo = max(0, jj - dg[1]), hi = min(Ly - 1, jj + dg[1]);
-        float acc = 0.0f;
-        for (int m = lo; m <= hi; ++m) acc = fma2(My[jj * kLMax + m], s1[(kk * Ly + m) * Lx + ii], acc);
-        s0[t] = acc;
+        for (int kk = 0; kk < Lz; ++kk) {
+            const float* col = s1 + kk * Ly * Lx + ii;
+            float acc = 0.0f;
+            for (int m = lo; m <= hi; ++m) acc = fma2(My[jj * kLMax + m], col[m * Lx], acc);
+            s0[(kk * Ly + jj) * Lx + ii] = acc;
+        }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-        const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
-        const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
-        float acc = 0.0f;
-        for (int m = lo; m <= hi; ++m) acc = fma2(Mz[kk * kLMax + m], s0[(m * Ly + jj) * Lx + ii], acc);
-        atomicAdd(y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * (f0[2] + kk), acc);
+    if (act) {  // z pass and scatter-add
+        float* ycol = y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
+        const float* col = s0 + jj * Lx + ii;
+        for (int kk = 0; kk < Lz; ++kk) {
+            const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
+            float acc = 0.0f;
+            for (int m = lo; m <= hi; ++m) acc = fma2(Mz[kk * kLMax + m], col[m * Ly * Lx], acc);
+            atomicAdd(ycol + nxy * kk, acc);
+        }
     }
 }
 
@@ -195,9 +151,9 @@ cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64
     const size_t smem = 3 * kLMax * kLMax * sizeof(float2) + 2 * (size_t)a.max_nloc * sizeof(float);
     if (ntiles == 0) return cudaSuccess;
     if (x64)
-        hodge_block_f32_kernel<double><<<dim3(ntiles, 3), 256, smem, s>>>(a, x64, y);
+        hodge_block_f32_kernel<double><<<dim3(ntiles, 3), dim3(16, 16), smem, s>>>(a, x64, y);
     else
-        hodge_block_f32_kernel<float><<<dim3(ntiles, 3), 256, smem, s>>>(a, x32, y);
+        hodge_block_f32_kernel<float><<<dim3(ntiles, 3), dim3(16, 16), smem, s>>>(a, x32, y);
     return cudaGetLastError();
 }
 
@@ -409,6 +365,161 @@ cudaError_t launch_line_f32(const LineF32Args& a, int kl, bool mass, const doubl
                             cudaStream_t s) {
     if (mass) return in64 ? launch_line_kl<true, double>(a, kl, in64, out, s) : launch_line_kl<true, float>(a, kl, in32, out, s);
     return in64 ? launch_line_kl<false, double>(a, kl, in64, out, s) : launch_line_kl<false, float>(a, kl, in32, out, s);
+}
+
+}  // namespace smx
+
+namespace smx {
+
+// ------------------------------------------------------------------ dense mode products (mixed step)
+// Along one axis, every line of a component is multiplied by a precomputed
+// dense n x n operator B (FP64 values as FP32 (hi, lo) pairs): B = A^{-1}
+// (pairing solve) or A^{-1} M (fused separable Hodge star).  Unlike the
+// banded recurrence this has no dependency chain: each output is an
+// independent dot product, so the pass runs at the FP32 throughput of the
+// CUDA cores instead of the latency of a serial recurrence.
+// CTA: kModeLines lines staged as T[j][line] in shared memory, B (transposed)
+// in shared memory.
+constexpr int kModeLines = 64;    // lines per CTA
+constexpr int kModeLineGroups = 16;  // threads along lines: 4 lines each (one float4 of the tile)
+constexpr int kModeOutGroups = 16;   // threads along outputs: outputs i = og + 16 r
+
+// Register-blocked: thread (lg, og) accumulates 4 lines x NOUT outputs; per
+// entry j it reads one float4 of the staged tile T[j][4 lg .. 4 lg + 3] and
+// NOUT split coefficients Bt[j][og + 16 r] (warp-broadcast), then issues
+// 8 NOUT FMAs.  Rows i >= n read zero padding and are not stored.
+template <class TIN, int NOUT>
+__global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kernel(ModeF32Args A,
+                                                                                   const TIN* __restrict__ in,
+                                                                                   float* __restrict__ out) {
+    extern __shared__ float smf[];
+    const int c = blockIdx.y;
+    const DevComp C = A.field.c[c];
+    const int axis = A.axis;
+    const int n = C.n[axis];
+    const int nlines = C.n[0] * C.n[1] * C.n[2] / n;
+    const int l0 = blockIdx.x * kModeLines;
+    if (l0 >= nlines) return;
+    const int nl = min(kModeLines, nlines - l0);
+    constexpr int NPAD = kModeOutGroups * NOUT;                 // padded output count
+    float2* Bt = reinterpret_cast<float2*>(smf);                // n x NPAD (transposed, zero padded)
+    float* T = reinterpret_cast<float*>(Bt + n * NPAD);         // n x kModeLines (16-byte aligned rows)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float2* Bg = A.B[c];
+    for (int t = tid; t < n * NPAD; t += nt) {
+        const int j = t / NPAD, i = t - j * NPAD;
+        if (i < n)
+            cp_async8f(Bt + t, Bg + i * n + j);
+        else
+            Bt[t] = make_float2(0.0f, 0.0f);
+    }
+    const int nx = C.n[0], nxy = C.n[0] * C.n[1];
+    const TIN* src = in + C.off;
+    if (axis == 0) {
+        const TIN* chunk = src + (long long)l0 * n;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int line = g / n, m = g - line * n;
+            T[m * kModeLines + line] = to_f(__ldg(chunk + g));
+        }
+    } else {
+        const int stride = axis == 1 ? nx : nxy;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int m = g / nl, w = g - m * nl;
+            const int l = l0 + w;
+            const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+            T[m * kModeLines + w] = to_f(__ldg(src + base + m * stride));
+        }
+    }
+    if (nl < kModeLines)  // keep the unused tile columns finite
+        for (int g = tid; g < (kModeLines - nl) * n; g += nt) {
+            const int m = g / (kModeLines - nl), w = nl + g - m * (kModeLines - nl);
+            T[m * kModeLines + w] = 0.0f;
+        }
+    cp_async_wait_all_f();
+    __syncthreads();
+    const int lg = tid % kModeLineGroups, og = tid / kModeLineGroups;
+    float acc[4][NOUT];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < NOUT; ++r) acc[q][r] = 0.0f;
+    for (int j = 0; j < n; ++j) {
+        const float4 t = *reinterpret_cast<const float4*>(T + j * kModeLines + 4 * lg);
+        const float2* brow = Bt + j * NPAD + og;
+#pragma unroll
+        for (int r = 0; r < NOUT; ++r) {
+            const float2 bb = brow[r * kModeOutGroups];
+            acc[0][r] = fma2(bb, t.x, acc[0][r]);
+            acc[1][r] = fma2(bb, t.y, acc[1][r]);
+            acc[2][r] = fma2(bb, t.z, acc[2][r]);
+            acc[3][r] = fma2(bb, t.w, acc[3][r]);
+        }
+    }
+    __syncthreads();  // T is reused for the outputs
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) {
+        const int i = og + r * kModeOutGroups;
+        if (i < n)
+            *reinterpret_cast<float4*>(T + i * kModeLines + 4 * lg) =
+                make_float4(acc[0][r], acc[1][r], acc[2][r], acc[3][r]);
+    }
+    __syncthreads();
+    float* dst = out + C.off;
+    if (axis == 0) {
+        float* chunk = dst + (long long)l0 * n;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int line = g / n, m = g - line * n;
+            chunk[g] = T[m * kModeLines + line];
+        }
+    } else {
+        const int stride = axis == 1 ? nx : nxy;
+        for (int g = tid; g < nl * n; g += nt) {
+            const int m = g / nl, ww = g - m * nl;
+            const int l = l0 + ww;
+            const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+            dst[base + m * stride] = T[m * kModeLines + ww];
+        }
+    }
+}
+
+template <int NOUT>
+static cudaError_t launch_mode_t(const ModeF32Args& a, const double* in64, const float* in32, float* out, int maxn,
+                                 long long nb, cudaStream_t s) {
+    const size_t smem = (size_t)maxn * kModeOutGroups * NOUT * sizeof(float2) + (size_t)maxn * kModeLines * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mode_f32_kernel<double, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(mode_f32_kernel<float, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    const dim3 grid((unsigned)nb, 3);
+    if (in64)
+        mode_f32_kernel<double, NOUT><<<grid, kModeLineGroups * kModeOutGroups, smem, s>>>(a, in64, out);
+    else
+        mode_f32_kernel<float, NOUT><<<grid, kModeLineGroups * kModeOutGroups, smem, s>>>(a, in32, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const float* in32, float* out, cudaStream_t s) {
+    long long maxlines = 0;
+    int maxn = 0;
+    for (int c = 0; c < 3; ++c) {
+        const long long nc = (long long)a.field.c[c].n[0] * a.field.c[c].n[1] * a.field.c[c].n[2];
+        const int n = a.field.c[c].n[a.axis];
+        if (n > 0) maxlines = std::max(maxlines, nc / n);
+        maxn = std::max(maxn, n);
+    }
+    if (maxn > kModeMaxN) return cudaErrorInvalidValue;
+    const long long nb = (maxlines + kModeLines - 1) / kModeLines;
+    if (nb == 0) return cudaSuccess;
+    switch ((maxn + kModeOutGroups - 1) / kModeOutGroups) {
+        case 1: return launch_mode_t<1>(a, in64, in32, out, maxn, nb, s);
+        case 2: return launch_mode_t<2>(a, in64, in32, out, maxn, nb, s);
+        case 3: return launch_mode_t<3>(a, in64, in32, out, maxn, nb, s);
+        case 4: return launch_mode_t<4>(a, in64, in32, out, maxn, nb, s);
+        case 5: return launch_mode_t<5>(a, in64, in32, out, maxn, nb, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace smx

@@ -53,6 +53,7 @@ _SIGS = {
     "smx_workspace_bytes": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
     "smx_bind_workspace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "smx_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
+    "smx_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "smx_curl_primal": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
     "smx_curl_dual": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                       ctypes.c_double],
@@ -203,6 +204,9 @@ class Context:
     def set_stream(self, stream):
         _check(_lib().smx_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)),
                "smx_set_stream")
+
+    def set_graphs(self, on):
+        _check(_lib().smx_set_graphs(self.h, 1 if on else 0), "smx_set_graphs")
 
     def factor_matrix(self, axis, which):
         n = ctypes.c_int64()

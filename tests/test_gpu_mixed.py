@@ -21,6 +21,9 @@ CASES = {
     "p4_aniso_elementwise": dict(p=(4, 3, 2), nel=(10, 7, 9), eps=2.0,
                                  mu=("blocks", synth.block_material(4, (10, 7, 9), 1.0, 4.0)), steps=40,
                                  init="random"),
+    # lines longer than the dense mode-product limit (80): the banded FP32 line recurrences run instead
+    "p2_long_lines": dict(p=2, nel=(90, 4, 3), eps=("blocks", synth.block_material(6, (3, 2, 1), 1.0, 4.0)),
+                          steps=40, init="random"),
 }
 
 

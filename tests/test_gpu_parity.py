@@ -179,3 +179,33 @@ def test_cfl_matches_oracle(name):
     ref = S.cfl(tol=1e-13, iters=3000)[0]
     got = G.cfl(iters=3000, tol=1e-13)
     assert abs(got - ref) <= 1e-7 * ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_graph_replay(precision):
+    """smx_step on a non-default stream: captured into a CUDA graph on the first call, replayed after."""
+    import torch
+    from paper_2302_04979_gb300 import smx
+    case = CASES["p3_blocks_ragged"]
+    S = _oracle(case)
+    G = smx.Context(case["p"], case["nel"], eps=case["eps"], mu=case["mu"], precision=precision).bind()
+    stream = torch.cuda.Stream()
+    G.set_stream(stream)
+    d = synth.uniform(80, S.N_e, -1, 1)
+    b = S.D1 @ synth.uniform(81, S.N_e, -1, 1)
+    e = S.e_from_d(d)
+    dt, nsteps = 0.01, 3
+    ref = S.step(d, b, e, dt, 2 * nsteps)
+    dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
+    hd = torch.zeros(S.N_h, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    n0 = G.launch_count()
+    G.step(dd, bd, ed, hd, dt, nsteps)   # capture + first replay
+    n1 = G.launch_count()
+    G.step(dd, bd, ed, hd, dt, nsteps)   # replay of the cached graph
+    n2 = G.launch_count()
+    stream.synchronize()
+    assert n1 - n0 == n2 - n1 > 0
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    for got, want in zip((dd, bd, ed, hd), ref):
+        assert rel_l2(to_host(got), want) < tol
