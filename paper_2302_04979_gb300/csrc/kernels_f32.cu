@@ -380,14 +380,16 @@ namespace smx {
 // CUDA cores instead of the latency of a serial recurrence.
 // CTA: kModeLines lines staged as T[j][line] in shared memory, B (transposed)
 // in shared memory.
-constexpr int kModeLines = 64;    // lines per CTA
-constexpr int kModeLineGroups = 16;  // threads along lines: 4 lines each (one float4 of the tile)
-constexpr int kModeOutGroups = 16;   // threads along outputs: outputs i = og + 16 r
+constexpr int kModeLines = 32;       // lines per CTA
+constexpr int kModeLd = 36;          // tile row stride (floats): 16-byte aligned, spreads banks
+constexpr int kModeLineGroups = 8;   // threads along lines: 4 lines each (one float4 of the tile)
+constexpr int kModeOutGroups = 32;   // threads along outputs: outputs i = og + 32 r
 
 // Register-blocked: thread (lg, og) accumulates 4 lines x NOUT outputs; per
 // entry j it reads one float4 of the staged tile T[j][4 lg .. 4 lg + 3] and
-// NOUT split coefficients Bt[j][og + 16 r] (warp-broadcast), then issues
-// 8 NOUT FMAs.  Rows i >= n read zero padding and are not stored.
+// NOUT split coefficients Bt[j][og + 32 r] (shared by the 8 threads of a
+// warp with the same og), then issues 8 NOUT FMAs.  Rows i >= n read zero
+// padding and are not stored.
 template <class TIN, int NOUT>
 __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kernel(ModeF32Args A,
                                                                                    const TIN* __restrict__ in,
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
     const int nl = min(kModeLines, nlines - l0);
     constexpr int NPAD = kModeOutGroups * NOUT;                 // padded output count
     float2* Bt = reinterpret_cast<float2*>(smf);                // n x NPAD (transposed, zero padded)
-    float* T = reinterpret_cast<float*>(Bt + n * NPAD);         // n x kModeLines (16-byte aligned rows)
+    float* T = reinterpret_cast<float*>(Bt + n * NPAD);         // n x kModeLd (16-byte aligned rows)
     const int tid = threadIdx.x, nt = blockDim.x;
     const float2* Bg = A.B[c];
     for (int t = tid; t < n * NPAD; t += nt) {
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
         const TIN* chunk = src + (long long)l0 * n;
         for (int g = tid; g < nl * n; g += nt) {
             const int line = g / n, m = g - line * n;
-            T[m * kModeLines + line] = to_f(__ldg(chunk + g));
+            T[m * kModeLd + line] = to_f(__ldg(chunk + g));
         }
     } else {
         const int stride = axis == 1 ? nx : nxy;
@@ -427,13 +429,13 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
             const int m = g / nl, w = g - m * nl;
             const int l = l0 + w;
             const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-            T[m * kModeLines + w] = to_f(__ldg(src + base + m * stride));
+            T[m * kModeLd + w] = to_f(__ldg(src + base + m * stride));
         }
     }
     if (nl < kModeLines)  // keep the unused tile columns finite
         for (int g = tid; g < (kModeLines - nl) * n; g += nt) {
             const int m = g / (kModeLines - nl), w = nl + g - m * (kModeLines - nl);
-            T[m * kModeLines + w] = 0.0f;
+            T[m * kModeLd + w] = 0.0f;
         }
     cp_async_wait_all_f();
     __syncthreads();
@@ -443,8 +445,9 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < NOUT; ++r) acc[q][r] = 0.0f;
+#pragma unroll 2
     for (int j = 0; j < n; ++j) {
-        const float4 t = *reinterpret_cast<const float4*>(T + j * kModeLines + 4 * lg);
+        const float4 t = *reinterpret_cast<const float4*>(T + j * kModeLd + 4 * lg);
         const float2* brow = Bt + j * NPAD + og;
 #pragma unroll
         for (int r = 0; r < NOUT; ++r) {
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
     for (int r = 0; r < NOUT; ++r) {
         const int i = og + r * kModeOutGroups;
         if (i < n)
-            *reinterpret_cast<float4*>(T + i * kModeLines + 4 * lg) =
+            *reinterpret_cast<float4*>(T + i * kModeLd + 4 * lg) =
                 make_float4(acc[0][r], acc[1][r], acc[2][r], acc[3][r]);
     }
     __syncthreads();
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
         float* chunk = dst + (long long)l0 * n;
         for (int g = tid; g < nl * n; g += nt) {
             const int line = g / n, m = g - line * n;
-            chunk[g] = T[m * kModeLines + line];
+            chunk[g] = T[m * kModeLd + line];
         }
     } else {
         const int stride = axis == 1 ? nx : nxy;
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
             const int m = g / nl, ww = g - m * nl;
             const int l = l0 + ww;
             const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-            dst[base + m * stride] = T[m * kModeLines + ww];
+            dst[base + m * stride] = T[m * kModeLd + ww];
         }
     }
 }
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
 template <int NOUT>
 static cudaError_t launch_mode_t(const ModeF32Args& a, const double* in64, const float* in32, float* out, int maxn,
                                  long long nb, cudaStream_t s) {
-    const size_t smem = (size_t)maxn * kModeOutGroups * NOUT * sizeof(float2) + (size_t)maxn * kModeLines * sizeof(float);
+    const size_t smem = (size_t)maxn * kModeOutGroups * NOUT * sizeof(float2) + (size_t)maxn * kModeLd * sizeof(float);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(mode_f32_kernel<double, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -516,8 +519,6 @@ cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const floa
         case 1: return launch_mode_t<1>(a, in64, in32, out, maxn, nb, s);
         case 2: return launch_mode_t<2>(a, in64, in32, out, maxn, nb, s);
         case 3: return launch_mode_t<3>(a, in64, in32, out, maxn, nb, s);
-        case 4: return launch_mode_t<4>(a, in64, in32, out, maxn, nb, s);
-        case 5: return launch_mode_t<5>(a, in64, in32, out, maxn, nb, s);
         default: return cudaErrorInvalidValue;
     }
 }
