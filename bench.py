@@ -33,7 +33,9 @@ if ROOT not in sys.path:
 METRIC = "leapfrog DoF-steps/s (p=3, 64^3) FP64 vs mixed; % HBM/tensor roofline"
 UNIT = "DoF-steps/s"
 P, NEL, EPS_BLOCKS, SEED = 3, 64, (8, 8, 8), 2302
-FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (152 SMs x ~2 DFMA/clk x 2 flop at ~2.07 GHz)
+# GB300 FP64 CUDA-core peak from unit counts and clock: 152 SMs x 2 DFMA lanes/clk x 2 flop x 2.07 GHz
+# (the nominal 1.25 TFLOP/s; the repository's FMA probe measures 1.19)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -184,6 +186,15 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------ GPU arm
 HBM_PEAK_GBS = 6793.1   # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
 
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel at this
+# workload (profiles/fp64_step_p3_64cube.md, profiles/mixed_step_p3_64cube.md; cold
+# caches, outputs stay in L2).  Kept only while the kernel is unchanged since the capture.
+NCU_TRAFFIC = {
+    "mass_solve_x": 6.90e6, "mass_solve_y": 6.90e6, "mass_solve_z": 6.90e6,
+    "solve_x": 6.72e6, "solve_y": 6.72e6, "solve_z": 6.72e6,
+    "hodge_block": 13.51e6,
+}
+
 
 def kernel_table(ctx, smx, ktimes):
     """Per-kernel-class launches, time, share and algorithmic work per launch."""
@@ -319,6 +330,14 @@ def run_ours(args, rank, world, local):
     m_ms = reduce_max(m_ms, world)
     m_steady, mkern = steady_and_kernels(mctx, smx, mstate, dt, args.steps, flush, stream)
     m_steady = reduce_max(m_steady, world)
+    # the same mixed step with the dense line operators on the FP32 CUDA cores instead of the tensor cores
+    mctx.set_mode_kernel("simt")
+    for _ in range(args.warmup):
+        mctx.step(*mstate, dt, 1)
+    s_ms, _ = time_steps(mctx, mstate, dt, args.steps, flush, stream, world)
+    s_ms = reduce_max(s_ms, world)
+    mctx.set_mode_kernel("tensor")
+    mctx.device_status()
     clocks = sampler.stop()
 
     # ---- end to end through the host-buffer C call (copies inside the timed region)
@@ -338,13 +357,15 @@ def run_ours(args, rank, world, local):
     # ---- roofline of the dominant kernel: FP64 form is bound by the FP64 pipe
     dom = max(kern, key=lambda n: kern[n]["total_ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kern[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": kern[dom]["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json; "
-                           "our FMA probe measured 1.19)",
+            "unit": "TFLOP/s", "frac": kern[dom]["fp64_tflops"] / FP64_PEAK_TFLOPS,
+            "traffic": NCU_TRAFFIC.get(dom),
+            "peak_source": "FP64 unit count x clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
+                           "MEASURED_PEAKS.json has no FP64 entry; the FMA probe measured 1.19 TFLOP/s",
             "hbm_gbs": kern[dom]["gbs"]}
     mdom = max(mkern, key=lambda n: mkern[n]["total_ms"])
     mroof = {"kernel": mdom, "bound": "hbm", "achieved": mkern[mdom]["gbs"], "peak": HBM_PEAK_GBS, "unit": "GB/s",
-             "frac": mkern[mdom]["gbs"] / HBM_PEAK_GBS, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+             "frac": mkern[mdom]["gbs"] / HBM_PEAK_GBS, "traffic": NCU_TRAFFIC.get(mdom),
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
     out = None
     if rank == 0:
@@ -357,8 +378,12 @@ def run_ours(args, rank, world, local):
                                 "ms_per_step": steady_ms / args.steps,
                                 "note": "K steps in one smx_step call, no L2 flush (state L2-resident)"},
                "mixed": {"value": reduce_sum(dof * args.steps, world) / (m_ms * 1e-3), "unit": UNIT,
-                         "ms_per_step": m_ms / args.steps, "dtype": "f32 operators (split coefficients), f64 state",
+                         "ms_per_step": m_ms / args.steps, "dtype": "bf16x3 tensor-core line operators, f32 curl and block Hodge (split coefficients), f64 state",
                          "gpu_launches": m_launches, "roofline": mroof, "kernels": mkern,
+                         "line_operators": "tcgen05 tensor cores, BF16 three-term split, FP32 accumulate",
+                         "simt_line_operators": {"value": reduce_sum(dof * args.steps, world) / (s_ms * 1e-3),
+                                                 "ms_per_step": s_ms / args.steps,
+                                                 "note": "same step, dense line operators on FP32 CUDA cores"},
                          "speedup_vs_fp64": total_ms / m_ms,
                          "steady_state": {"value": reduce_sum(dof * args.steps, world) / (m_steady * 1e-3),
                                           "ms_per_step": m_steady / args.steps}}}

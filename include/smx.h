@@ -46,6 +46,7 @@ extern "C" {
 #define SMX_ENOMEM (-7)      /* host allocation failed */
 #define SMX_ESINGULAR (-8)   /* a 1D pairing factor has a (near) zero pivot */
 #define SMX_ENOSPACE (-9)    /* problem larger than the library's fixed device array (SMX_NOALLOC_BYTES) */
+#define SMX_ETIMEOUT (-10)   /* a device-side wait gave up after its time limit (see smx_device_status) */
 
 /* ---- geometry map F : (0,1)^3 -> Omega (Sec. 2.3) ---- */
 #define SMX_GEOM_IDENTITY 0  /* F = identity: the unit-cube cavity of Sec. 5.1.1 */
@@ -91,9 +92,9 @@ typedef struct {
  * per coefficient per half step); the curl differences, the Hodge mass apply
  * and the pairing sweeps run in FP32 with operator coefficients stored as
  * FP32 (hi, lo) pairs (hi + lo = the FP64 value to about 2^-48), so only the
- * data is rounded to FP32.  Supported for the identity map with constant or
- * block material (SMX_EINVAL otherwise).  Only smx_step / smx_step_host
- * change; every other call stays FP64. */
+ * data is rounded to FP32.  On a curved map or with pointwise material the
+ * quadrature metric is stored in FP32 (rounded once).  Only smx_step /
+ * smx_step_host (and smx_hodge_star_mixed) change; every other call stays FP64. */
 #define SMX_FP64 0
 #define SMX_MIXED 1
 
@@ -137,6 +138,23 @@ int smx_set_stream(smx_ctx* ctx, void* stream);
  * per-kernel timing is on or the stream is the legacy default stream (NULL),
  * which cannot be captured.  enable = 0 always launches eagerly. */
 int smx_set_graphs(smx_ctx* ctx, int enable);
+
+/* Kernel for the dense line operators of the mixed step (SMX_MIXED with every
+ * line length <= 80; Eq. kroninverse applied as a dense product per axis):
+ *   SMX_MODE_TENSOR (default): tcgen05 tensor cores; data and operator split
+ *     into three BF16 terms each, six products accumulated in FP32 (the
+ *     accuracy of an FP32 dot product);
+ *   SMX_MODE_SIMT: FP32 CUDA cores with the operator as FP32 (hi, lo) pairs.
+ * Both give the same result to FP32 rounding.  Errors: SMX_EINVAL. */
+#define SMX_MODE_TENSOR 0
+#define SMX_MODE_SIMT 1
+int smx_set_mode_kernel(smx_ctx* ctx, int which);
+
+/* Synchronise the context stream and read the device status word: SMX_OK, or
+ * SMX_ETIMEOUT if a kernel of this context gave up a bounded device-side wait
+ * (the tensor-core completion wait, one second) since the last call; the word
+ * is then cleared.  Results of the affected launches are not valid. */
+int smx_device_status(smx_ctx* ctx);
 
 /* b += alpha * D^1 e: primal curl by the +-1 incidence matrix (Eq. discrete2_faraday,
  * Remark on incidence matrices after Table 1).  e: N_e, b: N_h, device, no aliasing. */
@@ -207,9 +225,10 @@ int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
  *   4 solve along x, 5 solve along y, 6 solve along z, 7 reductions,
  *   8/9/10 fused mass + solve along x/y/z (separable Hodge star),
  *   11 curl_primal and 12 curl_dual of the mixed step (FP32 differences),
- *   13 FP32 block Hodge, 14/15/16 FP32 line passes along x/y/z, 17 casts.
+ *   13 FP32 block Hodge, 14/15/16 FP32 line passes along x/y/z, 17 casts,
+ *   18 FP32 quadrature Hodge.
  * ms[SMX_NCLASS] receives milliseconds, counts[SMX_NCLASS] launches per class. */
-#define SMX_NCLASS 18
+#define SMX_NCLASS 19
 int smx_launch_count(const smx_ctx* ctx, int64_t* n);
 int smx_set_timing(smx_ctx* ctx, int enable);
 int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);
@@ -268,6 +287,14 @@ int smx_factor_matrix(const smx_ctx* ctx, int axis, int which, int64_t* n, doubl
  * the Hodge star runs as three fused mass + solve line passes (the plain mass
  * apply still uses the block kernel). */
 int smx_hodge_mode(const smx_ctx* ctx, int field, int* mode);
+
+/* The Hodge star of the mixed step on its own (Eq. discrete2_hodge_eps /
+ * discrete2_hodge_mu in mixed precision): out = K_1^{-1} M~ x (SMX_FIELD_D) or
+ * K~_1^{-1} M x (SMX_FIELD_B) computed by the FP32 kernels smx_step uses for
+ * SMX_MIXED (x read as FP64, result FP32 widened into the FP64 out; device
+ * arrays).  Errors: SMX_EINVAL, SMX_ESTATE (no workspace, or the context is
+ * not SMX_MIXED), SMX_ECUDA. */
+int smx_hodge_star_mixed(smx_ctx* ctx, int field, const double* x, double* out);
 
 #ifdef __cplusplus
 }

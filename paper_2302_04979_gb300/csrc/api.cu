@@ -43,7 +43,7 @@ struct HodgeHost {
     long long Qtot = 0;
     int Qn[3] = {0, 0, 0};
     // device offsets in the workspace (bytes)
-    size_t o_tf0[3], o_tlen[3], o_tmat[3], o_gamma, o_bval[3], o_G;
+    size_t o_tf0[3] = {}, o_tlen[3] = {}, o_tmat[3] = {}, o_gamma = 0, o_bval[3] = {}, o_G = 0;
 };
 
 struct Blob {
@@ -113,6 +113,8 @@ struct smx_ctx {
     size_t o_e32 = 0, o_h32 = 0, o_y32 = 0;
     float *e32 = nullptr, *h32 = nullptr, *y32 = nullptr;
     HodgeBlockF32Args hb32[2];
+    size_t o_bval32[2][3], o_G32[2];  // quadrature Hodge (curved map / pointwise material): FP32 tables
+    HodgeQuadF32Args hq32[2];
     LineF32Args ln32[2][3];  // [field][axis]: plain pairing sweeps (block Hodge) or fused mass + solve (separable)
     // captured CUDA graph of the last smx_step call, keyed by its pointers, dt and nsteps
     int use_graphs = 1;
@@ -120,6 +122,12 @@ struct smx_ctx {
     bool use_mode = false;   // dense mode products instead of line recurrences (every line length <= kModeMaxN)
     size_t o_mode32[2][3][3];
     ModeF32Args md32[2][3];  // [field][axis]
+    // the same operators as three BF16 parts for the tensor-core kernel (the default)
+    int mode_kernel = SMX_MODE_TENSOR;
+    size_t o_modetc[2][3][3];
+    ModeTcArgs mtc[2][3];
+    size_t o_status = 0;          // device status word (bit 0: a tensor-core wait gave up)
+    unsigned* status = nullptr;
 };
 
 namespace {
@@ -472,44 +480,60 @@ int dot_impl(smx_ctx* C, const double* x, const double* y, long long n, int slot
 
 // ---- mixed precision: FP32 operators on the FP64 state
 // FP32 Hodge star from the FP64 2-form x into out (h = 0: h32 = K~_1^{-1} M^2 b;
-// h = 1: e32 = K_1^{-1} M~^2 d), same algorithms as the FP64 path.
-int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out) {
+// h = 1: e32 = K_1^{-1} M~^2 d), same algorithms as the FP64 path.  out64
+// (optional) also receives the result widened to FP64: written by the last
+// tensor-core sweep itself, else by a cast kernel.
+// y32 = M x in FP32 (block-Kronecker or quadrature Hodge, by the field's mode).
+int mass_f32(smx_ctx* C, int h, const double* x) {
+    const long long ntot = C->fld[kFieldOfHodge[h]].total;
+    CK(cudaMemsetAsync(C->y32, 0, (size_t)ntot * sizeof(float), C->stream));
+    if (C->hodge[h].mode == 1)
+        return run(C, 18, 1, [&] { return launch_hodge_quad_f32(C->hq32[h], x, C->y32, C->stream); });
+    return run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->y32, C->stream); });
+}
+
+int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* out64 = nullptr) {
     int st;
+    const long long ntot = C->fld[kFieldOfHodge[h]].total;
+    auto widen = [&]() {
+        return out64 ? run(C, 17, 1, [&] { return launch_cast_f2d(out, out64, ntot, C->stream); }) : SMX_OK;
+    };
     if (C->use_mode) {
         // dense mode products: A^{-1} M per axis (separable) or block mass + A^{-1} per axis
         const double* x64 = x;
         const float* x32 = nullptr;
         if (!C->hodge[h].separable) {
-            const long long n = C->fld[kFieldOfHodge[h]].total;
-            CK(cudaMemsetAsync(C->y32, 0, (size_t)n * sizeof(float), C->stream));
-            st = run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->y32, C->stream); });
-            if (st) return st;
+            if ((st = mass_f32(C, h, x))) return st;
             x64 = nullptr;
             x32 = C->y32;
         }
-        st = run(C, 14, 1, [&] { return launch_mode_f32(C->md32[h][0], x64, x32, out, C->stream); });
-        if (st) return st;
-        st = run(C, 15, 1, [&] { return launch_mode_f32(C->md32[h][1], nullptr, out, out, C->stream); });
-        if (st) return st;
-        return run(C, 16, 1, [&] { return launch_mode_f32(C->md32[h][2], nullptr, out, out, C->stream); });
+        const bool tc = C->mode_kernel == SMX_MODE_TENSOR;
+        auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
+            return run(C, 14 + a, 1, [&] {
+                return tc ? launch_mode_tc(C->mtc[h][a], i64, i32, out, o64, C->stream)
+                          : launch_mode_f32(C->md32[h][a], i64, i32, out, C->stream);
+            });
+        };
+        if ((st = pass(0, x64, x32, nullptr))) return st;
+        if ((st = pass(1, nullptr, out, nullptr))) return st;
+        if ((st = pass(2, nullptr, out, tc ? out64 : nullptr))) return st;
+        return tc ? SMX_OK : widen();
     }
     if (C->hodge[h].separable) {
         st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, true, x, nullptr, out, C->stream); });
         if (st) return st;
         st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, true, nullptr, out, out, C->stream); });
         if (st) return st;
-        return run(C, 16, 1,
-                   [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, true, nullptr, out, out, C->stream); });
+        st = run(C, 16, 1, [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, true, nullptr, out, out, C->stream); });
+        return st ? st : widen();
     }
-    const long long n = C->fld[kFieldOfHodge[h]].total;
-    CK(cudaMemsetAsync(C->y32, 0, (size_t)n * sizeof(float), C->stream));
-    st = run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->y32, C->stream); });
-    if (st) return st;
+    if ((st = mass_f32(C, h, x))) return st;
     st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, false, nullptr, C->y32, out, C->stream); });
     if (st) return st;
     st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, false, nullptr, out, out, C->stream); });
     if (st) return st;
-    return run(C, 16, 1, [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, false, nullptr, out, out, C->stream); });
+    st = run(C, 16, 1, [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, false, nullptr, out, out, C->stream); });
+    return st ? st : widen();
 }
 
 int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp, double dt,
@@ -521,17 +545,16 @@ int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
     st = run(C, 11, 1, [&] { return launch_curl_f32(false, FE, FB, C->e32, b, -0.5 * dt, nullptr, nullptr, 0, 0.0, C->stream); });
     if (st) return st;
     for (int n = 0; n < nsteps; ++n) {
-        if ((st = hodge_star_f32_impl(C, 0, b, C->h32))) return st;
+        const bool last = n + 1 == nsteps;  // the last stars also write the FP64 1-forms h and e
+        if ((st = hodge_star_f32_impl(C, 0, b, C->h32, last ? h : nullptr))) return st;
         st = run(C, 12, 1, [&] { return launch_curl_f32(true, FH, FD, C->h32, d, dt, jhat, amp, n, 0.0, C->stream); });
         if (st) return st;
-        if ((st = hodge_star_f32_impl(C, 1, d, C->e32))) return st;
+        if ((st = hodge_star_f32_impl(C, 1, d, C->e32, last ? e : nullptr))) return st;
         const double alpha = (n + 1 == nsteps) ? -0.5 * dt : -dt;
         st = run(C, 11, 1, [&] { return launch_curl_f32(false, FE, FB, C->e32, b, alpha, nullptr, nullptr, 0, 0.0, C->stream); });
         if (st) return st;
     }
-    st = run(C, 17, 1, [&] { return launch_cast_f2d(C->e32, e, C->N_e, C->stream); });
-    if (st) return st;
-    return run(C, 17, 1, [&] { return launch_cast_f2d(C->h32, h, C->N_h, C->stream); });
+    return SMX_OK;
 }
 
 int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out);
@@ -585,6 +608,7 @@ const char* smx_strerror(int s) {
         case SMX_ENOMEM: return "host allocation failed";
         case SMX_ESINGULAR: return "singular 1D pairing factor";
         case SMX_ENOSPACE: return "problem larger than the fixed no-alloc device array";
+        case SMX_ETIMEOUT: return "a device-side wait gave up after its time limit";
         default: return "unknown status";
     }
 }
@@ -662,10 +686,6 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             return SMX_EINVAL;
         }
         C->precision = P->precision;
-        if (C->precision == SMX_MIXED && (C->hodge[0].mode != 0 || C->hodge[1].mode != 0)) {
-            delete C;  // the FP32 operators cover the block-Kronecker Hodge only
-            return SMX_EINVAL;
-        }
         // pack the tables
         for (int a = 0; a < 3; ++a)
             for (int w = 0; w < 4; ++w) {
@@ -688,6 +708,11 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             } else {
                 for (int a = 0; a < 3; ++a) H.o_bval[a] = C->blob.add(H.bval[a]);
                 H.o_G = C->blob.add(H.G);
+                if (C->precision == SMX_MIXED) {  // the mixed step's FP32 copies (metric rounded once)
+                    for (int a = 0; a < 3; ++a)
+                        C->o_bval32[h][a] = C->blob.add(std::vector<float>(H.bval[a].begin(), H.bval[a].end()));
+                    C->o_G32[h] = C->blob.add(std::vector<float>(H.G.begin(), H.G.end()));
+                }
                 H.G.clear();
                 H.G.shrink_to_fit();
             }
@@ -727,6 +752,7 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                                 H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
                                             : inv[a][w];
                             C->o_mode32[h][a][c] = C->blob.add(split_pairs(B));
+                            C->o_modetc[h][a][c] = C->blob.add(bf16_split_operator(B, n, mode_tc_npad(n)));
                         }
                 }
             }
@@ -737,7 +763,8 @@ int smx_create(const smx_params* P, smx_ctx** out) {
         C->o_scratch2 = C->o_scratch + ((nmax * sizeof(double) + 255) & ~size_t(255));
         C->o_partial = C->o_scratch2 + ((nmax * sizeof(double) + 255) & ~size_t(255));
         C->o_dots = C->o_partial + ((kDotBlocks * sizeof(double) + 255) & ~size_t(255));
-        C->o_state = C->o_dots + 256;
+        C->o_status = C->o_dots + 256;
+        C->o_state = C->o_status + 256;
         C->total_bytes = C->o_state + ((2 * (size_t)(C->N_e + C->N_h) * sizeof(double) + 255) & ~size_t(255));
         if (C->precision == SMX_MIXED) {
             auto f32 = [](long long n) { return ((size_t)n * sizeof(float) + 255) & ~size_t(255); };
@@ -806,6 +833,8 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
     C->scratch2 = reinterpret_cast<double*>(ws + C->o_scratch2);
     C->partial = reinterpret_cast<double*>(ws + C->o_partial);
     C->dots = reinterpret_cast<double*>(ws + C->o_dots);
+    C->status = reinterpret_cast<unsigned*>(ws + C->o_status);
+    CK(cudaMemsetAsync(C->status, 0, sizeof(unsigned), C->stream));
     C->state = reinterpret_cast<double*>(ws + C->o_state);
     // pairing sweeps
     for (int which = 0; which < 2; ++which) {
@@ -883,6 +912,24 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
             const HodgeHost& H = C->hodge[h];
             const int fld = kFieldOfHodge[h];
             const int which = h == 0 ? 1 : 0;  // M^2 pairs with K~_1, M~^2 with K_1
+            if (H.mode == 1) {
+                HodgeQuadF32Args& Q = C->hq32[h];
+                const HodgeQuadArgs& Q64 = C->hq[h];
+                Q.field = Q64.field;
+                for (int a = 0; a < 3; ++a) {
+                    Q.nel[a] = Q64.nel[a];
+                    Q.q[a] = Q64.q[a];
+                    Q.Qn[a] = Q64.Qn[a];
+                    Q.bval[a] = reinterpret_cast<const float*>(ws + C->o_bval32[h][a]);
+                    for (int c = 0; c < 3; ++c) {
+                        Q.kinds[a][c] = Q64.kinds[a][c];
+                        Q.deg[a][c] = Q64.deg[a][c];
+                        Q.koff[a][c] = Q64.koff[a][c];
+                    }
+                }
+                Q.G = reinterpret_cast<const float*>(ws + C->o_G32[h]);
+                Q.Qtot = Q64.Qtot;
+            }
             HodgeBlockF32Args& B = C->hb32[h];
             B.field = C->fld[fld];
             for (int a = 0; a < 3; ++a) {
@@ -904,6 +951,14 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                 Md.axis = a;
                 for (int c = 0; c < 3; ++c)
                     Md.B[c] = C->use_mode ? reinterpret_cast<const float2*>(ws + C->o_mode32[h][a][c]) : nullptr;
+                ModeTcArgs& Mt = C->mtc[h][a];
+                Mt.field = C->fld[fld];
+                Mt.axis = a;
+                Mt.status = C->status;
+                for (int c = 0; c < 3; ++c) {
+                    Mt.B[c] = C->use_mode ? static_cast<const void*>(ws + C->o_modetc[h][a][c]) : nullptr;
+                    Mt.npad[c] = mode_tc_npad(C->fld[fld].c[c].n[a]);
+                }
             }
             for (int a = 0; a < 3; ++a) {
                 LineF32Args& Lg = C->ln32[h][a];
@@ -1013,6 +1068,37 @@ int smx_set_graphs(smx_ctx* C, int enable) {
     if (!C) return SMX_EINVAL;
     C->use_graphs = enable ? 1 : 0;
     return SMX_OK;
+}
+
+int smx_set_mode_kernel(smx_ctx* C, int which) {
+    if (!C || (which != SMX_MODE_TENSOR && which != SMX_MODE_SIMT)) return SMX_EINVAL;
+    if (which != C->mode_kernel && C->graph.exec) {  // a captured step launches the other kernel
+        cudaGraphExecDestroy(C->graph.exec);
+        C->graph.exec = nullptr;
+    }
+    C->mode_kernel = which;
+    return SMX_OK;
+}
+
+int smx_device_status(smx_ctx* C) {
+    NEED_WS(C);
+    unsigned v = 0;
+    CK(cudaMemcpyAsync(&v, C->status, sizeof v, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    if (v == 0) return SMX_OK;
+    CK(cudaMemsetAsync(C->status, 0, sizeof(unsigned), C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    return SMX_ETIMEOUT;
+}
+
+int smx_hodge_star_mixed(smx_ctx* C, int field, const double* x, double* out) {
+    NEED_WS(C);
+    if (!x || !out) return SMX_EINVAL;
+    if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
+    if (C->precision != SMX_MIXED) return SMX_ESTATE;
+    const int h = field == SMX_FIELD_B ? 0 : 1;
+    float* o32 = h == 0 ? C->h32 : C->e32;
+    return hodge_star_f32_impl(C, h, x, o32, out);
 }
 
 int smx_energy(smx_ctx* C, const double* d, const double* b, const double* e, double dt, double out[2]) {
@@ -1218,6 +1304,12 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
             *flops = 0.0;
             *bytes = 12.0 * N;
             return SMX_OK;
+        case 18: {  // FP32 quadrature Hodge: the FP64 quadrature kernel's flops, FP32 metric
+            const int st = smx_kernel_work(C, 3, field, flops, bytes);
+            if (st) return st;
+            *bytes = 12.0 * N + 24.0 * (double)C->hodge[bside ? 0 : 1].Qtot;
+            return SMX_OK;
+        }
         default:
             return SMX_EINVAL;
     }

@@ -16,6 +16,7 @@
 
 #include <cuda_runtime.h>
 
+#include "convert.cuh"
 #include "internal.h"
 
 namespace smx {
@@ -35,6 +36,9 @@ __device__ __forceinline__ T incidence_t(const DevComp& u, const T* __restrict__
     return hi - lo;
 }
 
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return f2d_exact(v); }
+
 template <int C, bool DUAL, class T>
 __device__ __forceinline__ void curl_plane_comp(const DevField& IN, const DevField& OUT, const T* __restrict__ in,
                                                 double* __restrict__ out, double alpha,
@@ -45,16 +49,30 @@ __device__ __forceinline__ void curl_plane_comp(const DevField& IN, const DevFie
     const int nx = O.n[0], nxy = O.n[0] * O.n[1];
     if (p >= nxy) return;
     const int j = p / nx, i = p - j * nx;
-    const int k1 = min(k0 + kCurlKz, O.n[2]);
+    const int nk = min(kCurlKz, O.n[2] - k0);
     double s = 0.0;
     if (DUAL && jhat != nullptr) s = amp != nullptr ? __ldg(amp + amp_index) : s_host;
-#pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-        const T vt = incidence_t<a1, DUAL, T>(IN.c[a2], in, i, j, k) - incidence_t<a2, DUAL, T>(IN.c[a1], in, i, j, k);
-        double v = static_cast<double>(vt);
-        const long long g = O.off + p + (long long)nxy * k;
-        if (DUAL && jhat != nullptr) v = fma(-s, __ldg(jhat + g), v);
-        out[g] = fma(alpha, v, out[g]);
+    // every load of the chunk first (the stores below cannot be hoisted over by the compiler), then the updates
+    T d1[kCurlKz], d2[kCurlKz];
+    double o[kCurlKz], jv[kCurlKz];
+#pragma unroll
+    for (int kk = 0; kk < kCurlKz; ++kk) {
+        if (kk < nk) {
+            const int k = k0 + kk;
+            const long long g = O.off + p + (long long)nxy * k;
+            d1[kk] = incidence_t<a1, DUAL, T>(IN.c[a2], in, i, j, k);
+            d2[kk] = incidence_t<a2, DUAL, T>(IN.c[a1], in, i, j, k);
+            o[kk] = out[g];
+            jv[kk] = (DUAL && jhat != nullptr) ? __ldg(jhat + g) : 0.0;
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < kCurlKz; ++kk) {
+        if (kk < nk) {
+            double v = widen(d1[kk] - d2[kk]);
+            if (DUAL && jhat != nullptr) v = fma(-s, jv[kk], v);
+            out[O.off + p + (long long)nxy * (k0 + kk)] = fma(alpha, v, o[kk]);
+        }
     }
 }
 

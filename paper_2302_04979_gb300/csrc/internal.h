@@ -90,6 +90,20 @@ struct HodgeBlockF32Args {
     int max_nloc;
 };
 
+// FP32 quadrature Hodge apply: HodgeQuadArgs with FP32 basis values and metric.
+struct HodgeQuadF32Args {
+    DevField field;
+    int nel[3];
+    int q[3];
+    int kinds[3][3];
+    int deg[3][3];
+    int koff[3][3];
+    const float* bval[3];
+    const float* G;
+    long long Qtot;
+    int Qn[3];
+};
+
 struct LineF32Args {
     DevField field;
     const float2* L[3];     // per component: n x KL
@@ -109,6 +123,21 @@ struct ModeF32Args {
 constexpr int kModeMaxN = 80;  // largest line length the mode-product kernel handles
 
 cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const float* in32, float* out, cudaStream_t s);
+
+// The same mode products on the tensor cores (kernels_tc.cu): the operator as
+// three BF16 parts in the shared-memory layout of that file, built on the host
+// by bf16_split_operator (setup.h).
+struct ModeTcArgs {
+    DevField field;
+    const void* B[3];   // per component: 3 parts x (npad / 8) chunks x (16 npad + 16) bytes
+    int npad[3];        // per component: line length rounded up to a multiple of 16
+    int axis;
+    unsigned* status;   // device word: bit 0 set when an MMA completion wait gave up
+};
+int mode_tc_npad(int n);
+// out64 (optional): the result also widened to FP64.
+cudaError_t launch_mode_tc(const ModeTcArgs& a, const double* in64, const float* in32, float* out, double* out64,
+                           cudaStream_t s);
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
                             cudaStream_t s);
@@ -116,6 +145,7 @@ cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t
 cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
 cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, float* y,
                                    cudaStream_t s);
+cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, float* y, cudaStream_t s);
 cudaError_t launch_line_f32(const LineF32Args& a, int kl, bool mass, const double* in64, const float* in32, float* out,
                             cudaStream_t s);
 

@@ -55,18 +55,22 @@ __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockAr
         gmat[a] = A.tmat[a] + (long long)slot * kLMax * kLMax;
     }
     const double gam = A.gamma[(tz * A.ntile[1] + ty) * A.ntile[0] + tx];
+    // tile masses with row stride kLd = kLMax + 1 (rows ii read at one column across a
+    // warp fall on distinct banks)
+    constexpr int kLd = kLMax + 1;
     double* Mx = sm;
-    double* My = Mx + kLMax * kLMax;
-    double* Mz = My + kLMax * kLMax;
-    double* s0 = Mz + kLMax * kLMax;
+    double* My = Mx + kLMax * kLd;
+    double* Mz = My + kLMax * kLd;
+    double* s0 = Mz + kLMax * kLd;
     const int Lx = L[0], Ly = L[1], Lz = L[2];
     const int nloc = Lx * Ly * Lz;
     double* s1 = s0 + nloc;
     // tile masses; gamma folded into Mz
     for (int t = threadIdx.x; t < kLMax * kLMax; t += blockDim.x) {
-        Mx[t] = __ldg(gmat[0] + t);
-        My[t] = __ldg(gmat[1] + t);
-        Mz[t] = gam * __ldg(gmat[2] + t);
+        const int d = (t / kLMax) * kLd + t % kLMax;
+        Mx[d] = __ldg(gmat[0] + t);
+        My[d] = __ldg(gmat[1] + t);
+        Mz[d] = gam * __ldg(gmat[2] + t);
     }
     const DevComp C = A.field.c[c];
     const long long nxy = (long long)C.n[0] * C.n[1];
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockAr
         const int ii = t % Lx, row = t - ii;
         const int lo = max(0, ii - dg[0]), hi = min(Lx - 1, ii + dg[0]);
         double acc = 0.0;
-        for (int m = lo; m <= hi; ++m) acc = fma(Mx[ii * kLMax + m], s0[row + m], acc);
+        for (int m = lo; m <= hi; ++m) acc = fma(Mx[ii * kLd + m], s0[row + m], acc);
         s1[t] = acc;
     }
     __syncthreads();
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockAr
         const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
         const int lo = max(0, jj - dg[1]), hi = min(Ly - 1, jj + dg[1]);
         double acc = 0.0;
-        for (int m = lo; m <= hi; ++m) acc = fma(My[jj * kLMax + m], s1[(kk * Ly + m) * Lx + ii], acc);
+        for (int m = lo; m <= hi; ++m) acc = fma(My[jj * kLd + m], s1[(kk * Ly + m) * Lx + ii], acc);
         s0[t] = acc;
     }
     __syncthreads();
@@ -98,18 +102,18 @@ __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockAr
         const int ii = t % Lx, r = t / Lx, jj = r % Ly, kk = r / Ly;
         const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
         double acc = 0.0;
-        for (int m = lo; m <= hi; ++m) acc = fma(Mz[kk * kLMax + m], s0[(m * Ly + jj) * Lx + ii], acc);
+        for (int m = lo; m <= hi; ++m) acc = fma(Mz[kk * kLd + m], s0[(m * Ly + jj) * Lx + ii], acc);
         atomicAdd(y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * (f0[2] + kk), acc);
     }
 }
 
 cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s) {
     const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
-    const size_t smem = (3 * kLMax * kLMax + 2 * (size_t)a.max_nloc) * sizeof(double);
+    const size_t smem = (3 * kLMax * (kLMax + 1) + 2 * (size_t)a.max_nloc) * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(hodge_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((3 * kLMax * kLMax + 2 * kLMax * kLMax * kLMax) * sizeof(double)));
+                             (int)((3 * kLMax * (kLMax + 1) + 2 * kLMax * kLMax * kLMax) * sizeof(double)));
         attr = true;
     }
     if (ntiles > 0) hodge_block_kernel<<<dim3(ntiles, 3), kHodgeThreads, smem, s>>>(a, x, y);

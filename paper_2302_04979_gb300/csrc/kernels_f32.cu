@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "convert.cuh"
 #include "curl.cuh"
 #include "internal.h"
 
@@ -29,10 +30,8 @@ __device__ __forceinline__ void cp_async8f(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all_f() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <class T>
-__device__ __forceinline__ float to_f(T v) {
-    return static_cast<float>(v);
-}
+__device__ __forceinline__ float to_f(double v) { return d2f_rn(v); }  // integer pipe (convert.cuh)
+__device__ __forceinline__ float to_f(float v) { return v; }
 
 // ------------------------------------------------------------------ curl (FP32 differences, FP64 state; curl.cuh)
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
@@ -45,11 +44,11 @@ cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, 
 // ------------------------------------------------------------------ casts
 __global__ void cast_d2f_kernel(const double* __restrict__ x, float* __restrict__ y, long long n) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) y[i] = static_cast<float>(x[i]);
+    if (i < n) y[i] = d2f_rn(x[i]);
 }
 __global__ void cast_f2d_kernel(const float* __restrict__ x, double* __restrict__ y, long long n) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) y[i] = static_cast<double>(x[i]);
+    if (i < n) y[i] = f2d_exact(x[i]);
 }
 cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t s) {
     if (n > 0) cast_d2f_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
@@ -88,22 +87,26 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
         gmat[a] = A.tmat[a] + (long long)slot * kLMax * kLMax;
     }
     const double gam = A.gamma[(tz * A.ntile[1] + ty) * A.ntile[0] + tx];
+    // tile masses with row stride kLd = kLMax + 1: the x pass reads rows ii of Mx at the
+    // same column across a warp, which an unpadded 16-entry stride puts on one bank
+    constexpr int kLd = kLMax + 1;
     float2* Mx = reinterpret_cast<float2*>(smf);
-    float2* My = Mx + kLMax * kLMax;
-    float2* Mz = My + kLMax * kLMax;
-    float* s0 = reinterpret_cast<float*>(Mz + kLMax * kLMax);
+    float2* My = Mx + kLMax * kLd;
+    float2* Mz = My + kLMax * kLd;
+    float* s0 = reinterpret_cast<float*>(Mz + kLMax * kLd);
     const int Lx = L[0], Ly = L[1], Lz = L[2];
     const int nloc = Lx * Ly * Lz;
     float* s1 = s0 + nloc;
     const int flat = threadIdx.y * 16 + threadIdx.x;
     for (int t = flat; t < kLMax * kLMax; t += 256) {
-        Mx[t] = gmat[0][t];
-        My[t] = gmat[1][t];
+        const int d = (t / kLMax) * kLd + t % kLMax;
+        Mx[d] = gmat[0][t];
+        My[d] = gmat[1][t];
         // gamma folded into z in FP64, then split again
         const float2 z = gmat[2][t];
         const double v = gam * ((double)z.x + (double)z.y);
         const float hi = (float)v;
-        Mz[t] = make_float2(hi, (float)(v - (double)hi));
+        Mz[d] = make_float2(hi, (float)(v - (double)hi));
     }
     const DevComp C = A.field.c[c];
     const long long nxy = (long long)C.n[0] * C.n[1];
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
         for (int kk = 0; kk < Lz; ++kk) {
             const float* row = s0 + (kk * Ly + jj) * Lx;
             float acc = 0.0f;
-            for (int m = lo; m <= hi; ++m) acc = fma2(Mx[ii * kLMax + m], row[m], acc);
+            for (int m = lo; m <= hi; ++m) acc = fma2(Mx[ii * kLd + m], row[m], acc);
             s1[(kk * Ly + jj) * Lx + ii] = acc;
         }
     }
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
         for (int kk = 0; kk < Lz; ++kk) {
             const float* col = s1 + kk * Ly * Lx + ii;
             float acc = 0.0f;
-            for (int m = lo; m <= hi; ++m) acc = fma2(My[jj * kLMax + m], col[m * Lx], acc);
+            for (int m = lo; m <= hi; ++m) acc = fma2(My[jj * kLd + m], col[m * Lx], acc);
             s0[(kk * Ly + jj) * Lx + ii] = acc;
         }
     }
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
         for (int kk = 0; kk < Lz; ++kk) {
             const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
             float acc = 0.0f;
-            for (int m = lo; m <= hi; ++m) acc = fma2(Mz[kk * kLMax + m], col[m * Ly * Lx], acc);
+            for (int m = lo; m <= hi; ++m) acc = fma2(Mz[kk * kLd + m], col[m * Ly * Lx], acc);
             atomicAdd(ycol + nxy * kk, acc);
         }
     }
@@ -148,12 +151,140 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
 cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, float* y,
                                    cudaStream_t s) {
     const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
-    const size_t smem = 3 * kLMax * kLMax * sizeof(float2) + 2 * (size_t)a.max_nloc * sizeof(float);
+    const size_t smem = 3 * kLMax * (kLMax + 1) * sizeof(float2) + 2 * (size_t)a.max_nloc * sizeof(float);
     if (ntiles == 0) return cudaSuccess;
     if (x64)
         hodge_block_f32_kernel<double><<<dim3(ntiles, 3), dim3(16, 16), smem, s>>>(a, x64, y);
     else
         hodge_block_f32_kernel<float><<<dim3(ntiles, 3), dim3(16, 16), smem, s>>>(a, x32, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Hodge: quadrature, FP32
+// Curved map or pointwise material (the FP64 kernel's algorithm): per element,
+// interpolate the three components at the q^3 Gauss points by sum
+// factorisation, apply the symmetric metric G (weight, material and 2-form
+// pullback folded in, stored as FP32), integrate back, scatter-add into the
+// FP32 output with atomics.  One CTA per element.
+constexpr int kQuadF32Threads = 128;
+
+__global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQuadF32Args A,
+                                                                        const double* __restrict__ x,
+                                                                        float* __restrict__ y) {
+    extern __shared__ float smq[];
+    const int e = blockIdx.x;
+    const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
+    const int el[3] = {ex, ey, ez};
+    const int qx = A.q[0], qy = A.q[1], qz = A.q[2];
+    const int Qe = qx * qy * qz;
+    float* U = smq;                          // 3 * Qe values at the Gauss points
+    float* T1 = U + 3 * Qe;                  // scratch, <= Qe * kRMax
+    float* T2 = T1 + Qe * kRMax;             // scratch, <= Qe * kRMax
+    float* X = T2 + Qe * kRMax;              // local coefficients, <= kRMax^3
+    float* Bv = X + kRMax * kRMax * kRMax;   // 3 axes x 8 points x kRMax
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto load_basis = [&](int c) {
+        for (int t = tid; t < 3 * 8 * kRMax; t += nt) {
+            const int a = t / (8 * kRMax), rem = t % (8 * kRMax), qp = rem / kRMax, r = rem % kRMax;
+            if (qp < A.q[a])
+                Bv[t] = __ldg(A.bval[a] + (((long long)A.kinds[c][a] * A.nel[a] + el[a]) * A.q[a] + qp) * kRMax + r);
+        }
+    };
+    for (int c = 0; c < 3; ++c) {
+        const DevComp C = A.field.c[c];
+        const int rx = A.deg[c][0] + 1, ry = A.deg[c][1] + 1, rz = A.deg[c][2] + 1;
+        load_basis(c);
+        for (int t = tid; t < rx * ry * rz; t += nt) {
+            const int r0 = t % rx, rr = t / rx, r1 = rr % ry, r2 = rr / ry;
+            const int gi = el[0] + r0 + A.koff[c][0], gj = el[1] + r1 + A.koff[c][1], gk = el[2] + r2 + A.koff[c][2];
+            float v = 0.0f;
+            if (gi >= 0 && gi < C.n[0] && gj >= 0 && gj < C.n[1] && gk >= 0 && gk < C.n[2])
+                v = to_f(__ldg(x + C.off + gi + (long long)C.n[0] * (gj + (long long)C.n[1] * gk)));
+            X[t] = v;
+        }
+        __syncthreads();
+        const float* Bx = Bv;
+        const float* By = Bv + 8 * kRMax;
+        const float* Bz = Bv + 16 * kRMax;
+        for (int t = tid; t < rz * ry * qx; t += nt) {  // T1[r2][r1][qx]
+            const int a = t % qx, rr = t / qx;
+            float acc = 0.0f;
+            for (int r0 = 0; r0 < rx; ++r0) acc = fmaf(Bx[a * kRMax + r0], X[rr * rx + r0], acc);
+            T1[t] = acc;
+        }
+        __syncthreads();
+        for (int t = tid; t < rz * qy * qx; t += nt) {  // T2[r2][qy][qx]
+            const int a = t % qx, rr = t / qx, b = rr % qy, r2 = rr / qy;
+            float acc = 0.0f;
+            for (int r1 = 0; r1 < ry; ++r1) acc = fmaf(By[b * kRMax + r1], T1[(r2 * ry + r1) * qx + a], acc);
+            T2[t] = acc;
+        }
+        __syncthreads();
+        for (int t = tid; t < Qe; t += nt) {  // U_c[qz][qy][qx]
+            const int ab = t % (qx * qy), g = t / (qx * qy);
+            float acc = 0.0f;
+            for (int r2 = 0; r2 < rz; ++r2) acc = fmaf(Bz[g * kRMax + r2], T2[r2 * qx * qy + ab], acc);
+            U[c * Qe + t] = acc;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < Qe; t += nt) {  // metric at each Gauss point
+        const int a = t % qx, rr = t / qx, b = rr % qy, g = rr / qy;
+        const long long qi = ((long long)(ez * qz + g) * A.Qn[1] + (ey * qy + b)) * A.Qn[0] + (ex * qx + a);
+        const float g00 = __ldg(A.G + qi), g01 = __ldg(A.G + A.Qtot + qi), g02 = __ldg(A.G + 2 * A.Qtot + qi);
+        const float g11 = __ldg(A.G + 3 * A.Qtot + qi), g12 = __ldg(A.G + 4 * A.Qtot + qi);
+        const float g22 = __ldg(A.G + 5 * A.Qtot + qi);
+        const float u0 = U[t], u1 = U[Qe + t], u2 = U[2 * Qe + t];
+        U[t] = g00 * u0 + g01 * u1 + g02 * u2;
+        U[Qe + t] = g01 * u0 + g11 * u1 + g12 * u2;
+        U[2 * Qe + t] = g02 * u0 + g12 * u1 + g22 * u2;
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+        const DevComp C = A.field.c[c];
+        const int rx = A.deg[c][0] + 1, ry = A.deg[c][1] + 1, rz = A.deg[c][2] + 1;
+        load_basis(c);
+        __syncthreads();
+        const float* Bx = Bv;
+        const float* By = Bv + 8 * kRMax;
+        const float* Bz = Bv + 16 * kRMax;
+        for (int t = tid; t < rz * qy * qx; t += nt) {  // T2[r2][qy][qx] = sum_qz Bz[qz][r2] V[qz][qy][qx]
+            const int ab = t % (qx * qy), r2 = t / (qx * qy);
+            float acc = 0.0f;
+            for (int g = 0; g < qz; ++g) acc = fmaf(Bz[g * kRMax + r2], U[c * Qe + g * qx * qy + ab], acc);
+            T2[t] = acc;
+        }
+        __syncthreads();
+        for (int t = tid; t < rz * ry * qx; t += nt) {  // T1[r2][r1][qx] = sum_qy By[qy][r1] T2[r2][qy][qx]
+            const int a = t % qx, rr = t / qx, r1 = rr % ry, r2 = rr / ry;
+            float acc = 0.0f;
+            for (int b = 0; b < qy; ++b) acc = fmaf(By[b * kRMax + r1], T2[(r2 * qy + b) * qx + a], acc);
+            T1[t] = acc;
+        }
+        __syncthreads();
+        for (int t = tid; t < rx * ry * rz; t += nt) {  // sum_qx Bx[qx][r0] T1[r2][r1][qx], scatter-add
+            const int r0 = t % rx, rr = t / rx, r1 = rr % ry, r2 = rr / ry;
+            const int gi = el[0] + r0 + A.koff[c][0], gj = el[1] + r1 + A.koff[c][1], gk = el[2] + r2 + A.koff[c][2];
+            if (gi >= 0 && gi < C.n[0] && gj >= 0 && gj < C.n[1] && gk >= 0 && gk < C.n[2]) {
+                float acc = 0.0f;
+                for (int a = 0; a < qx; ++a) acc = fmaf(Bx[a * kRMax + r0], T1[rr * qx + a], acc);
+                atomicAdd(y + C.off + gi + (long long)C.n[0] * (gj + (long long)C.n[1] * gk), acc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, float* y, cudaStream_t s) {
+    const int nel = a.nel[0] * a.nel[1] * a.nel[2];
+    const int Qe = a.q[0] * a.q[1] * a.q[2];
+    const size_t smem = (3 * Qe + 2 * Qe * kRMax + kRMax * kRMax * kRMax + 3 * 8 * kRMax) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(hodge_quad_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    if (nel > 0) hodge_quad_f32_kernel<<<nel, kQuadF32Threads, smem, s>>>(a, x, y);
     return cudaGetLastError();
 }
 

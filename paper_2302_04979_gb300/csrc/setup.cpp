@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 namespace smx {
 
@@ -201,6 +202,37 @@ std::vector<double> element_mass(int kind, int p, int nel, int e) {
             for (int b = 0; b < m; ++b) Me[a * m + b] += w * v[a] * v[b];
     }
     return Me;
+}
+
+// Round an FP32 value to BF16, nearest even (IEEE rounding on the 16 dropped bits).
+static uint16_t bf16_nearest(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    if ((u & 0x7F800000u) == 0x7F800000u) return static_cast<uint16_t>(u >> 16);  // inf / nan: not expected
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return static_cast<uint16_t>(u >> 16);
+}
+
+static double bf16_to_double(uint16_t h) {
+    const uint32_t u = static_cast<uint32_t>(h) << 16;
+    float f;
+    std::memcpy(&f, &u, sizeof f);
+    return f;
+}
+
+std::vector<uint16_t> bf16_split_operator(const std::vector<double>& B, int n, int npad) {
+    const size_t chunk = static_cast<size_t>(8) * npad + 8, part = static_cast<size_t>(npad / 8) * chunk;
+    std::vector<uint16_t> out(3 * part, 0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            double r = B[static_cast<size_t>(i) * n + k];
+            for (int q = 0; q < 3; ++q) {
+                const uint16_t h = bf16_nearest(static_cast<float>(r));
+                out[q * part + (k / 8) * chunk + static_cast<size_t>(8) * i + k % 8] = h;
+                r -= bf16_to_double(h);  // exact: r and h agree in their leading bits
+            }
+        }
+    return out;
 }
 
 }  // namespace smx

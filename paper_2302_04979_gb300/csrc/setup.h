@@ -52,4 +52,11 @@ std::vector<double> band_lu_dense(const BandLU& f);
 // int_e phi_i phi_j with q = p+1 Gauss points.
 std::vector<double> element_mass(int kind, int p, int nel, int e);
 
+// Three-term BF16 split of a dense n x n row-major FP64 operator B,
+// B ~= B0 + B1 + B2 (each remainder taken exactly in FP64), laid out for the
+// tensor-core mode products: part q, element (row i, column k) at uint16 index
+//   q * (npad / 8) * (8 npad + 8) + (k / 8) * (8 npad + 8) + 8 i + k % 8,
+// zero outside n x n (npad a multiple of 16, >= n).
+std::vector<uint16_t> bf16_split_operator(const std::vector<double>& B, int n, int npad);
+
 }  // namespace smx

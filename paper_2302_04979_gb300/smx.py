@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libsmx.so")
 
 # ---- constants mirrored from include/smx.h
 OK, EINVAL, EGEOM, EMAT, ECUDA, ENONFINITE, ESTATE, ENOMEM, ESINGULAR, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+ETIMEOUT = -10
+MODE_TENSOR, MODE_SIMT = 0, 1
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 MAT_CONST, MAT_BLOCKS, MAT_POINTWISE = 0, 1, 2
 FIELD_E, FIELD_B, FIELD_H, FIELD_D = 0, 1, 2, 3
@@ -54,6 +56,9 @@ _SIGS = {
     "smx_bind_workspace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "smx_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
     "smx_set_graphs": [ctypes.c_void_p, ctypes.c_int],
+    "smx_set_mode_kernel": [ctypes.c_void_p, ctypes.c_int],
+    "smx_device_status": [ctypes.c_void_p],
+    "smx_hodge_star_mixed": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_curl_primal": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
     "smx_curl_dual": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                       ctypes.c_double],
@@ -77,11 +82,11 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)],
 }
 
-NCLASS = 18
+NCLASS = 19
 KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
                   "reduction", "mass_solve_x", "mass_solve_y", "mass_solve_z",
                   "curl_primal_f32", "curl_dual_f32", "hodge_block_f32", "line_f32_x", "line_f32_y", "line_f32_z",
-                  "cast")
+                  "cast", "hodge_quad_f32")
 
 
 def _lib():
@@ -208,6 +213,15 @@ class Context:
     def set_graphs(self, on):
         _check(_lib().smx_set_graphs(self.h, 1 if on else 0), "smx_set_graphs")
 
+    def set_mode_kernel(self, which):
+        """Dense line operators of the mixed step on "tensor" cores (default) or FP32 "simt" cores."""
+        _check(_lib().smx_set_mode_kernel(self.h, {"tensor": MODE_TENSOR, "simt": MODE_SIMT}[which]),
+               "smx_set_mode_kernel")
+
+    def device_status(self):
+        """Synchronise; raise SmxError(ETIMEOUT) if a bounded device-side wait gave up since the last call."""
+        _check(_lib().smx_device_status(self.h), "smx_device_status")
+
     def factor_matrix(self, axis, which):
         n = ctypes.c_int64()
         _check(_lib().smx_factor_matrix(self.h, axis, which, ctypes.byref(n), None), "smx_factor_matrix")
@@ -236,6 +250,10 @@ class Context:
 
     def hodge_star(self, field, x, out):
         _check(_lib().smx_hodge_star(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star")
+
+    def hodge_star_mixed(self, field, x, out):
+        """The mixed step's FP32 Hodge star on its own (context created with precision="mixed")."""
+        _check(_lib().smx_hodge_star_mixed(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star_mixed")
 
     def hodge_star_noalloc(self, field, x, out):
         """hodge_star without a bound workspace: tables and scratch in the library's fixed device array."""

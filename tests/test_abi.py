@@ -89,3 +89,13 @@ def test_calls_without_workspace_are_rejected(smx):
     assert lib.smx_bind_workspace(ctx.h, ctypes.c_void_p(256), 16) == smx.ESTATE
     assert lib.smx_bind_workspace(ctx.h, None, 1 << 30) == smx.EINVAL
     assert lib.smx_strerror(smx.EGEOM).startswith(b"geometry")
+    assert lib.smx_device_status(ctx.h) == smx.ESTATE
+    assert lib.smx_hodge_star_mixed(ctx.h, smx.FIELD_D, ctypes.c_void_p(8), ctypes.c_void_p(16)) == smx.ESTATE
+    assert lib.smx_strerror(smx.ETIMEOUT).startswith(b"a device-side wait")
+
+
+def test_mode_kernel_selection(smx):
+    ctx = smx.Context(3, 4, precision="mixed")
+    ctx.set_mode_kernel("simt")
+    ctx.set_mode_kernel("tensor")
+    assert smx.library().smx_set_mode_kernel(ctx.h, 7) == smx.EINVAL

@@ -8,6 +8,7 @@ and asserted against that bound.
 import numpy as np
 import pytest
 
+from oracle import hodge
 from oracle import maxwell as mx
 from paper_2302_04979_gb300 import synth
 from tests.gpu_util import rel_l2, to_dev, to_host
@@ -24,11 +25,26 @@ CASES = {
     # lines longer than the dense mode-product limit (80): the banded FP32 line recurrences run instead
     "p2_long_lines": dict(p=2, nel=(90, 4, 3), eps=("blocks", synth.block_material(6, (3, 2, 1), 1.0, 4.0)),
                           steps=40, init="random"),
+    # curved map and pointwise material: the FP32 quadrature Hodge
+    "p3_curved_bumps": dict(p=3, nel=(6, 5, 7), geometry="sine_bump", eps=synth.GaussianBumps(5), steps=40,
+                            init="random"),
+    "p2_pointwise": dict(p=2, nel=(7, 6, 5), eps=lambda x, y, z: 1.0 + x + 0.5 * y * z,
+                         mu=lambda x, y, z: 2.0 - 0.5 * z, steps=40, init="random"),
 }
 
 
+def _scheme(case):
+    geom = hodge.SineBumpMap(0.05) if case.get("geometry") == "sine_bump" else hodge.IdentityMap()
+    return mx.Scheme2(case["p"], case["nel"], geometry=geom, eps=case.get("eps", 1.0), mu=case.get("mu", 1.0))
+
+
+def _context(smx, case):
+    return smx.Context(case["p"], case["nel"], geometry=case.get("geometry", "identity"), eps=case.get("eps", 1.0),
+                       mu=case.get("mu", 1.0), precision="mixed").bind()
+
+
 def _setup(case):
-    S = mx.Scheme2(case["p"], case["nel"], eps=case.get("eps", 1.0), mu=case.get("mu", 1.0))
+    S = _scheme(case)
     if case["init"] == "te111":
         d = S.project_2form("D", mx.te111_E(0.0))
         b = np.zeros(S.N_h)
@@ -40,34 +56,89 @@ def _setup(case):
     return S, d, b, e, dt
 
 
+KERNELS = ("tensor", "simt")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_mixed_against_oracle(name):
+def test_mixed_against_oracle(name, kernel):
     import torch
     from paper_2302_04979_gb300 import smx
     case = CASES[name]
     S, d, b, e, dt = _setup(case)
     n = case["steps"]
     ref = S.step(d, b, e, dt, n)
-    ctx = smx.Context(case["p"], case["nel"], eps=case.get("eps", 1.0), mu=case.get("mu", 1.0),
-                      precision="mixed").bind()
+    ctx = _context(smx, case)
+    ctx.set_mode_kernel(kernel)
     dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
     hd = torch.zeros(S.N_h, dtype=torch.float64, device="cuda")
     ctx.step(dd, bd, ed, hd, dt, n)
+    ctx.device_status()
     errs = [rel_l2(to_host(g), w) for g, w in zip((dd, bd, ed, hd), ref)]
     W0 = S.energy(d, b, e, dt)[1]
     W1 = S.energy(to_host(dd), to_host(bd), to_host(ed), dt)[1]
-    print("\n%s mixed after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W drift %.2e"
-          % (name, n, *errs, abs(W1 - W0) / W0))
+    print("\n%s mixed (%s) after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W drift %.2e"
+          % (name, kernel, n, *errs, abs(W1 - W0) / W0))
     assert max(errs) < 1e-5
     assert abs(W1 - W0) / W0 < 1e-5
 
 
-def test_mixed_rejects_unsupported():
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_hodge_star_against_oracle(name, kernel):
+    """One mixed-precision Hodge star (K_1^{-1} M~ d and K~_1^{-1} M b) against the oracle's FP64 one.
+
+    Every stage rounds its data to FP32 once (the operators carry FP64 accuracy in
+    their split terms), so one star stays within a few FP32 roundings: 2e-6."""
+    import torch
     from paper_2302_04979_gb300 import smx
-    with pytest.raises(smx.SmxError):
-        smx.Context(3, 4, geometry="sine_bump", precision="mixed")
-    with pytest.raises(smx.SmxError):
-        smx.Context(3, 4, eps=lambda x, y, z: 1.0 + x, precision="mixed")
+    case = CASES[name]
+    S = _scheme(case)
+    d = synth.uniform(80, S.N_e, -1.0, 1.0)
+    b = synth.uniform(81, S.N_h, -1.0, 1.0)
+    ctx = _context(smx, case)
+    ctx.set_mode_kernel(kernel)
+    e_dev = torch.empty(S.N_e, dtype=torch.float64, device="cuda")
+    h_dev = torch.empty(S.N_h, dtype=torch.float64, device="cuda")
+    ctx.hodge_star_mixed(smx.FIELD_D, to_dev(d), e_dev)
+    ctx.hodge_star_mixed(smx.FIELD_B, to_dev(b), h_dev)
+    ctx.device_status()
+    ee, eh = rel_l2(to_host(e_dev), S.e_from_d(d)), rel_l2(to_host(h_dev), S.h_from_b(b))
+    print("\n%s mixed star (%s): rel L2 e %.2e h %.2e" % (name, kernel, ee, eh))
+    assert ee < 2e-6 and eh < 2e-6
+
+
+def test_mixed_kernels_agree_at_64cube():
+    """The benchmark workload's mixed Hodge stars: tensor-core and FP32 CUDA-core kernels agree to FP32 rounding."""
+    import torch
+    from paper_2302_04979_gb300 import smx
+    eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
+    ctx = smx.Context(3, 64, eps=eps, precision="mixed").bind()
+    d = to_dev(synth.uniform(82, ctx.N_e, -1.0, 1.0))
+    b = to_dev(synth.uniform(83, ctx.N_h, -1.0, 1.0))
+    out = {}
+    for kernel in KERNELS:
+        ctx.set_mode_kernel(kernel)
+        e = torch.empty(ctx.N_e, dtype=torch.float64, device="cuda")
+        h = torch.empty(ctx.N_h, dtype=torch.float64, device="cuda")
+        ctx.hodge_star_mixed(smx.FIELD_D, d, e)
+        ctx.hodge_star_mixed(smx.FIELD_B, b, h)
+        ctx.device_status()
+        out[kernel] = (to_host(e), to_host(h))
+    de = rel_l2(out["tensor"][0], out["simt"][0])
+    dh = rel_l2(out["tensor"][1], out["simt"][1])
+    print("\n64^3 mixed star, tensor vs simt: rel L2 e %.2e h %.2e" % (de, dh))
+    assert de < 1e-6 and dh < 1e-6
+
+
+def test_mixed_star_requires_mixed_context():
+    import torch
+    from paper_2302_04979_gb300 import smx
+    ctx = smx.Context(2, 4).bind()
+    x = torch.zeros(ctx.N_e, dtype=torch.float64, device="cuda")
+    with pytest.raises(smx.SmxError) as ei:
+        ctx.hodge_star_mixed(smx.FIELD_D, x, x.clone())
+    assert ei.value.status == smx.ESTATE
 
 
 @pytest.mark.slow
