@@ -226,9 +226,10 @@ int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
  *   8/9/10 fused mass + solve along x/y/z (separable Hodge star),
  *   11 curl_primal and 12 curl_dual of the mixed step (FP32 differences),
  *   13 FP32 block Hodge, 14/15/16 FP32 line passes along x/y/z, 17 casts,
- *   18 FP32 quadrature Hodge.
+ *   18 FP32 quadrature Hodge, 19 per-block mass derivative (reverse step),
+ *   20 receivers and small vector updates.
  * ms[SMX_NCLASS] receives milliseconds, counts[SMX_NCLASS] launches per class. */
-#define SMX_NCLASS 19
+#define SMX_NCLASS 21
 int smx_launch_count(const smx_ctx* ctx, int64_t* n);
 int smx_set_timing(smx_ctx* ctx, int enable);
 int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);
@@ -295,6 +296,95 @@ int smx_hodge_mode(const smx_ctx* ctx, int field, int* mode);
  * arrays).  Errors: SMX_EINVAL, SMX_ESTATE (no workspace, or the context is
  * not SMX_MIXED), SMX_ECUDA. */
 int smx_hodge_star_mixed(smx_ctx* ctx, int field, const double* x, double* out);
+
+/* ==== Reverse mode: gradient of a receiver misfit ====
+ * The paper defines the forward leapfrog only; these calls give the exact
+ * derivative of a loss of that discrete forward map (its discrete adjoint),
+ * with respect to the permittivity given on a block grid (SMX_MAT_BLOCKS)
+ * and to the source amplitudes.  One forward step (Sec. 4.2 / Sec. 5,
+ * kick-drift-kick, S_E = K_1^{-1} M~^2_{1/eps}, S_H = K~_1^{-1} M^2_{1/mu},
+ * a = dt/2):
+ *   b' = b_n - a D^1 S_E d_n,  d_{n+1} = d_n + dt (D~^1 S_H b' - s_n jhat),
+ *   b_{n+1} = b' - a D^1 S_E d_{n+1}.
+ * Its transpose uses D~^1 = (D^1)^T, the pairing sweeps with the transposed
+ * 1D factors (K_1^{-T}, K~_1^{-T}) and the symmetric masses.  FP64 contexts
+ * only (SMX_ESTATE otherwise). */
+
+/* Receiver points for a misfit: R maps e (N_e) to the three parametric
+ * components of the discrete electric 1-form (basis of X^1_{h,0}, Sec. 2.3)
+ * at n points xhat (host, n x 3, x fastest, in [0,1]); row 3 r + c.  Must be
+ * called before smx_bind_workspace (the table is part of the workspace).
+ * Errors: SMX_EINVAL, SMX_ESTATE (already bound or already set). */
+int smx_receivers_set(smx_ctx* ctx, int n, const double* xhat);
+
+/* out (device, 3n) = R e (device, N_e).  Errors: SMX_EINVAL (no receivers), SMX_ECUDA. */
+int smx_receivers_eval(smx_ctx* ctx, const double* e, double* out);
+
+/* ebar (device, N_e) += alpha R^T w (w device, 3n). */
+int smx_receivers_adjoint(smx_ctx* ctx, const double* w, double alpha, double* ebar);
+
+/* New permittivity values on the context's block grid (host, b_x b_y b_z
+ * values, x fastest; field must be SMX_FIELD_D and the context created with
+ * SMX_MAT_BLOCKS eps).  Updates the device Hodge tables in place (the block
+ * Kronecker tile weights, or the quadrature metric scaled block by block) and
+ * synchronises.  Errors: SMX_EINVAL, SMX_EMAT (value not finite and positive). */
+int smx_set_material_blocks(smx_ctx* ctx, int field, const double* values);
+
+/* One reverse step n+1 -> n.  In: the forward states d_n, d_{n+1} (device,
+ * N_e), the adjoints dbar = dL/dd_{n+1} (N_e), bbar = dL/db_{n+1} (N_h);
+ * ebar (device N_e or NULL): the loss's derivative with respect to e_n =
+ * S_E d_n (for a misfit 1/2 dt sum |R e_n - y_n|^2: dt R^T (R e_n - y_n));
+ * jhat (device N_e or NULL).  Out: dbar, bbar overwritten with dL/dd_n,
+ * dL/db_n; amp_bar (device, 1 value, if jhat): dL/ds_n; eps_bar (device, one
+ * value per permittivity block, or NULL): += the step's dL/deps.
+ * Asynchronous on the context stream. */
+int smx_step_adjoint(smx_ctx* ctx, const double* d_n, const double* d_np1, double* dbar, double* bbar,
+                     const double* ebar, const double* jhat, double dt, double* amp_bar, double* eps_bar);
+
+/* Start of the reverse sweep at the last step N: dbar = S_E^T ebar_N (bbar_N
+ * is zero), eps_bar += the eps derivative of ebar_N^T S_E d_N. */
+int smx_adjoint_terminal(smx_ctx* ctx, const double* d_N, const double* ebar, double* dbar, double* eps_bar);
+
+/* ==== Batched cavities: one persistent launch per leapfrog step ====
+ * Many independent cavities (each its own bound FP64 context: identity map,
+ * constant mu, block or constant eps; any p and nel) stepped together: one
+ * cooperative launch per step runs the ten phases of the kick-drift-kick
+ * step (the same device code as smx_step) over a flat work list of
+ * (cavity, unit) items, with grid barriers between phases.  Each barrier wait
+ * is bounded (one second); see smx_batch_status. */
+typedef struct smx_batch smx_batch;
+
+/* Build a batch over n bound contexts (host arrays; the contexts must outlive
+ * the batch and share one stream, that of ctxs[0]).  Host memory only.
+ * Errors: SMX_EINVAL (a context is unbound, mixed precision, curved, or has
+ * non-constant mu or quadrature-mode eps), SMX_ENOMEM. */
+int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out);
+int smx_batch_destroy(smx_batch* batch);
+
+/* Device workspace of the batch (cavity table, work lists, barrier words),
+ * caller-allocated as for a context; binding uploads the work lists and picks
+ * a default shape (line warps per CTA) that fits shared memory. */
+int smx_batch_workspace_bytes(const smx_batch* batch, size_t* bytes);
+int smx_batch_bind_workspace(smx_batch* batch, void* device_ptr, size_t bytes);
+
+/* State of cavity i: device arrays d, b, e (consistent: e = K_1^{-1} M~ d), h
+ * as for smx_step, optional source jhat with one amplitude per step in amp
+ * (device), and the cavity's own dt.  Resets the step counter (amp index). */
+int smx_batch_set_state(smx_batch* batch, int i, double* d, double* b, double* e, double* h, const double* jhat,
+                        const double* amp, double dt);
+
+/* nsteps leapfrog steps of every cavity: nsteps launches on the stream. */
+int smx_batch_step(smx_batch* batch, int nsteps);
+
+/* Synchronise; SMX_ETIMEOUT if a grid barrier gave up since the last call
+ * (the results of that launch are not valid), else SMX_OK. */
+int smx_batch_status(smx_batch* batch);
+
+/* Autotuner: times `steps` launches for each candidate shape (1, 2, 4, 8
+ * line warps per CTA, as shared memory allows) on the contexts' own state
+ * vectors (zero fields; the user's state is untouched) and keeps the fastest;
+ * *line_warps (optional) receives the choice. */
+int smx_batch_autotune(smx_batch* batch, int steps, int* line_warps);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@ struct HodgeHost {
     std::vector<int> tf0[3], tlen[3];
     std::vector<double> tmat[3];
     std::vector<double> gamma;
+    std::vector<int> tile_block;  // block material: the block of each tile
     // quadrature mode
     int q[3] = {0, 0, 0};
     std::vector<double> bval[3];
@@ -123,11 +124,22 @@ struct smx_ctx {
     size_t o_mode32[2][3][3];
     ModeF32Args md32[2][3];  // [field][axis]
     // the same operators as three BF16 parts for the tensor-core kernel (the default)
-    int mode_kernel = SMX_MODE_TENSOR;
+    int mode_kernel = SMX_MODE_SIMT;
     size_t o_modetc[2][3][3];
     ModeTcArgs mtc[2][3];
     size_t o_status = 0;          // device status word (bit 0: a tensor-core wait gave up)
     unsigned* status = nullptr;
+    // reverse step: transposed pairing sweeps, block permittivity, receivers
+    SolveArgs solveT[2][3];       // [K_1^T, K~_1^T][axis]
+    bool eps_blocks = false;      // eps given on a block grid: gradients and updates available
+    int eps_nb[3] = {0, 0, 0}, eps_epb[3] = {0, 0, 0};
+    std::vector<double> eps_vals;  // current block values (x fastest)
+    size_t o_pair_scale = 0, o_tile_block = 0;
+    PairArgs pair{};
+    std::vector<int> rec_ptr, rec_idx;
+    std::vector<double> rec_val;
+    size_t o_rec_ptr = 0, o_rec_idx = 0, o_rec_val = 0;
+    RecArgs rec{};
 };
 
 namespace {
@@ -241,7 +253,9 @@ int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
                     const int t3[3] = {tx, ty, tz};
                     int b3[3];
                     for (int a = 0; a < 3; ++a) b3[a] = bounds[a][t3[a]] / (C->nel[a] / m.blocks[a]);
-                    v = m.block_values[(b3[2] * m.blocks[1] + b3[1]) * m.blocks[0] + b3[0]];
+                    const int blk = (b3[2] * m.blocks[1] + b3[1]) * m.blocks[0] + b3[0];
+                    v = m.block_values[blk];
+                    H.tile_block.push_back(blk);
                 }
                 H.gamma[((size_t)tz * H.ntile[1] + ty) * H.ntile[0] + tx] = 1.0 / v;
             }
@@ -420,6 +434,27 @@ int factor_index(int which, int c, int a) {
     return row_kind == P0 ? 2 : 3;
 }
 
+// Workspace layout: the tables (blob), then scratch, reduction, status,
+// state and (mixed form) FP32 vectors, each 256-byte aligned.
+void layout(smx_ctx* C) {
+    C->tables_bytes = (C->blob.bytes.size() + 255) & ~size_t(255);
+    C->o_scratch = C->tables_bytes;
+    const size_t nmax = (size_t)std::max(C->N_e, C->N_h);
+    C->o_scratch2 = C->o_scratch + ((nmax * sizeof(double) + 255) & ~size_t(255));
+    C->o_partial = C->o_scratch2 + ((nmax * sizeof(double) + 255) & ~size_t(255));
+    C->o_dots = C->o_partial + ((kDotBlocks * sizeof(double) + 255) & ~size_t(255));
+    C->o_status = C->o_dots + 256;
+    C->o_state = C->o_status + 256;
+    C->total_bytes = C->o_state + ((2 * (size_t)(C->N_e + C->N_h) * sizeof(double) + 255) & ~size_t(255));
+    if (C->precision == SMX_MIXED) {
+        auto f32 = [](long long n) { return ((size_t)n * sizeof(float) + 255) & ~size_t(255); };
+        C->o_e32 = C->total_bytes;
+        C->o_h32 = C->o_e32 + f32(C->N_e);
+        C->o_y32 = C->o_h32 + f32(C->N_h);
+        C->total_bytes = C->o_y32 + f32((long long)nmax);
+    }
+}
+
 #define CK(call)                                          \
     do {                                                  \
         cudaError_t err_ = (call);                        \
@@ -478,18 +513,43 @@ int dot_impl(smx_ctx* C, const double* x, const double* y, long long n, int slot
     return run(C, 7, 2, [&] { return launch_dot(x, y, n, C->partial, C->dots + slot, C->stream); });
 }
 
+// ---- reverse step helpers
+// y += M x (the Hodge kernels scatter with atomics, so no zeroing means accumulation)
+int hodge_apply_acc_impl(smx_ctx* C, int h, const double* x, double* y) {
+    if (C->hodge[h].mode == 0) return run(C, 2, 1, [&] { return launch_hodge_block(C->hb[h], x, y, C->stream); });
+    return run(C, 3, 1, [&] { return launch_hodge_quad(C->hq[h], x, y, C->stream); });
+}
+
+// x = K^{-T} y: the pairing sweeps with the transposed 1D factors
+int solveT_impl(smx_ctx* C, int which, const double* y, double* x) {
+    int st = run(C, 4, 1, [&] { return launch_solve_axis(C->solveT[which][0], C->p[0] - 1, y, x, C->stream); });
+    if (st) return st;
+    st = run(C, 5, 1, [&] { return launch_solve_axis(C->solveT[which][1], C->p[1] - 1, x, x, C->stream); });
+    if (st) return st;
+    return run(C, 6, 1, [&] { return launch_solve_axis(C->solveT[which][2], C->p[2] - 1, x, x, C->stream); });
+}
+
+// out[c] += z^T (dM~/deps_c) d for every permittivity block c
+int pair_impl(smx_ctx* C, const double* z, const double* d, double* out) {
+    if (C->hodge[1].mode == 0)
+        return run(C, 19, 1, [&] { return launch_hodge_block_pair(C->hb[1], C->pair, z, d, out, C->stream); });
+    return run(C, 19, 1, [&] { return launch_hodge_quad_pair(C->hq[1], C->pair, z, d, out, C->stream); });
+}
+
 // ---- mixed precision: FP32 operators on the FP64 state
 // FP32 Hodge star from the FP64 2-form x into out (h = 0: h32 = K~_1^{-1} M^2 b;
 // h = 1: e32 = K_1^{-1} M~^2 d), same algorithms as the FP64 path.  out64
 // (optional) also receives the result widened to FP64: written by the last
 // tensor-core sweep itself, else by a cast kernel.
-// y32 = M x in FP32 (block-Kronecker or quadrature Hodge, by the field's mode).
+// scratch = M x: FP32 element (or tile) contributions, summed in FP64 -- with up to
+// (p+1)^3 contributions per coefficient an FP32 sum would lose accuracy where
+// they cancel (block-Kronecker or quadrature Hodge, by the field's mode).
 int mass_f32(smx_ctx* C, int h, const double* x) {
     const long long ntot = C->fld[kFieldOfHodge[h]].total;
-    CK(cudaMemsetAsync(C->y32, 0, (size_t)ntot * sizeof(float), C->stream));
+    CK(cudaMemsetAsync(C->scratch, 0, (size_t)ntot * sizeof(double), C->stream));
     if (C->hodge[h].mode == 1)
-        return run(C, 18, 1, [&] { return launch_hodge_quad_f32(C->hq32[h], x, C->y32, C->stream); });
-    return run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->y32, C->stream); });
+        return run(C, 18, 1, [&] { return launch_hodge_quad_f32(C->hq32[h], x, C->scratch, C->stream); });
+    return run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->scratch, C->stream); });
 }
 
 int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* out64 = nullptr) {
@@ -504,8 +564,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         const float* x32 = nullptr;
         if (!C->hodge[h].separable) {
             if ((st = mass_f32(C, h, x))) return st;
-            x64 = nullptr;
-            x32 = C->y32;
+            x64 = C->scratch;
         }
         const bool tc = C->mode_kernel == SMX_MODE_TENSOR;
         auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
@@ -528,7 +587,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         return st ? st : widen();
     }
     if ((st = mass_f32(C, h, x))) return st;
-    st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, false, nullptr, C->y32, out, C->stream); });
+    st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, false, C->scratch, nullptr, out, C->stream); });
     if (st) return st;
     st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, false, nullptr, out, out, C->stream); });
     if (st) return st;
@@ -637,6 +696,15 @@ int smx_create(const smx_params* P, smx_ctx** out) {
         }
         C->geometry = P->geometry;
         C->amp = P->geom_amplitude;
+        if (P->eps.kind == SMX_MAT_BLOCKS) {
+            C->eps_blocks = true;
+            for (int a = 0; a < 3; ++a) {
+                C->eps_nb[a] = P->eps.blocks[a];
+                C->eps_epb[a] = P->nel[a] / P->eps.blocks[a];
+            }
+            C->eps_vals.assign(P->eps.block_values,
+                               P->eps.block_values + (size_t)C->eps_nb[0] * C->eps_nb[1] * C->eps_nb[2]);
+        }
         for (int f = 0; f < 4; ++f) {
             long long off = 0;
             for (int c = 0; c < 3; ++c) {
@@ -708,10 +776,9 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             } else {
                 for (int a = 0; a < 3; ++a) H.o_bval[a] = C->blob.add(H.bval[a]);
                 H.o_G = C->blob.add(H.G);
-                if (C->precision == SMX_MIXED) {  // the mixed step's FP32 copies (metric rounded once)
-                    for (int a = 0; a < 3; ++a)
-                        C->o_bval32[h][a] = C->blob.add(std::vector<float>(H.bval[a].begin(), H.bval[a].end()));
-                    C->o_G32[h] = C->blob.add(std::vector<float>(H.G.begin(), H.G.end()));
+                if (C->precision == SMX_MIXED) {  // the mixed step's FP32 (hi, lo) copies
+                    for (int a = 0; a < 3; ++a) C->o_bval32[h][a] = C->blob.add(split_pairs(H.bval[a]));
+                    C->o_G32[h] = C->blob.add(split_pairs(H.G));
                 }
                 H.G.clear();
                 H.G.shrink_to_fit();
@@ -757,22 +824,13 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                 }
             }
         }
-        C->tables_bytes = (C->blob.bytes.size() + 255) & ~size_t(255);
-        C->o_scratch = C->tables_bytes;
-        const size_t nmax = (size_t)std::max(C->N_e, C->N_h);
-        C->o_scratch2 = C->o_scratch + ((nmax * sizeof(double) + 255) & ~size_t(255));
-        C->o_partial = C->o_scratch2 + ((nmax * sizeof(double) + 255) & ~size_t(255));
-        C->o_dots = C->o_partial + ((kDotBlocks * sizeof(double) + 255) & ~size_t(255));
-        C->o_status = C->o_dots + 256;
-        C->o_state = C->o_status + 256;
-        C->total_bytes = C->o_state + ((2 * (size_t)(C->N_e + C->N_h) * sizeof(double) + 255) & ~size_t(255));
-        if (C->precision == SMX_MIXED) {
-            auto f32 = [](long long n) { return ((size_t)n * sizeof(float) + 255) & ~size_t(255); };
-            C->o_e32 = C->total_bytes;
-            C->o_h32 = C->o_e32 + f32(C->N_e);
-            C->o_y32 = C->o_h32 + f32(C->N_h);
-            C->total_bytes = C->o_y32 + f32((long long)nmax);
+        if (C->eps_blocks) {  // per-block scale of the mass derivative (-1/eps) and the tiles' blocks
+            std::vector<double> sc(C->eps_vals.size());
+            for (size_t k = 0; k < sc.size(); ++k) sc[k] = -1.0 / C->eps_vals[k];
+            C->o_pair_scale = C->blob.add(sc);
+            C->o_tile_block = C->blob.add(C->hodge[1].tile_block);
         }
+        layout(C);
     } catch (const std::bad_alloc&) {
         delete C;
         return SMX_ENOMEM;
@@ -836,6 +894,36 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
     C->status = reinterpret_cast<unsigned*>(ws + C->o_status);
     CK(cudaMemsetAsync(C->status, 0, sizeof(unsigned), C->stream));
     C->state = reinterpret_cast<double*>(ws + C->o_state);
+    // transposed pairing sweeps (reverse step): K_1^T uses G^T, M^T in the D layout, K~_1^T uses G, M
+    for (int which = 0; which < 2; ++which) {
+        const int fld = which == 0 ? SMX_FIELD_D : SMX_FIELD_B;
+        for (int a = 0; a < 3; ++a) {
+            SolveArgs& S = C->solveT[which][a];
+            S.field = C->fld[fld];
+            S.axis = a;
+            for (int c = 0; c < 3; ++c) {
+                const int w = factor_index(which, c, a) ^ 2;  // 0 <-> 2 (G, G^T), 1 <-> 3 (M, M^T)
+                S.f[c].L = reinterpret_cast<const double*>(ws + C->o_fac[a][w][0]);
+                S.f[c].U = reinterpret_cast<const double*>(ws + C->o_fac[a][w][1]);
+                S.f[c].dinv = reinterpret_cast<const double*>(ws + C->o_fac[a][w][2]);
+                S.f[c].n = C->fac[a][w].n;
+            }
+        }
+    }
+    if (C->eps_blocks) {
+        C->pair.scale = reinterpret_cast<const double*>(ws + C->o_pair_scale);
+        C->pair.tile_block = reinterpret_cast<const int*>(ws + C->o_tile_block);
+        for (int a = 0; a < 3; ++a) {
+            C->pair.epb[a] = C->eps_epb[a];
+            C->pair.nb[a] = C->eps_nb[a];
+        }
+    }
+    if (!C->rec_ptr.empty()) {
+        C->rec.ptr = reinterpret_cast<const int*>(ws + C->o_rec_ptr);
+        C->rec.idx = reinterpret_cast<const int*>(ws + C->o_rec_idx);
+        C->rec.val = reinterpret_cast<const double*>(ws + C->o_rec_val);
+        C->rec.nrows = (int)C->rec_ptr.size() - 1;
+    }
     // pairing sweeps
     for (int which = 0; which < 2; ++which) {
         const int fld = which == 0 ? SMX_FIELD_D : SMX_FIELD_B;
@@ -920,14 +1008,14 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                     Q.nel[a] = Q64.nel[a];
                     Q.q[a] = Q64.q[a];
                     Q.Qn[a] = Q64.Qn[a];
-                    Q.bval[a] = reinterpret_cast<const float*>(ws + C->o_bval32[h][a]);
+                    Q.bval[a] = reinterpret_cast<const float2*>(ws + C->o_bval32[h][a]);
                     for (int c = 0; c < 3; ++c) {
                         Q.kinds[a][c] = Q64.kinds[a][c];
                         Q.deg[a][c] = Q64.deg[a][c];
                         Q.koff[a][c] = Q64.koff[a][c];
                     }
                 }
-                Q.G = reinterpret_cast<const float*>(ws + C->o_G32[h]);
+                Q.G = reinterpret_cast<const float2*>(ws + C->o_G32[h]);
                 Q.Qtot = Q64.Qtot;
             }
             HodgeBlockF32Args& B = C->hb32[h];
@@ -1313,6 +1401,409 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
         default:
             return SMX_EINVAL;
     }
+}
+
+// ---- reverse step, receivers, block material updates
+int smx_receivers_set(smx_ctx* C, int n, const double* xhat) {
+    if (!C || n < 0 || (n > 0 && !xhat)) return SMX_EINVAL;
+    if (C->ws) return SMX_ESTATE;  // the receiver table is part of the workspace layout
+    if (!C->rec_ptr.empty()) return SMX_ESTATE;
+    for (int k = 0; k < 3 * n; ++k)
+        if (!(xhat[k] >= 0.0 && xhat[k] <= 1.0)) return SMX_EINVAL;
+    try {
+        std::vector<int> ptr(1, 0), idx;
+        std::vector<double> val;
+        const DevField& E = C->fld[SMX_FIELD_E];
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < 3; ++c) {
+                // the component's basis along each axis at the point: the d+1 functions of its element
+                double v[3][16];
+                int i0[3], dim[3], deg[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int kind = kFieldKinds[SMX_FIELD_E][c][a], nel = C->nel[a];
+                    const double x = xhat[3 * r + a];
+                    const int e = std::min(nel - 1, (int)(x * nel));
+                    local_basis(kind, C->p[a], nel, e, x, v[a]);
+                    i0[a] = e + kind_offset(kind);
+                    dim[a] = kind_dim(kind, C->p[a], nel);
+                    deg[a] = kind_degree(kind, C->p[a]);
+                }
+                for (int k = 0; k <= deg[2]; ++k)
+                    for (int j = 0; j <= deg[1]; ++j)
+                        for (int i = 0; i <= deg[0]; ++i) {
+                            const int gi = i0[0] + i, gj = i0[1] + j, gk = i0[2] + k;
+                            if (gi < 0 || gi >= dim[0] || gj < 0 || gj >= dim[1] || gk < 0 || gk >= dim[2]) continue;
+                            const double w = v[0][i] * v[1][j] * v[2][k];
+                            if (w == 0.0) continue;
+                            idx.push_back((int)(E.c[c].off + gi + (long long)E.c[c].n[0] * (gj + (long long)E.c[c].n[1] * gk)));
+                            val.push_back(w);
+                        }
+                ptr.push_back((int)idx.size());
+            }
+        if (idx.empty()) {  // keep the tables non-empty
+            idx.push_back(0);
+            val.push_back(0.0);
+        }
+        C->rec_ptr = ptr;
+        C->rec_idx = idx;
+        C->rec_val = val;
+        C->o_rec_ptr = C->blob.add(C->rec_ptr);
+        C->o_rec_idx = C->blob.add(C->rec_idx);
+        C->o_rec_val = C->blob.add(C->rec_val);
+        layout(C);
+    } catch (const std::bad_alloc&) {
+        return SMX_ENOMEM;
+    }
+    return SMX_OK;
+}
+
+int smx_receivers_eval(smx_ctx* C, const double* e, double* out) {
+    NEED_WS(C);
+    if (!e || !out || C->rec_ptr.empty()) return SMX_EINVAL;
+    return run(C, 20, 1, [&] { return launch_receivers_eval(C->rec, e, out, C->stream); });
+}
+
+int smx_receivers_adjoint(smx_ctx* C, const double* w, double alpha, double* ebar) {
+    NEED_WS(C);
+    if (!w || !ebar || C->rec_ptr.empty() || !std::isfinite(alpha)) return SMX_EINVAL;
+    return run(C, 20, 1, [&] { return launch_receivers_adjoint(C->rec, w, alpha, ebar, C->stream); });
+}
+
+int smx_set_material_blocks(smx_ctx* C, int field, const double* values) {
+    NEED_WS(C);
+    if (field != SMX_FIELD_D || !values || !C->eps_blocks) return SMX_EINVAL;
+    const size_t nb = C->eps_vals.size();
+    for (size_t k = 0; k < nb; ++k)
+        if (!finite_pos(values[k])) return SMX_EMAT;
+    HodgeHost& H = C->hodge[1];
+    std::vector<double> scale(nb);
+    for (size_t k = 0; k < nb; ++k) scale[k] = -1.0 / values[k];
+    if (H.mode == 0) {
+        for (size_t t = 0; t < H.gamma.size(); ++t) H.gamma[t] = 1.0 / values[H.tile_block[t]];
+        CK(cudaMemcpyAsync(C->ws + H.o_gamma, H.gamma.data(), H.gamma.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           C->stream));
+    } else {
+        // the stored metric carries gamma = 1/eps: scale each block's points by eps_old / eps_new
+        std::vector<double> ratio(nb);
+        for (size_t k = 0; k < nb; ++k) ratio[k] = C->eps_vals[k] / values[k];
+        CK(cudaMemcpyAsync(C->scratch, ratio.data(), nb * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+        float2* g32 = C->precision == SMX_MIXED ? reinterpret_cast<float2*>(C->ws + C->o_G32[1]) : nullptr;
+        CK(launch_rescale_metric(reinterpret_cast<double*>(C->ws + H.o_G), g32, C->hq[1], C->eps_epb, C->eps_nb,
+                                 C->scratch, C->stream));
+    }
+    CK(cudaMemcpyAsync(C->ws + C->o_pair_scale, scale.data(), nb * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    C->eps_vals.assign(values, values + nb);
+    return SMX_OK;
+}
+
+int smx_step_adjoint(smx_ctx* C, const double* d_n, const double* d_np1, double* dbar, double* bbar,
+                     const double* ebar, const double* jhat, double dt, double* amp_bar, double* eps_bar) {
+    NEED_WS(C);
+    if (!d_n || !d_np1 || !dbar || !bbar || !(dt > 0.0) || !std::isfinite(dt)) return SMX_EINVAL;
+    if (C->precision != SMX_FP64) return SMX_ESTATE;
+    if (eps_bar && !C->eps_blocks) return SMX_EINVAL;
+    const double a = 0.5 * dt;
+    double* A1 = C->scratch;
+    double* A2 = C->scratch2;
+    const size_t be = (size_t)C->N_e * sizeof(double), bh = (size_t)C->N_h * sizeof(double);
+    int st;
+    // w = dbar + S_E^T (-a D^1^T bbar), with D^1^T = D~^1; eps pair (z1, d_{n+1})
+    CK(cudaMemsetAsync(A1, 0, be, C->stream));
+    if ((st = curl_dual_impl(C, bbar, A1, -a, nullptr, nullptr, 0, 0.0))) return st;
+    if ((st = solveT_impl(C, 0, A1, A2))) return st;
+    if (eps_bar && (st = pair_impl(C, A2, d_np1, eps_bar))) return st;
+    if ((st = hodge_apply_acc_impl(C, 1, A2, dbar))) return st;
+    // source amplitude: sbar_n = -dt jhat^T w
+    if (jhat && amp_bar) {
+        if ((st = run(C, 7, 2, [&] { return launch_dot(jhat, dbar, C->N_e, C->partial, amp_bar, C->stream); })))
+            return st;
+        if ((st = run(C, 20, 1, [&] { return launch_scale_copy(amp_bar, amp_bar, -dt, 1, C->stream); }))) return st;
+    }
+    // bbar' = bbar + dt S_H^T D~^1^T w, with D~^1^T = D^1
+    CK(cudaMemsetAsync(A1, 0, bh, C->stream));
+    if ((st = curl_primal_impl(C, dbar, A1, dt))) return st;
+    if ((st = solveT_impl(C, 1, A1, A2))) return st;
+    if ((st = hodge_apply_acc_impl(C, 0, A2, bbar))) return st;
+    // dbar_n = w + S_E^T (-a D~^1 bbar' + ebar); eps pair (z3, d_n)
+    CK(cudaMemsetAsync(A1, 0, be, C->stream));
+    if ((st = curl_dual_impl(C, bbar, A1, -a, nullptr, nullptr, 0, 0.0))) return st;
+    if (ebar && (st = run(C, 20, 1, [&] { return launch_axpy(ebar, A1, 1.0, C->N_e, C->stream); }))) return st;
+    if ((st = solveT_impl(C, 0, A1, A2))) return st;
+    if (eps_bar && (st = pair_impl(C, A2, d_n, eps_bar))) return st;
+    return hodge_apply_acc_impl(C, 1, A2, dbar);
+}
+
+int smx_adjoint_terminal(smx_ctx* C, const double* d_N, const double* ebar, double* dbar, double* eps_bar) {
+    NEED_WS(C);
+    if (!d_N || !ebar || !dbar) return SMX_EINVAL;
+    if (C->precision != SMX_FP64) return SMX_ESTATE;
+    if (eps_bar && !C->eps_blocks) return SMX_EINVAL;
+    int st;
+    if ((st = solveT_impl(C, 0, ebar, C->scratch2))) return st;
+    if (eps_bar && (st = pair_impl(C, C->scratch2, d_N, eps_bar))) return st;
+    CK(cudaMemsetAsync(dbar, 0, (size_t)C->N_e * sizeof(double), C->stream));
+    return hodge_apply_acc_impl(C, 1, C->scratch2, dbar);
+}
+
+// ---- batched cavities
+struct smx_batch {
+    std::vector<smx_ctx*> ctx;
+    std::vector<BatchCavity> cav;
+    std::vector<int2> items[kBatchPhases];
+    size_t o_cav = 0, o_items[kBatchPhases] = {}, o_bar = 0, o_status = 0, total = 0;
+    unsigned char* ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int maxn = 0, maxkl = 0, max_nloc = 0;
+    int line_warps = 0, grid = 0;
+    size_t smem = 0;
+    long long steps = 0;  // amplitude index of the next step
+    bool state_set = false;
+};
+
+namespace {
+
+void batch_curl_items(std::vector<int2>& list, int cav, const DevField& out) {
+    int plane = 0, nz = 0;
+    for (int c = 0; c < 3; ++c) {
+        plane = std::max(plane, out.c[c].n[0] * out.c[c].n[1]);
+        nz = std::max(nz, out.c[c].n[2]);
+    }
+    const int pb = (plane + kCurlThreads - 1) / kCurlThreads, zc = (nz + kCurlKz - 1) / kCurlKz;
+    for (int c = 0; c < 3; ++c)
+        for (int z = 0; z < zc; ++z)
+            for (int b = 0; b < pb; ++b) list.push_back(make_int2(cav, batch_curl_unit(c, b, z)));
+}
+
+void batch_line_items(std::vector<int2>& list, int cav, const DevField& f, int axis) {
+    for (int c = 0; c < 3; ++c) {
+        const int n = f.c[c].n[axis];
+        if (n <= 0) continue;
+        const long long lines = (long long)f.c[c].n[0] * f.c[c].n[1] * f.c[c].n[2] / n;
+        for (long long lb = 0; lb < (lines + kSolveLines - 1) / kSolveLines; ++lb)
+            list.push_back(make_int2(cav, batch_comp_unit(c, (int)lb)));
+    }
+}
+
+}  // namespace
+
+int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out) {
+    if (n < 1 || !ctxs || !out) return SMX_EINVAL;
+    *out = nullptr;
+    smx_batch* B = new (std::nothrow) smx_batch();
+    if (!B) return SMX_ENOMEM;
+    try {
+        for (int i = 0; i < n; ++i) {
+            smx_ctx* C = ctxs[i];
+            // identity map, FP64, constant mu (separable star of B), block or constant eps, bound
+            if (!C || !C->ws || C->precision != SMX_FP64 || C->geometry != SMX_GEOM_IDENTITY ||
+                !C->hodge[0].separable || C->hodge[1].mode != 0) {
+                delete B;
+                return SMX_EINVAL;
+            }
+            B->ctx.push_back(C);
+            BatchCavity K{};
+            K.fE = C->fld[SMX_FIELD_E];
+            K.fB = C->fld[SMX_FIELD_B];
+            K.fH = C->fld[SMX_FIELD_H];
+            K.fD = C->fld[SMX_FIELD_D];
+            for (int a = 0; a < 3; ++a) {
+                K.msH[a] = C->ms[0][a];
+                K.msD[a] = C->ms[1][a];
+                K.solveE[a] = C->solve[0][a];
+                K.kl[a] = C->p[a] - 1;
+                B->maxkl = std::max(B->maxkl, C->p[a] - 1);
+                for (int c = 0; c < 3; ++c)
+                    for (int f = 0; f < 4; ++f) B->maxn = std::max(B->maxn, C->fld[f].c[c].n[a]);
+            }
+            K.hbD = C->hb[1];
+            K.sepD = C->hodge[1].separable ? 1 : 0;
+            K.y = C->scratch;
+            B->max_nloc = std::max(B->max_nloc, C->hodge[1].max_nloc);
+            B->cav.push_back(K);
+            batch_curl_items(B->items[0], i, K.fB);
+            for (int a = 0; a < 3; ++a) batch_line_items(B->items[1 + a], i, K.fH, a);
+            batch_curl_items(B->items[4], i, K.fD);
+            if (!K.sepD) {
+                const long long nz = (K.fE.total + kBatchThreads * 8 - 1) / (kBatchThreads * 8);
+                for (long long z = 0; z < nz; ++z) B->items[4].push_back(make_int2(i, batch_zero_unit((int)z)));
+                const HodgeHost& H = C->hodge[1];
+                const int nt = H.ntile[0] * H.ntile[1] * H.ntile[2];
+                for (int c = 0; c < 3; ++c)
+                    for (int t = 0; t < nt; ++t) B->items[5].push_back(make_int2(i, batch_comp_unit(c, t)));
+            }
+            for (int a = 0; a < 3; ++a) batch_line_items(B->items[6 + a], i, K.fD, a);
+            B->items[9] = B->items[0];
+        }
+        // workspace: cavity table, item lists, barrier and status words
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            const size_t o = off;
+            off += (bytes + 255) & ~size_t(255);
+            return o;
+        };
+        B->o_cav = take(B->cav.size() * sizeof(BatchCavity));
+        for (int ph = 0; ph < kBatchPhases; ++ph) B->o_items[ph] = take(std::max<size_t>(1, B->items[ph].size()) * sizeof(int2));
+        B->o_bar = take(2 * sizeof(unsigned));
+        B->o_status = take(sizeof(unsigned));
+        B->total = off;
+    } catch (const std::bad_alloc&) {
+        delete B;
+        return SMX_ENOMEM;
+    }
+    *out = B;
+    return SMX_OK;
+}
+
+int smx_batch_destroy(smx_batch* B) {
+    delete B;
+    return SMX_OK;
+}
+
+int smx_batch_workspace_bytes(const smx_batch* B, size_t* bytes) {
+    if (!B || !bytes) return SMX_EINVAL;
+    *bytes = B->total;
+    return SMX_OK;
+}
+
+static int batch_configure(smx_batch* B, int line_warps) {
+    const size_t warp = batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
+    const size_t hodge = (size_t)3 * kLMax * (kLMax + 1) + 2 * (size_t)B->max_nloc + 8;
+    const size_t smem = std::max(warp * line_warps, hodge) * sizeof(double);
+    if (smem > 226 * 1024) return SMX_EINVAL;
+    const int per_sm = batch_blocks_per_sm(smem);
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return SMX_EINVAL;
+    B->line_warps = line_warps;
+    B->smem = smem;
+    B->grid = per_sm * sms;
+    return SMX_OK;
+}
+
+int smx_batch_bind_workspace(smx_batch* B, void* dev, size_t bytes) {
+    if (!B || !dev) return SMX_EINVAL;
+    if (bytes < B->total || (reinterpret_cast<uintptr_t>(dev) & 255)) return SMX_ESTATE;
+    B->ws = static_cast<unsigned char*>(dev);
+    B->stream = B->ctx[0]->stream;
+    for (int ph = 0; ph < kBatchPhases; ++ph)
+        if (!B->items[ph].empty())
+            CK(cudaMemcpyAsync(B->ws + B->o_items[ph], B->items[ph].data(), B->items[ph].size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, B->stream));
+    CK(cudaMemsetAsync(B->ws + B->o_bar, 0, 2 * sizeof(unsigned) + 256, B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    // default: as many line warps as the shared memory allows, at most 8
+    int lw = 8;
+    while (lw > 1 && batch_configure(B, lw) != SMX_OK) --lw;
+    return batch_configure(B, lw);
+}
+
+int smx_batch_set_state(smx_batch* B, int i, double* d, double* b, double* e, double* h, const double* jhat,
+                        const double* amp, double dt) {
+    if (!B || !B->ws || i < 0 || i >= (int)B->cav.size() || !d || !b || !e || !h) return SMX_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt) || (jhat && !amp)) return SMX_EINVAL;
+    BatchCavity& K = B->cav[i];
+    K.d = d;
+    K.b = b;
+    K.e = e;
+    K.h = h;
+    K.jhat = jhat;
+    K.amp = amp;
+    K.dt = dt;
+    B->state_set = false;
+    B->steps = 0;
+    return SMX_OK;
+}
+
+static int batch_launch(smx_batch* B, int nsteps) {
+    if (!B->state_set) {
+        for (const BatchCavity& K : B->cav)
+            if (!K.d) return SMX_ESTATE;
+        CK(cudaMemcpyAsync(B->ws + B->o_cav, B->cav.data(), B->cav.size() * sizeof(BatchCavity),
+                           cudaMemcpyHostToDevice, B->stream));
+        B->state_set = true;
+    }
+    BatchArgs A{};
+    A.cav = reinterpret_cast<const BatchCavity*>(B->ws + B->o_cav);
+    for (int ph = 0; ph < kBatchPhases; ++ph) {
+        A.items[ph] = reinterpret_cast<const int2*>(B->ws + B->o_items[ph]);
+        A.nitems[ph] = (int)B->items[ph].size();
+    }
+    A.bar = reinterpret_cast<unsigned*>(B->ws + B->o_bar);
+    A.status = reinterpret_cast<unsigned*>(B->ws + B->o_status);
+    A.line_warps = B->line_warps;
+    A.warp_smem = (int)batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
+    for (int n = 0; n < nsteps; ++n) {
+        A.step = (int)B->steps++;
+        CK(launch_batch_step(A, B->grid, B->smem, B->stream));
+    }
+    return SMX_OK;
+}
+
+int smx_batch_step(smx_batch* B, int nsteps) {
+    if (!B || !B->ws || nsteps < 0) return SMX_EINVAL;
+    return batch_launch(B, nsteps);
+}
+
+int smx_batch_status(smx_batch* B) {
+    if (!B || !B->ws) return SMX_EINVAL;
+    unsigned v = 0;
+    CK(cudaMemcpyAsync(&v, B->ws + B->o_status, sizeof v, cudaMemcpyDeviceToHost, B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    if (v == 0) return SMX_OK;
+    CK(cudaMemsetAsync(B->ws + B->o_status, 0, sizeof(unsigned), B->stream));
+    CK(cudaMemsetAsync(B->ws + B->o_bar, 0, 2 * sizeof(unsigned), B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    return SMX_ETIMEOUT;
+}
+
+int smx_batch_autotune(smx_batch* B, int steps, int* line_warps) {
+    if (!B || !B->ws || steps < 1) return SMX_EINVAL;
+    // time each shape on the contexts' own state vectors (zero fields: the work does not depend on the data)
+    std::vector<BatchCavity> saved = B->cav;
+    const long long saved_steps = B->steps;
+    for (size_t i = 0; i < B->cav.size(); ++i) {
+        smx_ctx* C = B->ctx[i];
+        BatchCavity& K = B->cav[i];
+        K.d = C->state;
+        K.e = C->state + C->N_e;
+        K.b = C->state + 2 * C->N_e;
+        K.h = K.b + C->N_h;
+        K.jhat = nullptr;
+        K.amp = nullptr;
+        K.dt = 1e-3;
+        CK(cudaMemsetAsync(C->state, 0, 2 * (size_t)(C->N_e + C->N_h) * sizeof(double), C->stream));
+    }
+    B->state_set = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_lw = B->line_warps;
+    for (int lw = 1; lw <= 8; lw *= 2) {
+        if (batch_configure(B, lw) != SMX_OK) continue;
+        int st = batch_launch(B, 1);  // warm-up
+        if (st) return st;
+        CK(cudaEventRecord(e0, B->stream));
+        if ((st = batch_launch(B, steps))) return st;
+        CK(cudaEventRecord(e1, B->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_lw = lw;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->cav = saved;
+    B->steps = saved_steps;
+    B->state_set = false;
+    const int st = batch_configure(B, best_lw);
+    if (line_warps) *line_warps = best_lw;
+    return st;
 }
 
 int smx_hodge_star_noalloc(smx_ctx* C, int field, const double* x, double* out) {

@@ -21,8 +21,6 @@
 
 namespace smx {
 
-constexpr int kCurlThreads = 256;
-constexpr int kCurlKz = 8;
 
 template <int A, bool DUAL, class T>
 __device__ __forceinline__ T incidence_t(const DevComp& u, const T* __restrict__ v, int i, int j, int k) {

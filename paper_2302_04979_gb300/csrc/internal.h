@@ -13,6 +13,8 @@ constexpr int kRMax = 8;       // max local functions per element and axis (p + 
 constexpr int kPMax = 6;       // largest supported degree
 constexpr int kSolveLines = 32;  // lines per CTA in the pairing sweeps
 constexpr int kDotBlocks = 304;  // CTAs of the first reduction stage (2 x 152 SMs)
+constexpr int kCurlThreads = 256;  // curl: points of a component plane per CTA
+constexpr int kCurlKz = 8;         // curl: planes along z per thread
 
 // One component of a field: extents (x, y, z) and offset in the global vector.
 struct DevComp {
@@ -98,8 +100,8 @@ struct HodgeQuadF32Args {
     int kinds[3][3];
     int deg[3][3];
     int koff[3][3];
-    const float* bval[3];
-    const float* G;
+    const float2* bval[3];   // (hi, lo) pairs
+    const float2* G;         // (hi, lo) pairs, 6 arrays of Qtot
     long long Qtot;
     int Qn[3];
 };
@@ -143,11 +145,73 @@ cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, 
                             cudaStream_t s);
 cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
 cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
-cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, float* y,
+cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, double* y,
                                    cudaStream_t s);
-cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, float* y, cudaStream_t s);
+cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_line_f32(const LineF32Args& a, int kl, bool mass, const double* in64, const float* in32, float* out,
                             cudaStream_t s);
+
+// ---- reverse step and receivers (kernels_adj.cu)
+// Receiver rows in CSR form: row r = 3 * point + component of the E field.
+struct RecArgs {
+    const int* ptr;      // nrows + 1
+    const int* idx;      // entry -> index into e
+    const double* val;   // entry -> basis value
+    int nrows;
+};
+// Per-block derivative of the electric mass: block layout and scale[c] = -1/eps_c.
+struct PairArgs {
+    const double* scale;     // per block
+    const int* tile_block;   // block-Kronecker Hodge: block of each tile
+    int epb[3];              // elements per block along x, y, z
+    int nb[3];               // blocks along x, y, z
+};
+cudaError_t launch_receivers_eval(const RecArgs& r, const double* e, double* out, cudaStream_t s);
+cudaError_t launch_receivers_adjoint(const RecArgs& r, const double* w, double alpha, double* ebar, cudaStream_t s);
+cudaError_t launch_axpy(const double* x, double* y, double a, long long n, cudaStream_t s);
+cudaError_t launch_rescale_metric(double* G64, float2* G32, const HodgeQuadArgs& a, const int epb[3], const int nb[3],
+                                  const double* ratio, cudaStream_t s);
+cudaError_t launch_hodge_quad_pair(const HodgeQuadArgs& a, const PairArgs& p, const double* z, const double* d,
+                                   double* out, cudaStream_t s);
+cudaError_t launch_hodge_block_pair(const HodgeBlockArgs& a, const PairArgs& p, const double* z, const double* x,
+                                    double* out, cudaStream_t s);
+
+// ---- batched cavities: one persistent launch per leapfrog step (kernels.cu)
+// Identity map, constant mu (separable Hodge star of B) and block (or
+// constant) eps; FP64.  Per cavity: its field layouts, the argument blocks of
+// its own context, its state and scratch.
+struct BatchCavity {
+    DevField fE, fB, fH, fD;
+    MassSolveArgs msH[3];     // Hodge star of B: fused mass + K~_1 solve per axis
+    MassSolveArgs msD[3];     // Hodge star of D when eps is constant (sepD)
+    HodgeBlockArgs hbD;       // block Hodge of D otherwise
+    SolveArgs solveE[3];      // K_1 sweeps
+    double *d, *b, *e, *h, *y;
+    const double* jhat;       // or null
+    const double* amp;        // device, one value per step (with jhat)
+    double dt;
+    int kl[3];                // p - 1 per axis
+    int sepD;
+};
+constexpr int kBatchPhases = 10;
+constexpr int kBatchThreads = 256;
+struct BatchArgs {
+    const BatchCavity* cav;
+    const int2* items[kBatchPhases];   // per phase: (cavity, unit)
+    int nitems[kBatchPhases];
+    unsigned* bar;          // [0] arrivals, [1] generation
+    unsigned* status;       // bit 1: a grid barrier gave up
+    int line_warps;         // warps of a CTA that take line items
+    int warp_smem;          // doubles of shared memory per line warp
+    int step;               // index into amp
+};
+// unit encodings
+__host__ __device__ inline int batch_curl_unit(int c, int pb, int zc) { return (c << 28) | (zc << 14) | pb; }
+__host__ __device__ inline int batch_zero_unit(int z) { return (1 << 30) | z; }
+__host__ __device__ inline int batch_comp_unit(int c, int k) { return (c << 24) | k; }
+cudaError_t launch_batch_step(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+int batch_blocks_per_sm(size_t smem);
+size_t batch_line_warp_doubles(int maxn, int kl);  // staging of one line warp
 
 // ---- launchers (kernels.cu); all enqueue on `s` and return cudaGetLastError()
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b,

@@ -34,11 +34,9 @@ cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double*
 // memory, three banded 1D passes, scatter-add (FP64 atomics) into y.
 constexpr int kHodgeThreads = 256;
 
-__global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockArgs A, const double* __restrict__ x,
-                                                                    double* __restrict__ y) {
-    extern __shared__ double sm[];
-    const int c = blockIdx.y;
-    const int tile = blockIdx.x;
+// The work of one (tile, component) by a CTA of kHodgeThreads threads.
+__device__ __forceinline__ void hodge_block_tile(const HodgeBlockArgs& A, int c, int tile,
+                                                 const double* __restrict__ x, double* __restrict__ y, double* sm) {
     const int tx = tile % A.ntile[0];
     const int tyz = tile / A.ntile[0];
     const int ty = tyz % A.ntile[1];
@@ -105,6 +103,12 @@ __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockAr
         for (int m = lo; m <= hi; ++m) acc = fma(Mz[kk * kLd + m], s0[(m * Ly + jj) * Lx + ii], acc);
         atomicAdd(y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * (f0[2] + kk), acc);
     }
+}
+
+__global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockArgs A, const double* __restrict__ x,
+                                                                    double* __restrict__ y) {
+    extern __shared__ double sm[];
+    hodge_block_tile(A, blockIdx.y, blockIdx.x, x, y, sm);
 }
 
 cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s) {
@@ -314,17 +318,16 @@ __device__ __forceinline__ void lu_backward(const double* __restrict__ z, double
     }
 }
 
+// One block of kSolveLines lines (index lb) of component c, by one warp (tid = lane).
 template <int KL>
-__global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, const double* __restrict__ in,
-                                                                 double* __restrict__ out) {
-    extern __shared__ double sm[];
-    const int c = blockIdx.y;
+__device__ __forceinline__ void solve_lines(const SolveArgs& A, int c, int lb, const double* __restrict__ in,
+                                            double* __restrict__ out, double* sm, int tid) {
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
     const int n = C.n[axis];
     const int ncomp = C.n[0] * C.n[1] * C.n[2];
     const int nlines = ncomp / n;
-    const int l0 = blockIdx.x * kSolveLines;
+    const int l0 = lb * kSolveLines;
     if (l0 >= nlines) return;
     const int nl = min(kSolveLines, nlines - l0);
     const DevFactor F = A.f[c];
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
     double* fU = fL + n * KL;
     double* fD = fU + n * KL;
     double* S = fD + n;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nt = kSolveLines;
     for (int t = tid; t < n * KL; t += nt) {
         cp_async8(fL + t, F.L + t);
         cp_async8(fU + t, F.U + t);
@@ -355,7 +358,7 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
         for (int m = 0; m < n; ++m) cp_async8(S + m * kSolveLines + tid, src + base + m * stride);
     }
     cp_async_wait_all();
-    __syncthreads();
+    __syncwarp();
     if (tid < nl) {
         const int sL = axis == 0 ? ldl : 1;
         const int sM = axis == 0 ? 1 : kSolveLines;
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
         lu_forward<KL>(S + tid * sL, S2 + tid * sL, sM, n, fL);
         lu_backward<KL>(S2 + tid * sL, S + tid * sL, sM, n, fU, fD);
     }
-    __syncthreads();
+    __syncwarp();
     double* dst = out + C.off;
     if (axis == 0) {
         double* chunk = dst + (long long)l0 * n;
@@ -378,6 +381,13 @@ __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, co
 #pragma unroll 4
         for (int m = 0; m < n; ++m) dst[base + m * stride] = S[m * kSolveLines + tid];
     }
+}
+
+template <int KL>
+__global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, const double* __restrict__ in,
+                                                                 double* __restrict__ out) {
+    extern __shared__ double sm[];
+    solve_lines<KL>(A, blockIdx.y, blockIdx.x, in, out, sm, threadIdx.x);
 }
 
 template <int KL>
@@ -447,14 +457,13 @@ __device__ __forceinline__ void mass_line(const double* __restrict__ ypad, doubl
 }
 
 template <int KL, int D>
-__device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, const double* __restrict__ in,
-                                                double* __restrict__ out, double* sm) {
-    const int c = blockIdx.y;
+__device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, int c, int lb, const double* __restrict__ in,
+                                                double* __restrict__ out, double* sm, int tid) {
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
     const int n = C.n[axis];
     const int nlines = C.n[0] * C.n[1] * C.n[2] / n;
-    const int l0 = blockIdx.x * kSolveLines;
+    const int l0 = lb * kSolveLines;
     if (l0 >= nlines) return;
     const int nl = min(kSolveLines, nlines - l0);
     const DevFactor F = A.f[c];
@@ -467,7 +476,7 @@ __device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, const do
     const int np = n + 2 * D;
     const int ldin = np | 1, ldout = n | 1;
     double* Sout = Sin + kSolveLines * ldin;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nt = kSolveLines;
     const double* Mg = A.mass[c];
     for (int t = tid; t < n * KL; t += nt) {
         cp_async8(fL + t, F.L + t);
@@ -500,7 +509,7 @@ __device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, const do
         for (int m = 0; m < n; ++m) cp_async8(Sin + (D + m) * kSolveLines + tid, src + base + m * stride);
     }
     cp_async_wait_all();
-    __syncthreads();
+    __syncwarp();
     const int oL = axis == 0 ? ldout : 1;
     if (tid < nl) {
         // t = M y: independent banded dot products, no recurrence
@@ -509,7 +518,7 @@ __device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, const do
         lu_forward<KL>(Sout + tid * oL, Sin + tid * sL, sM, n, fL);
         lu_backward<KL>(Sin + tid * sL, Sout + tid * oL, sM, n, fU, fD);
     }
-    __syncthreads();
+    __syncwarp();
     double* dst = out + C.off;
     if (axis == 0) {
         double* chunk = dst + (long long)l0 * n;
@@ -526,18 +535,25 @@ __device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, const do
     }
 }
 
+// The fused pass for one block of lines, the mass half-bandwidth of the component chosen at run time.
+template <int KL>
+__device__ __forceinline__ void mass_solve_lines(const MassSolveArgs& A, int c, int lb, const double* __restrict__ in,
+                                                 double* __restrict__ out, double* sm, int tid) {
+    const int d = A.deg[c];
+    if (d == KL - 1) {
+        if constexpr (KL >= 1) mass_solve_body<KL, (KL >= 1 ? KL - 1 : 0)>(A, c, lb, in, out, sm, tid);
+    } else if (d == KL) {
+        mass_solve_body<KL, KL>(A, c, lb, in, out, sm, tid);
+    } else {
+        mass_solve_body<KL, KL + 1>(A, c, lb, in, out, sm, tid);
+    }
+}
+
 template <int KL>
 __global__ void __launch_bounds__(kSolveLines) mass_solve_axis_kernel(MassSolveArgs A, const double* __restrict__ in,
                                                                       double* __restrict__ out) {
     extern __shared__ double sm[];
-    const int d = A.deg[blockIdx.y];
-    if (d == KL - 1) {
-        if constexpr (KL >= 1) mass_solve_body<KL, (KL >= 1 ? KL - 1 : 0)>(A, in, out, sm);
-    } else if (d == KL) {
-        mass_solve_body<KL, KL>(A, in, out, sm);
-    } else {
-        mass_solve_body<KL, KL + 1>(A, in, out, sm);
-    }
+    mass_solve_lines<KL>(A, blockIdx.y, blockIdx.x, in, out, sm, threadIdx.x);
 }
 
 template <int KL>
@@ -623,6 +639,187 @@ cudaError_t launch_scale_copy(const double* x, double* y, double a, long long n,
     const long long nb = (n + 255) / 256;
     if (nb > 0) scale_copy_kernel<<<(unsigned)nb, 256, 0, s>>>(x, y, a, n);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched cavities
+// One persistent (cooperative) launch runs a whole leapfrog step of many
+// independent cavities: ten phases separated by grid barriers,
+//   0 b -= dt/2 D^1 e            4 d += dt (D~^1 h - s jhat); y = 0
+//   1-3 h = A^{-1} M b per axis  5 y = M~ d (block Hodge)
+//   6-8 e = K_1^{-1} y per axis (or the fused mass + solve passes when eps
+//       is constant)               9 b -= dt/2 D^1 e
+// Each phase walks a flat list of (cavity, unit) items: whole-CTA units
+// (curl chunks, Hodge tiles, zeroing) or line units (kSolveLines lines, one
+// warp, each line warp with its own shared-memory staging).  The work of a
+// unit is the device function of the single-cavity kernel, so a batched step
+// computes exactly what the separate launches compute.
+
+__device__ __forceinline__ unsigned long long batch_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All CTAs are co-resident (cooperative launch).  The wait is bounded (one
+// second); a CTA that gives up sets bit 1 of the status word and the whole
+// launch returns after the barrier.
+__device__ bool batch_barrier(unsigned* bar, unsigned* status, unsigned nblocks) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = batch_ns();
+            while (*gen == g) {
+                if (batch_ns() - t0 > 1000000000ull) {
+                    ok = 0;
+                    atomicOr(status, 2u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok_s = ok && !(*(volatile unsigned*)status & 2u);
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <bool DUAL>
+__device__ __noinline__ void batch_curl(const BatchCavity& K, int unit, const double* in, double* out,
+                                           double alpha, const double* jhat, const double* amp, int step) {
+    const int c = (unit >> 28) & 3, zc = (unit >> 14) & 0x3FFF, pb = unit & 0x3FFF;
+    const DevField& IN = DUAL ? K.fH : K.fE;
+    const DevField& OUT = DUAL ? K.fD : K.fB;
+    const int p = pb * kCurlThreads + threadIdx.x;
+    if (c == 0) curl_plane_comp<0, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz);
+    else if (c == 1) curl_plane_comp<1, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz);
+    else curl_plane_comp<2, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz);
+}
+
+// Each variant is its own (not inlined) function, so the persistent kernel
+// does not carry the register pressure of all of them at once.
+template <int KL>
+__device__ __noinline__ void batch_mass_solve_k(const MassSolveArgs& A, int c, int lb, const double* in, double* out,
+                                                double* sm, int lane) {
+    mass_solve_lines<KL>(A, c, lb, in, out, sm, lane);
+}
+template <int KL>
+__device__ __noinline__ void batch_solve_k(const SolveArgs& A, int c, int lb, const double* in, double* out,
+                                           double* sm, int lane) {
+    solve_lines<KL>(A, c, lb, in, out, sm, lane);
+}
+__device__ __noinline__ void batch_hodge_tile(const HodgeBlockArgs& A, int c, int tile, const double* x, double* y,
+                                              double* sm) {
+    hodge_block_tile(A, c, tile, x, y, sm);
+}
+
+__device__ __forceinline__ void batch_mass_solve(const MassSolveArgs& A, int kl, int c, int lb, const double* in,
+                                                 double* out, double* sm, int lane) {
+    switch (kl) {
+        case 1: batch_mass_solve_k<1>(A, c, lb, in, out, sm, lane); break;
+        case 2: batch_mass_solve_k<2>(A, c, lb, in, out, sm, lane); break;
+        case 3: batch_mass_solve_k<3>(A, c, lb, in, out, sm, lane); break;
+        case 4: batch_mass_solve_k<4>(A, c, lb, in, out, sm, lane); break;
+        default: batch_mass_solve_k<5>(A, c, lb, in, out, sm, lane); break;
+    }
+}
+
+__device__ __forceinline__ void batch_solve(const SolveArgs& A, int kl, int c, int lb, const double* in, double* out,
+                                            double* sm, int lane) {
+    switch (kl) {
+        case 1: batch_solve_k<1>(A, c, lb, in, out, sm, lane); break;
+        case 2: batch_solve_k<2>(A, c, lb, in, out, sm, lane); break;
+        case 3: batch_solve_k<3>(A, c, lb, in, out, sm, lane); break;
+        case 4: batch_solve_k<4>(A, c, lb, in, out, sm, lane); break;
+        default: batch_solve_k<5>(A, c, lb, in, out, sm, lane); break;
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs B) {
+    extern __shared__ double smb[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned nblocks = gridDim.x;
+    for (int ph = 0; ph < kBatchPhases; ++ph) {
+        const int2* items = B.items[ph];
+        const int n = B.nitems[ph];
+        const bool line_phase = (ph >= 1 && ph <= 3) || (ph >= 6 && ph <= 8);
+        if (!line_phase) {
+            for (int it = blockIdx.x; it < n; it += nblocks) {
+                const int2 w = items[it];
+                const BatchCavity& K = B.cav[w.x];
+                if (ph == 0 || ph == 9) {
+                    batch_curl<false>(K, w.y, K.e, K.b, -0.5 * K.dt, nullptr, nullptr, 0);
+                } else if (ph == 4) {
+                    if (w.y & (1 << 30)) {  // zero a chunk of y
+                        const long long z0 = (long long)(w.y & 0xFFFFFF) * (kBatchThreads * 8);
+                        for (int q = 0; q < 8; ++q) {
+                            const long long i = z0 + q * kBatchThreads + threadIdx.x;
+                            if (i < K.fE.total) K.y[i] = 0.0;
+                        }
+                    } else {
+                        batch_curl<true>(K, w.y, K.h, K.d, K.dt, K.jhat, K.amp, B.step);
+                    }
+                } else {  // ph == 5: block Hodge of D into y
+                    batch_hodge_tile(K.hbD, w.y >> 24, w.y & 0xFFFFFF, K.d, K.y, smb);
+                    __syncthreads();  // the next unit reuses the shared memory
+                }
+            }
+        } else if (warp < B.line_warps) {
+            double* sm = smb + (size_t)warp * B.warp_smem;
+            const int gw = blockIdx.x * B.line_warps + warp, nw = nblocks * B.line_warps;
+            for (int it = gw; it < n; it += nw) {
+                const int2 w = items[it];
+                const BatchCavity& K = B.cav[w.x];
+                const int c = w.y >> 24, lb = w.y & 0xFFFFFF;
+                if (ph <= 3) {
+                    const int a = ph - 1;
+                    batch_mass_solve(K.msH[a], K.kl[a], c, lb, a == 0 ? K.b : K.h, K.h, sm, lane);
+                } else {
+                    const int a = ph - 6;
+                    if (K.sepD)
+                        batch_mass_solve(K.msD[a], K.kl[a], c, lb, a == 0 ? K.d : K.e, K.e, sm, lane);
+                    else
+                        batch_solve(K.solveE[a], K.kl[a], c, lb, a == 0 ? K.y : K.e, K.e, sm, lane);
+                }
+                __syncwarp();  // the next unit reuses this warp's staging
+            }
+        }
+        if (ph + 1 < kBatchPhases && !batch_barrier(B.bar, B.status, nblocks)) return;
+    }
+}
+
+size_t batch_line_warp_doubles(int maxn, int kl) {
+    const int D = kl + 1, W = 2 * D + 1;
+    return (size_t)(2 * kl + 1 + W) * maxn + (size_t)((maxn + 2 * D) | 1) * kSolveLines +
+           (size_t)(maxn | 1) * kSolveLines + 8;
+}
+
+int batch_blocks_per_sm(size_t smem) {
+    // the dynamic shared memory the launch will request (the kernel's own static words come on top)
+    if (cudaFuncSetAttribute(batch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();  // clear: the shape does not fit
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel, kBatchThreads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_batch_step(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
+    BatchArgs args = a;
+    void* params[] = {&args};
+    return cudaLaunchCooperativeKernel((const void*)batch_step_kernel, dim3(grid), dim3(kBatchThreads), params, smem, s);
 }
 
 }  // namespace smx

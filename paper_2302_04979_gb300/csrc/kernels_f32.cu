@@ -67,7 +67,7 @@ cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t
 // (L <= 16 per axis) and march along z, so no index is divided at run time.
 template <class TIN>
 __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args A, const TIN* __restrict__ x,
-                                                              float* __restrict__ y) {
+                                                              double* __restrict__ y) {
     extern __shared__ float smf[];
     const int c = blockIdx.y;
     const int tile = blockIdx.x;
@@ -137,18 +137,18 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     }
     __syncthreads();
     if (act) {  // z pass and scatter-add
-        float* ycol = y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
+        double* ycol = y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
         const float* col = s0 + jj * Lx + ii;
         for (int kk = 0; kk < Lz; ++kk) {
             const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
             float acc = 0.0f;
             for (int m = lo; m <= hi; ++m) acc = fma2(Mz[kk * kLd + m], col[m * Ly * Lx], acc);
-            atomicAdd(ycol + nxy * kk, acc);
+            atomicAdd(ycol + nxy * kk, f2d_exact(acc));
         }
     }
 }
 
-cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, float* y,
+cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, double* y,
                                    cudaStream_t s) {
     const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
     const size_t smem = 3 * kLMax * (kLMax + 1) * sizeof(float2) + 2 * (size_t)a.max_nloc * sizeof(float);
@@ -164,24 +164,26 @@ cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64
 // Curved map or pointwise material (the FP64 kernel's algorithm): per element,
 // interpolate the three components at the q^3 Gauss points by sum
 // factorisation, apply the symmetric metric G (weight, material and 2-form
-// pullback folded in, stored as FP32), integrate back, scatter-add into the
-// FP32 output with atomics.  One CTA per element.
+// pullback folded in), integrate back, scatter-add into the FP32 output with
+// atomics.  One CTA per element.  The basis values and the metric are FP32
+// (hi, lo) pairs, so the operator keeps FP64 accuracy and only the data is
+// rounded to FP32, as in the block-Kronecker kernel.
 constexpr int kQuadF32Threads = 128;
 
 __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQuadF32Args A,
                                                                         const double* __restrict__ x,
-                                                                        float* __restrict__ y) {
+                                                                        double* __restrict__ y) {
     extern __shared__ float smq[];
     const int e = blockIdx.x;
     const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
     const int el[3] = {ex, ey, ez};
     const int qx = A.q[0], qy = A.q[1], qz = A.q[2];
     const int Qe = qx * qy * qz;
-    float* U = smq;                          // 3 * Qe values at the Gauss points
+    float2* Bv = reinterpret_cast<float2*>(smq);  // 3 axes x 8 points x kRMax (hi, lo)
+    float* U = reinterpret_cast<float*>(Bv + 3 * 8 * kRMax);  // 3 * Qe values at the Gauss points
     float* T1 = U + 3 * Qe;                  // scratch, <= Qe * kRMax
     float* T2 = T1 + Qe * kRMax;             // scratch, <= Qe * kRMax
     float* X = T2 + Qe * kRMax;              // local coefficients, <= kRMax^3
-    float* Bv = X + kRMax * kRMax * kRMax;   // 3 axes x 8 points x kRMax
     const int tid = threadIdx.x, nt = blockDim.x;
     auto load_basis = [&](int c) {
         for (int t = tid; t < 3 * 8 * kRMax; t += nt) {
@@ -203,27 +205,27 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
             X[t] = v;
         }
         __syncthreads();
-        const float* Bx = Bv;
-        const float* By = Bv + 8 * kRMax;
-        const float* Bz = Bv + 16 * kRMax;
+        const float2* Bx = Bv;
+        const float2* By = Bv + 8 * kRMax;
+        const float2* Bz = Bv + 16 * kRMax;
         for (int t = tid; t < rz * ry * qx; t += nt) {  // T1[r2][r1][qx]
             const int a = t % qx, rr = t / qx;
             float acc = 0.0f;
-            for (int r0 = 0; r0 < rx; ++r0) acc = fmaf(Bx[a * kRMax + r0], X[rr * rx + r0], acc);
+            for (int r0 = 0; r0 < rx; ++r0) acc = fma2(Bx[a * kRMax + r0], X[rr * rx + r0], acc);
             T1[t] = acc;
         }
         __syncthreads();
         for (int t = tid; t < rz * qy * qx; t += nt) {  // T2[r2][qy][qx]
             const int a = t % qx, rr = t / qx, b = rr % qy, r2 = rr / qy;
             float acc = 0.0f;
-            for (int r1 = 0; r1 < ry; ++r1) acc = fmaf(By[b * kRMax + r1], T1[(r2 * ry + r1) * qx + a], acc);
+            for (int r1 = 0; r1 < ry; ++r1) acc = fma2(By[b * kRMax + r1], T1[(r2 * ry + r1) * qx + a], acc);
             T2[t] = acc;
         }
         __syncthreads();
         for (int t = tid; t < Qe; t += nt) {  // U_c[qz][qy][qx]
             const int ab = t % (qx * qy), g = t / (qx * qy);
             float acc = 0.0f;
-            for (int r2 = 0; r2 < rz; ++r2) acc = fmaf(Bz[g * kRMax + r2], T2[r2 * qx * qy + ab], acc);
+            for (int r2 = 0; r2 < rz; ++r2) acc = fma2(Bz[g * kRMax + r2], T2[r2 * qx * qy + ab], acc);
             U[c * Qe + t] = acc;
         }
         __syncthreads();
@@ -231,13 +233,13 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
     for (int t = tid; t < Qe; t += nt) {  // metric at each Gauss point
         const int a = t % qx, rr = t / qx, b = rr % qy, g = rr / qy;
         const long long qi = ((long long)(ez * qz + g) * A.Qn[1] + (ey * qy + b)) * A.Qn[0] + (ex * qx + a);
-        const float g00 = __ldg(A.G + qi), g01 = __ldg(A.G + A.Qtot + qi), g02 = __ldg(A.G + 2 * A.Qtot + qi);
-        const float g11 = __ldg(A.G + 3 * A.Qtot + qi), g12 = __ldg(A.G + 4 * A.Qtot + qi);
-        const float g22 = __ldg(A.G + 5 * A.Qtot + qi);
+        const float2 g00 = __ldg(A.G + qi), g01 = __ldg(A.G + A.Qtot + qi), g02 = __ldg(A.G + 2 * A.Qtot + qi);
+        const float2 g11 = __ldg(A.G + 3 * A.Qtot + qi), g12 = __ldg(A.G + 4 * A.Qtot + qi);
+        const float2 g22 = __ldg(A.G + 5 * A.Qtot + qi);
         const float u0 = U[t], u1 = U[Qe + t], u2 = U[2 * Qe + t];
-        U[t] = g00 * u0 + g01 * u1 + g02 * u2;
-        U[Qe + t] = g01 * u0 + g11 * u1 + g12 * u2;
-        U[2 * Qe + t] = g02 * u0 + g12 * u1 + g22 * u2;
+        U[t] = fma2(g00, u0, fma2(g01, u1, fma2(g02, u2, 0.0f)));
+        U[Qe + t] = fma2(g01, u0, fma2(g11, u1, fma2(g12, u2, 0.0f)));
+        U[2 * Qe + t] = fma2(g02, u0, fma2(g12, u1, fma2(g22, u2, 0.0f)));
     }
     __syncthreads();
     for (int c = 0; c < 3; ++c) {
@@ -245,20 +247,20 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
         const int rx = A.deg[c][0] + 1, ry = A.deg[c][1] + 1, rz = A.deg[c][2] + 1;
         load_basis(c);
         __syncthreads();
-        const float* Bx = Bv;
-        const float* By = Bv + 8 * kRMax;
-        const float* Bz = Bv + 16 * kRMax;
+        const float2* Bx = Bv;
+        const float2* By = Bv + 8 * kRMax;
+        const float2* Bz = Bv + 16 * kRMax;
         for (int t = tid; t < rz * qy * qx; t += nt) {  // T2[r2][qy][qx] = sum_qz Bz[qz][r2] V[qz][qy][qx]
             const int ab = t % (qx * qy), r2 = t / (qx * qy);
             float acc = 0.0f;
-            for (int g = 0; g < qz; ++g) acc = fmaf(Bz[g * kRMax + r2], U[c * Qe + g * qx * qy + ab], acc);
+            for (int g = 0; g < qz; ++g) acc = fma2(Bz[g * kRMax + r2], U[c * Qe + g * qx * qy + ab], acc);
             T2[t] = acc;
         }
         __syncthreads();
         for (int t = tid; t < rz * ry * qx; t += nt) {  // T1[r2][r1][qx] = sum_qy By[qy][r1] T2[r2][qy][qx]
             const int a = t % qx, rr = t / qx, r1 = rr % ry, r2 = rr / ry;
             float acc = 0.0f;
-            for (int b = 0; b < qy; ++b) acc = fmaf(By[b * kRMax + r1], T2[(r2 * qy + b) * qx + a], acc);
+            for (int b = 0; b < qy; ++b) acc = fma2(By[b * kRMax + r1], T2[(r2 * qy + b) * qx + a], acc);
             T1[t] = acc;
         }
         __syncthreads();
@@ -267,18 +269,19 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
             const int gi = el[0] + r0 + A.koff[c][0], gj = el[1] + r1 + A.koff[c][1], gk = el[2] + r2 + A.koff[c][2];
             if (gi >= 0 && gi < C.n[0] && gj >= 0 && gj < C.n[1] && gk >= 0 && gk < C.n[2]) {
                 float acc = 0.0f;
-                for (int a = 0; a < qx; ++a) acc = fmaf(Bx[a * kRMax + r0], T1[rr * qx + a], acc);
-                atomicAdd(y + C.off + gi + (long long)C.n[0] * (gj + (long long)C.n[1] * gk), acc);
+                for (int a = 0; a < qx; ++a) acc = fma2(Bx[a * kRMax + r0], T1[rr * qx + a], acc);
+                atomicAdd(y + C.off + gi + (long long)C.n[0] * (gj + (long long)C.n[1] * gk), f2d_exact(acc));
             }
         }
         __syncthreads();
     }
 }
 
-cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, float* y, cudaStream_t s) {
+cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, double* y, cudaStream_t s) {
     const int nel = a.nel[0] * a.nel[1] * a.nel[2];
     const int Qe = a.q[0] * a.q[1] * a.q[2];
-    const size_t smem = (3 * Qe + 2 * Qe * kRMax + kRMax * kRMax * kRMax + 3 * 8 * kRMax) * sizeof(float);
+    const size_t smem =
+        3 * 8 * kRMax * sizeof(float2) + (3 * Qe + 2 * Qe * kRMax + kRMax * kRMax * kRMax) * sizeof(float);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(hodge_quad_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -522,9 +525,8 @@ constexpr int kModeOutGroups = 32;   // threads along outputs: outputs i = og + 
 // warp with the same og), then issues 8 NOUT FMAs.  Rows i >= n read zero
 // padding and are not stored.
 template <class TIN, int NOUT>
-__global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kernel(ModeF32Args A,
-                                                                                   const TIN* __restrict__ in,
-                                                                                   float* __restrict__ out) {
+__global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kernel(ModeF32Args A, const TIN* in,
+                                                                                   float* out) {
     extern __shared__ float smf[];
     const int c = blockIdx.y;
     const DevComp C = A.field.c[c];
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
         const TIN* chunk = src + (long long)l0 * n;
         for (int g = tid; g < nl * n; g += nt) {
             const int line = g / n, m = g - line * n;
-            T[m * kModeLd + line] = to_f(__ldg(chunk + g));
+            T[m * kModeLd + line] = to_f(chunk[g]);
         }
     } else {
         const int stride = axis == 1 ? nx : nxy;
@@ -560,7 +562,7 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
             const int m = g / nl, w = g - m * nl;
             const int l = l0 + w;
             const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-            T[m * kModeLd + w] = to_f(__ldg(src + base + m * stride));
+            T[m * kModeLd + w] = to_f(src[base + m * stride]);
         }
     }
     if (nl < kModeLines)  // keep the unused tile columns finite

@@ -59,6 +59,20 @@ _SIGS = {
     "smx_set_mode_kernel": [ctypes.c_void_p, ctypes.c_int],
     "smx_device_status": [ctypes.c_void_p],
     "smx_hodge_star_mixed": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_receivers_set": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "smx_receivers_eval": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_receivers_adjoint": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p],
+    "smx_set_material_blocks": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "smx_step_adjoint": [ctypes.c_void_p] * 7 + [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p],
+    "smx_adjoint_terminal": [ctypes.c_void_p] * 5,
+    "smx_batch_create": [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+    "smx_batch_destroy": [ctypes.c_void_p],
+    "smx_batch_workspace_bytes": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+    "smx_batch_bind_workspace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "smx_batch_set_state": [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6 + [ctypes.c_double],
+    "smx_batch_step": [ctypes.c_void_p, ctypes.c_int],
+    "smx_batch_status": [ctypes.c_void_p],
+    "smx_batch_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "smx_curl_primal": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
     "smx_curl_dual": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                       ctypes.c_double],
@@ -82,11 +96,11 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)],
 }
 
-NCLASS = 19
+NCLASS = 21
 KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
                   "reduction", "mass_solve_x", "mass_solve_y", "mass_solve_z",
                   "curl_primal_f32", "curl_dual_f32", "hodge_block_f32", "line_f32_x", "line_f32_y", "line_f32_z",
-                  "cast", "hodge_quad_f32")
+                  "cast", "hodge_quad_f32", "mass_derivative", "receivers")
 
 
 def _lib():
@@ -255,6 +269,33 @@ class Context:
         """The mixed step's FP32 Hodge star on its own (context created with precision="mixed")."""
         _check(_lib().smx_hodge_star_mixed(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star_mixed")
 
+    # ---- reverse mode
+    def receivers_set(self, xhat):
+        """Receiver points (n x 3 parametric coordinates); before bind()."""
+        xh = np.ascontiguousarray(xhat, dtype=np.float64).reshape(-1, 3)
+        _check(_lib().smx_receivers_set(self.h, xh.shape[0], xh.ctypes.data_as(ctypes.c_void_p)), "smx_receivers_set")
+        self.n_receivers = xh.shape[0]
+
+    def receivers_eval(self, e, out):
+        _check(_lib().smx_receivers_eval(self.h, _ptr(e), _ptr(out)), "smx_receivers_eval")
+
+    def receivers_adjoint(self, w, alpha, ebar):
+        _check(_lib().smx_receivers_adjoint(self.h, _ptr(w), float(alpha), _ptr(ebar)), "smx_receivers_adjoint")
+
+    def set_material_blocks(self, values):
+        """New permittivity block values, array (b_z, b_y, b_x) (the context's block grid)."""
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        _check(_lib().smx_set_material_blocks(self.h, FIELD_D, v.ctypes.data_as(ctypes.c_void_p)),
+               "smx_set_material_blocks")
+
+    def step_adjoint(self, d_n, d_np1, dbar, bbar, dt, ebar=None, jhat=None, amp_bar=None, eps_bar=None):
+        _check(_lib().smx_step_adjoint(self.h, _ptr(d_n), _ptr(d_np1), _ptr(dbar), _ptr(bbar), _ptr(ebar), _ptr(jhat),
+                                       float(dt), _ptr(amp_bar), _ptr(eps_bar)), "smx_step_adjoint")
+
+    def adjoint_terminal(self, d_N, ebar, dbar, eps_bar=None):
+        _check(_lib().smx_adjoint_terminal(self.h, _ptr(d_N), _ptr(ebar), _ptr(dbar), _ptr(eps_bar)),
+               "smx_adjoint_terminal")
+
     def hodge_star_noalloc(self, field, x, out):
         """hodge_star without a bound workspace: tables and scratch in the library's fixed device array."""
         _check(_lib().smx_hodge_star_noalloc(self.h, field, _ptr(x), _ptr(out)), "smx_hodge_star_noalloc")
@@ -308,3 +349,41 @@ class Context:
         _check(_lib().smx_cfl(self.h, int(iters), float(tol), _ptr(v), _ptr(w), _ptr(t), ctypes.byref(out)),
                "smx_cfl")
         return out.value
+
+
+class Batch:
+    """Independent cavities (bound FP64 contexts) stepped by one persistent launch per step."""
+
+    def __init__(self, contexts, device="cuda"):
+        import torch
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        _check(_lib().smx_batch_create(len(self.contexts), arr, ctypes.byref(h)), "smx_batch_create")
+        self.h = h
+        n = ctypes.c_size_t()
+        _check(_lib().smx_batch_workspace_bytes(h, ctypes.byref(n)), "smx_batch_workspace_bytes")
+        ws = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+        aligned = (ws.data_ptr() + 255) & ~255
+        _check(_lib().smx_batch_bind_workspace(h, ctypes.c_void_p(aligned), n.value), "smx_batch_bind_workspace")
+        self.workspace = ws
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _LIB is not None:
+            _LIB.smx_batch_destroy(self.h)
+            self.h = None
+
+    def set_state(self, i, d, b, e, h, dt, jhat=None, amp=None):
+        _check(_lib().smx_batch_set_state(self.h, int(i), _ptr(d), _ptr(b), _ptr(e), _ptr(h), _ptr(jhat), _ptr(amp),
+                                          float(dt)), "smx_batch_set_state")
+
+    def step(self, nsteps):
+        _check(_lib().smx_batch_step(self.h, int(nsteps)), "smx_batch_step")
+
+    def status(self):
+        _check(_lib().smx_batch_status(self.h), "smx_batch_status")
+
+    def autotune(self, steps=3):
+        lw = ctypes.c_int()
+        _check(_lib().smx_batch_autotune(self.h, int(steps), ctypes.byref(lw)), "smx_batch_autotune")
+        return lw.value

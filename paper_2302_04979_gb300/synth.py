@@ -77,3 +77,21 @@ def source_amplitudes(dt, nsteps, f0=1.0, tau=0.25, t0=0.75):
     """s(t_n + dt/2) for the Gaussian-modulated carrier s(t) = sin(2 pi f0 t) exp(-(t - t0)^2 / (2 tau^2))."""
     t = (np.arange(nsteps) + 0.5) * dt
     return np.sin(2.0 * np.pi * f0 * t) * np.exp(-((t - t0) ** 2) / (2.0 * tau ** 2))
+
+
+def bump_coefficients(seed, comp_shapes, comp=2, width=0.05):
+    """A smooth source vector for a field with components of shapes (nx, ny, nz): component
+    ``comp`` holds exp(-|x - x0|^2 / (2 width^2)) at the normalised index positions
+    ((i + 1/2)/nx, (j + 1/2)/ny, (k + 1/2)/nz), x0 = pulse_centre(seed); the others are zero.
+    Components are concatenated, x fastest."""
+    x0 = pulse_centre(seed)
+    parts = []
+    for c, (nx, ny, nz) in enumerate(comp_shapes):
+        if c != comp:
+            parts.append(np.zeros(nx * ny * nz))
+            continue
+        z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                              indexing="ij")
+        r2 = (x - x0[0]) ** 2 + (y - x0[1]) ** 2 + (z - x0[2]) ** 2
+        parts.append(np.exp(-r2 / (2.0 * width ** 2)).reshape(-1))
+    return np.concatenate(parts)

@@ -1,0 +1,109 @@
+"""Reverse mode on the GPU (smx_step_adjoint behind torch.autograd) against the oracle's
+discrete adjoint (oracle/adjoint.py, itself pinned by finite differences), and against
+central finite differences of the GPU loss at the full adjoint configuration."""
+import numpy as np
+import pytest
+
+from oracle import adjoint, hodge, maxwell
+from paper_2302_04979_gb300 import synth
+from tests.gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(geometry):
+    p, nel, blocks, nsteps = 2, (4, 4, 6), (2, 2, 3), 6
+    geom = hodge.SineBumpMap(0.05) if geometry == "sine_bump" else None
+    S0 = maxwell.Scheme2(p, nel, geometry=geom)
+    xr = synth.uniform(90, 9, 0.05, 0.95).reshape(3, 3)
+    jhat = synth.uniform(91, S0.N_e, -1.0, 1.0)
+    d0 = synth.uniform(92, S0.N_e, -1.0, 1.0)
+    b0 = S0.D1 @ synth.uniform(93, S0.N_e, -1.0, 1.0)
+    eps = synth.uniform(94, int(np.prod(blocks)), 1.0, 4.0).reshape(blocks[::-1])
+    dt = 0.4 * S0.cfl(tol=1e-8)[0]
+    amps = synth.uniform(95, nsteps, -1.0, 1.0)
+    P = adjoint.MisfitProblem(p, nel, geom, eps, 1.0, jhat, adjoint.Receivers(p, nel, xr), dt, nsteps, d0, b0)
+    obs = P.forward(eps * (1.0 + 0.1 * synth.uniform(96, eps.size, -1.0, 1.0).reshape(eps.shape)), amps)[3]
+    return dict(p=p, nel=nel, geometry=geometry, eps=eps, xr=xr, d0=d0, b0=b0, jhat=jhat, dt=dt, nsteps=nsteps,
+                amps=amps, obs=obs, P=P)
+
+
+def _gpu_grad(case, checkpoint_every=None):
+    import torch
+    from paper_2302_04979_gb300 import adjoint as gadj
+    prob = gadj.LeapfrogProblem(case["p"], case["nel"], case["eps"], case["xr"], case["d0"], case["b0"], case["jhat"],
+                                case["dt"], case["nsteps"], geometry=case["geometry"])
+    if checkpoint_every:
+        prob.k = checkpoint_every
+    eps_t = torch.tensor(case["eps"], dtype=torch.float64, requires_grad=True)
+    amps_t = torch.tensor(case["amps"], dtype=torch.float64, device="cuda", requires_grad=True)
+    obs = torch.as_tensor(case["obs"]).cuda()
+    traces = gadj.LeapfrogTraces.apply(eps_t, amps_t, prob)
+    loss = gadj.misfit(traces, obs, case["dt"])
+    loss.backward()
+    return float(loss), eps_t.grad.numpy(), amps_t.grad.cpu().numpy(), prob
+
+
+@pytest.mark.parametrize("geometry", ["identity", "sine_bump"])
+def test_gradient_matches_oracle(geometry):
+    case = _small(geometry)
+    loss_ref, geps_ref, gamp_ref = case["P"].gradient(case["eps"], case["amps"], case["obs"])
+    loss, geps, gamp, _ = _gpu_grad(case)
+    print("\n%s: loss %.6e vs %.6e; rel L2 grad eps %.2e, amps %.2e"
+          % (geometry, loss, loss_ref, rel_l2(geps, geps_ref), rel_l2(gamp, gamp_ref)))
+    assert abs(loss - loss_ref) <= 1e-11 * loss_ref
+    assert rel_l2(geps, geps_ref) < 1e-10
+    assert rel_l2(gamp, gamp_ref) < 1e-10
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient():
+    case = _small("sine_bump")
+    _, g1, a1, _ = _gpu_grad(case, checkpoint_every=1)
+    _, g3, a3, _ = _gpu_grad(case, checkpoint_every=4)
+    assert rel_l2(g3, g1) < 1e-13 and rel_l2(a3, a1) < 1e-13
+
+
+@pytest.mark.slow
+def test_adjoint_configuration_finite_differences():
+    """48^3, p=3, sine-bump map, permittivity on a 16^3 block grid (seeded U[1,4)), 500 steps,
+    32 seeded receivers, misfit against traces of a perturbed permittivity: the adjoint
+    gradient against central differences of the GPU loss in 8 seeded directions (1e-6)."""
+    import torch
+    from paper_2302_04979_gb300 import adjoint as gadj, smx
+    p, nel, nb, nsteps = 3, 48, 16, 500
+    eps = synth.uniform(2310, nb ** 3, 1.0, 4.0).reshape(nb, nb, nb)
+    probe = smx.Context(p, nel, geometry="sine_bump", amplitude=0.05, eps=("blocks", eps))
+    N_e, N_h = probe.N_e, probe.N_h
+    shapes = [probe.comp_shape(smx.FIELD_D, c) for c in range(3)]
+    del probe
+    xr = synth.uniform(2311, 96, 0.05, 0.95).reshape(32, 3)
+    jhat = synth.bump_coefficients(2312, shapes)
+    d0, b0 = np.zeros(N_e), np.zeros(N_h)
+    # about 0.5 x the CFL limit: 0.0126 at 16^3 for this map with eps in [1, 4), linear in h (Sec. 5.2)
+    dt = 0.002
+    amps = synth.source_amplitudes(dt, nsteps, f0=1.0, tau=0.25, t0=0.75)
+    prob = gadj.LeapfrogProblem(p, nel, eps, xr, d0, b0, jhat, dt, nsteps, geometry="sine_bump")
+    amps_dev = torch.as_tensor(amps).cuda()
+    prob.set_eps(eps * (1.0 + 0.05 * synth.uniform(2313, eps.size, -1.0, 1.0).reshape(eps.shape)))
+    obs = prob.forward(amps_dev)
+    eps_t = torch.tensor(eps, dtype=torch.float64, requires_grad=True)
+    amps_t = amps_dev.clone().requires_grad_(True)
+    traces = gadj.LeapfrogTraces.apply(eps_t, amps_t, prob)
+    loss = gadj.misfit(traces, obs, dt)
+    loss.backward()
+    geps, gamp = eps_t.grad.numpy(), amps_t.grad.cpu().numpy()
+
+    def L(e, a):
+        prob.set_eps(e)
+        return float(gadj.misfit(prob.forward(torch.as_tensor(a).cuda()), obs, dt))
+
+    worst = 0.0
+    for k in range(8):
+        ve = synth.normal(2400 + k, eps.size).reshape(eps.shape)
+        va = synth.normal(2500 + k, nsteps)
+        h = 2e-5
+        fd = (L(eps + h * ve, amps + h * va) - L(eps - h * ve, amps - h * va)) / (2 * h)
+        an = float(np.sum(geps * ve) + gamp @ va)
+        worst = max(worst, abs(fd - an) / abs(an))
+        print("direction %d: FD %.10e adjoint %.10e rel %.2e" % (k, fd, an, abs(fd - an) / abs(an)))
+    assert worst < 1e-6

@@ -1,0 +1,112 @@
+"""Batched cavities: one persistent launch per step (smx_batch_*) against the same cavities
+stepped one by one with smx_step (itself pinned to the oracle to 1e-11)."""
+import numpy as np
+import pytest
+
+from paper_2302_04979_gb300 import synth
+from tests.gpu_util import rel_l2, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _cavity(smx, torch, spec, seed):
+    ctx = smx.Context(spec["p"], spec["nel"], eps=spec["eps"], mu=spec.get("mu", 1.0)).bind()
+    d = to_dev(synth.uniform(seed, ctx.N_e, -1.0, 1.0))
+    b = torch.zeros(ctx.N_h, dtype=torch.float64, device="cuda")
+    ctx.curl_primal(to_dev(synth.uniform(seed + 1, ctx.N_e, -1.0, 1.0)), b, 1.0)
+    e = torch.empty_like(d)
+    ctx.hodge_star(smx.FIELD_D, d, e)
+    h = torch.zeros_like(b)
+    return ctx, [d, b, e, h]
+
+
+SMALL = [
+    dict(p=2, nel=(6, 5, 7), eps=("blocks", synth.block_material(1, (3, 5, 1), 1.0, 4.0))),
+    dict(p=3, nel=8, eps=2.0, mu=1.5),
+    dict(p=4, nel=(5, 6, 4), eps=("blocks", synth.block_material(2, (5, 3, 2), 1.0, 4.0))),
+    dict(p=3, nel=(9, 8, 10), eps=("blocks", synth.block_material(3, (3, 2, 5), 1.0, 4.0))),
+]
+
+
+def test_batch_matches_single_cavity_steps():
+    import torch
+    from paper_2302_04979_gb300 import smx
+    nsteps = 20
+    cavs = [_cavity(smx, torch, s, 10 * i) for i, s in enumerate(SMALL)]
+    ref = []
+    for k, (ctx, st) in enumerate(cavs):
+        dt = 0.5 * ctx.cfl(iters=300, tol=1e-8)
+        jhat = to_dev(synth.uniform(77 + k, ctx.N_e, -1.0, 1.0)) if k % 2 == 0 else None
+        amp = to_dev(synth.uniform(88 + k, nsteps, -1.0, 1.0)) if jhat is not None else None
+        mine = [t.clone() for t in st]
+        ctx.step(*mine, dt, nsteps, jhat=jhat, amp=amp)
+        ref.append((mine, dt, jhat, amp))
+    batch = smx.Batch([c for c, _ in cavs])
+    for k, (ctx, st) in enumerate(cavs):
+        _, dt, jhat, amp = ref[k]
+        batch.set_state(k, *st, dt, jhat=jhat, amp=amp)
+    batch.step(nsteps)
+    batch.status()
+    for k, (ctx, st) in enumerate(cavs):
+        errs = [rel_l2(to_host(g), to_host(w)) for g, w in zip(st, ref[k][0])]
+        print("\ncavity %d (p=%s nel=%s): rel L2 d %.2e b %.2e e %.2e h %.2e" % (k, SMALL[k]["p"], SMALL[k]["nel"], *errs))
+        assert max(errs) < 1e-13
+
+
+def test_autotune_keeps_state():
+    import torch
+    from paper_2302_04979_gb300 import smx
+    cavs = [_cavity(smx, torch, s, 10 * i) for i, s in enumerate(SMALL[:2])]
+    batch = smx.Batch([c for c, _ in cavs])
+    for k, (ctx, st) in enumerate(cavs):
+        batch.set_state(k, *st, 1e-3)
+    before = [[to_host(t) for t in st] for _, st in cavs]
+    lw = batch.autotune(steps=2)
+    assert lw in (1, 2, 4, 8)
+    for (ctx, st), b0 in zip(cavs, before):
+        for t, t0 in zip(st, b0):
+            assert np.array_equal(to_host(t), t0)
+    batch.step(3)
+    batch.status()
+
+
+@pytest.mark.slow
+def test_batched_configuration_64_cavities():
+    """64 cavities of seeded uneven sizes (nel in [16, 48], even) and degrees p in {2, 3, 4}, each
+    with its own permittivity on a 2^3 block grid (seeded U[1, 4)) and its own Gaussian-pulse
+    source, 300 steps in persistent launches after autotuning; 8 sampled cavities against
+    single-cavity runs."""
+    import time
+    import torch
+    from paper_2302_04979_gb300 import smx
+    nsteps = 300
+    nel = 16 + 2 * (synth.splitmix64(4040, 64) % 17).astype(int)
+    p = 2 + (synth.splitmix64(4041, 64) % 3).astype(int)
+    cavs, extra = [], []
+    for k in range(64):
+        spec = dict(p=int(p[k]), nel=int(nel[k]), eps=("blocks", synth.block_material(4100 + k, (2, 2, 2), 1.0, 4.0)))
+        ctx, st = _cavity(smx, torch, spec, 5000 + 10 * k)
+        dt = 0.5 * ctx.cfl(iters=200, tol=1e-6)
+        shapes = [ctx.comp_shape(smx.FIELD_D, c) for c in range(3)]
+        jhat = to_dev(synth.bump_coefficients(4200 + k, shapes))
+        amp = to_dev(synth.source_amplitudes(dt, nsteps, f0=1.0, tau=0.25, t0=0.75))
+        cavs.append((ctx, st))
+        extra.append((dt, jhat, amp, [t.clone() for t in st]))
+    batch = smx.Batch([c for c, _ in cavs])
+    for k, (ctx, st) in enumerate(cavs):
+        batch.set_state(k, *st, extra[k][0], jhat=extra[k][1], amp=extra[k][2])
+    lw = batch.autotune(steps=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(nsteps)
+    batch.status()
+    el = time.perf_counter() - t0
+    dof = sum(c.N_e + c.N_h for c, _ in cavs)
+    print("\n64 cavities, %d DoF, %d steps: %.3f s, %.3e DoF-steps/s (line warps %d)" % (dof, nsteps, el,
+                                                                                       dof * nsteps / el, lw))
+    for k in range(0, 64, 8):
+        ctx, st = cavs[k]
+        dt, jhat, amp, mine = extra[k]
+        ctx.step(*mine, dt, nsteps, jhat=jhat, amp=amp)
+        errs = [rel_l2(to_host(g), to_host(w)) for g, w in zip(st, mine)]
+        assert max(errs) < 1e-12, (k, errs)
