@@ -495,7 +495,8 @@ int curl_dual_impl(smx_ctx* C, const double* h, double* d, double alpha, const d
 
 int hodge_apply_impl(smx_ctx* C, int h, const double* x, double* y) {
     const DevField& F = C->fld[kFieldOfHodge[h]];
-    CK(cudaMemsetAsync(y, 0, F.total * sizeof(double), C->stream));
+    int st = run(C, 20, 1, [&] { return launch_zero(y, F.total, C->stream); });
+    if (st) return st;
     if (C->hodge[h].mode == 0) return run(C, 2, 1, [&] { return launch_hodge_block(C->hb[h], x, y, C->stream); });
     return run(C, 3, 1, [&] { return launch_hodge_quad(C->hq[h], x, y, C->stream); });
 }
@@ -546,7 +547,8 @@ int pair_impl(smx_ctx* C, const double* z, const double* d, double* out) {
 // they cancel (block-Kronecker or quadrature Hodge, by the field's mode).
 int mass_f32(smx_ctx* C, int h, const double* x) {
     const long long ntot = C->fld[kFieldOfHodge[h]].total;
-    CK(cudaMemsetAsync(C->scratch, 0, (size_t)ntot * sizeof(double), C->stream));
+    const int st = run(C, 20, 1, [&] { return launch_zero(C->scratch, ntot, C->stream); });
+    if (st) return st;
     if (C->hodge[h].mode == 1)
         return run(C, 18, 1, [&] { return launch_hodge_quad_f32(C->hq32[h], x, C->scratch, C->stream); });
     return run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->scratch, C->stream); });
@@ -818,7 +820,15 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                             const std::vector<double> B =
                                 H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
                                             : inv[a][w];
-                            C->o_mode32[h][a][c] = C->blob.add(split_pairs(B));
+                            // CUDA-core kernel: transposed and zero padded to the kernel's output count,
+                            // Bt[k][i] = B[i][k] for i < npad, so the staging is one contiguous copy
+                            int maxn = 0;
+                            for (int c2 = 0; c2 < 3; ++c2) maxn = std::max(maxn, C->fld[fld].c[c2].n[a]);
+                            const int npad = mode_f32_npad(maxn);
+                            std::vector<double> Bt((size_t)n * npad, 0.0);
+                            for (int i = 0; i < n; ++i)
+                                for (int k = 0; k < n; ++k) Bt[(size_t)k * npad + i] = B[(size_t)i * n + k];
+                            C->o_mode32[h][a][c] = C->blob.add(split_pairs(Bt));
                             C->o_modetc[h][a][c] = C->blob.add(bf16_split_operator(B, n, mode_tc_npad(n)));
                         }
                 }
@@ -1033,12 +1043,22 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                 }
             B.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
             B.max_nloc = H.max_nloc;
+            for (int a = 0; a < 2; ++a) {
+                int m = 1;
+                for (int c = 0; c < 3; ++c)
+                    for (int t = 0; t < H.ntile[a]; ++t)
+                        m = std::max(m, H.tlen[a].empty() ? 1 : H.tlen[a][kFieldKinds[fld][c][a] * H.ntile[a] + t]);
+                B.max_len[a] = m;
+            }
             for (int a = 0; a < 3; ++a) {
                 ModeF32Args& Md = C->md32[h][a];
                 Md.field = C->fld[fld];
                 Md.axis = a;
                 for (int c = 0; c < 3; ++c)
                     Md.B[c] = C->use_mode ? reinterpret_cast<const float2*>(ws + C->o_mode32[h][a][c]) : nullptr;
+                int maxn = 0;
+                for (int c = 0; c < 3; ++c) maxn = std::max(maxn, C->fld[fld].c[c].n[a]);
+                Md.npad = mode_f32_npad(maxn);
                 ModeTcArgs& Mt = C->mtc[h][a];
                 Mt.field = C->fld[fld];
                 Mt.axis = a;

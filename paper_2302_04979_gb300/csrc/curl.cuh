@@ -18,6 +18,7 @@
 
 #include "convert.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace smx {
 
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kCurlThreads) curl_plane_kernel(DevField IN, D
                                                                   const double* __restrict__ jhat,
                                                                   const double* __restrict__ amp, int amp_index,
                                                                   double s_host) {
+    pdl_wait();
     const int p = blockIdx.x * kCurlThreads + threadIdx.x;
     const int k0 = blockIdx.y * kCurlKz;
     if (blockIdx.z == 0)
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(kCurlThreads) curl_plane_kernel(DevField IN, D
         curl_plane_comp<1, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0);
     else
         curl_plane_comp<2, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0);
+    pdl_trigger();
 }
 
 template <bool DUAL, class T>
@@ -100,8 +103,8 @@ static cudaError_t launch_curl_t(const DevField& IN, const DevField& OUT, const 
         nz = max(nz, OUT.c[c].n[2]);
     }
     const dim3 grid((plane + kCurlThreads - 1) / kCurlThreads, (nz + kCurlKz - 1) / kCurlKz, 3);
-    curl_plane_kernel<DUAL, T><<<grid, kCurlThreads, 0, s>>>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host);
-    return cudaGetLastError();
+    return launch_k(curl_plane_kernel<DUAL, T>, grid, dim3(kCurlThreads), 0, s, IN, OUT, in, out, alpha, jhat, amp,
+                    amp_index, s_host);
 }
 
 }  // namespace smx

@@ -14,7 +14,7 @@ constexpr int kPMax = 6;       // largest supported degree
 constexpr int kSolveLines = 32;  // lines per CTA in the pairing sweeps
 constexpr int kDotBlocks = 304;  // CTAs of the first reduction stage (2 x 152 SMs)
 constexpr int kCurlThreads = 256;  // curl: points of a component plane per CTA
-constexpr int kCurlKz = 8;         // curl: planes along z per thread
+constexpr int kCurlKz = 2;         // curl: planes along z per thread (more CTAs: latency-bound stencil)
 
 // One component of a field: extents (x, y, z) and offset in the global vector.
 struct DevComp {
@@ -90,6 +90,7 @@ struct HodgeBlockF32Args {
     const float2* tmat[3];
     const double* gamma;
     int max_nloc;
+    int max_len[2];      // largest tile length along x and y over the field's components (the CTA shape)
 };
 
 // FP32 quadrature Hodge apply: HodgeQuadArgs with FP32 basis values and metric.
@@ -119,12 +120,14 @@ struct LineF32Args {
 // Dense mode product along one axis: every line x of component c becomes B[c] x.
 struct ModeF32Args {
     DevField field;
-    const float2* B[3];  // per component: n x n, row-major, (hi, lo) pairs
+    const float2* B[3];  // per component: B^T, n rows of npad (hi, lo) pairs (zero past n)
     int axis;
+    int npad;            // mode_f32_npad(max line length)
 };
 constexpr int kModeMaxN = 80;  // largest line length the mode-product kernel handles
 
 cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const float* in32, float* out, cudaStream_t s);
+int mode_f32_npad(int maxn);  // padded output count of the CUDA-core kernel for lines up to maxn
 
 // The same mode products on the tensor cores (kernels_tc.cu): the operator as
 // three BF16 parts in the shared-memory layout of that file, built on the host
@@ -227,5 +230,6 @@ cudaError_t launch_mass_solve_axis(const MassSolveArgs& a, int kl, const double*
 cudaError_t launch_dot(const double* x, const double* y, long long n, double* partial, double* out,
                        cudaStream_t s);
 cudaError_t launch_scale_copy(const double* x, double* y, double a, long long n, cudaStream_t s);
+cudaError_t launch_zero(double* y, long long n, cudaStream_t s);  // y = 0 as a kernel of the launch chain
 
 }  // namespace smx

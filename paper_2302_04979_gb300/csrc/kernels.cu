@@ -9,6 +9,7 @@
 
 #include "curl.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace smx {
 
@@ -108,7 +109,9 @@ __device__ __forceinline__ void hodge_block_tile(const HodgeBlockArgs& A, int c,
 __global__ void __launch_bounds__(kHodgeThreads) hodge_block_kernel(HodgeBlockArgs A, const double* __restrict__ x,
                                                                     double* __restrict__ y) {
     extern __shared__ double sm[];
+    pdl_wait();
     hodge_block_tile(A, blockIdx.y, blockIdx.x, x, y, sm);
+    pdl_trigger();
 }
 
 cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s) {
@@ -120,7 +123,7 @@ cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double*
                              (int)((3 * kLMax * (kLMax + 1) + 2 * kLMax * kLMax * kLMax) * sizeof(double)));
         attr = true;
     }
-    if (ntiles > 0) hodge_block_kernel<<<dim3(ntiles, 3), kHodgeThreads, smem, s>>>(a, x, y);
+    if (ntiles > 0) return launch_k(hodge_block_kernel, dim3(ntiles, 3), dim3(kHodgeThreads), smem, s, a, x, y);
     return cudaGetLastError();
 }
 
@@ -134,6 +137,7 @@ constexpr int kQuadThreads = 128;
 __global__ void __launch_bounds__(kQuadThreads) hodge_quad_kernel(HodgeQuadArgs A, const double* __restrict__ x,
                                                                   double* __restrict__ y) {
     extern __shared__ double sm[];
+    pdl_wait();
     const int e = blockIdx.x;
     const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
     const int el[3] = {ex, ey, ez};
@@ -256,7 +260,7 @@ cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y
         cudaFuncSetAttribute(hodge_quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    if (nel > 0) hodge_quad_kernel<<<nel, kQuadThreads, smem, s>>>(a, x, y);
+    if (nel > 0) return launch_k(hodge_quad_kernel, dim3(nel), dim3(kQuadThreads), smem, s, a, x, y);
     return cudaGetLastError();
 }
 
@@ -387,7 +391,9 @@ template <int KL>
 __global__ void __launch_bounds__(kSolveLines) solve_axis_kernel(SolveArgs A, const double* __restrict__ in,
                                                                  double* __restrict__ out) {
     extern __shared__ double sm[];
+    pdl_wait();
     solve_lines<KL>(A, blockIdx.y, blockIdx.x, in, out, sm, threadIdx.x);
+    pdl_trigger();
 }
 
 template <int KL>
@@ -407,7 +413,7 @@ static cudaError_t launch_solve_t(const SolveArgs& a, const double* in, double* 
         attr = true;
     }
     const long long nb = (maxlines + kSolveLines - 1) / kSolveLines;
-    if (nb > 0) solve_axis_kernel<KL><<<dim3((unsigned)nb, 3), kSolveLines, smem, s>>>(a, in, out);
+    if (nb > 0) return launch_k(solve_axis_kernel<KL>, dim3((unsigned)nb, 3), dim3(kSolveLines), smem, s, a, in, out);
     return cudaGetLastError();
 }
 
@@ -553,7 +559,9 @@ template <int KL>
 __global__ void __launch_bounds__(kSolveLines) mass_solve_axis_kernel(MassSolveArgs A, const double* __restrict__ in,
                                                                       double* __restrict__ out) {
     extern __shared__ double sm[];
+    pdl_wait();
     mass_solve_lines<KL>(A, blockIdx.y, blockIdx.x, in, out, sm, threadIdx.x);
+    pdl_trigger();
 }
 
 template <int KL>
@@ -575,7 +583,8 @@ static cudaError_t launch_mass_solve_t(const MassSolveArgs& a, const double* in,
         attr = true;
     }
     const long long nb = (maxlines + kSolveLines - 1) / kSolveLines;
-    if (nb > 0) mass_solve_axis_kernel<KL><<<dim3((unsigned)nb, 3), kSolveLines, smem, s>>>(a, in, out);
+    if (nb > 0)
+        return launch_k(mass_solve_axis_kernel<KL>, dim3((unsigned)nb, 3), dim3(kSolveLines), smem, s, a, in, out);
     return cudaGetLastError();
 }
 
@@ -639,6 +648,19 @@ cudaError_t launch_scale_copy(const double* x, double* y, double a, long long n,
     const long long nb = (n + 255) / 256;
     if (nb > 0) scale_copy_kernel<<<(unsigned)nb, 256, 0, s>>>(x, y, a, n);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ y = 0 (in the launch chain of a step)
+__global__ void zero_kernel(double* __restrict__ y, long long n) {
+    pdl_wait();
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = 0.0;
+    pdl_trigger();
+}
+
+cudaError_t launch_zero(double* y, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    return launch_k(zero_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, y, n);
 }
 
 // ------------------------------------------------------------------ batched cavities

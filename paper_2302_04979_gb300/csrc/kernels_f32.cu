@@ -14,6 +14,7 @@
 
 #include "convert.cuh"
 #include "curl.cuh"
+#include "pdl.cuh"
 #include "internal.h"
 
 namespace smx {
@@ -27,6 +28,10 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async8f(void* smem, const void* gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16f(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all_f() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -43,19 +48,21 @@ cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, 
 
 // ------------------------------------------------------------------ casts
 __global__ void cast_d2f_kernel(const double* __restrict__ x, float* __restrict__ y, long long n) {
+    pdl_wait();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = d2f_rn(x[i]);
 }
 __global__ void cast_f2d_kernel(const float* __restrict__ x, double* __restrict__ y, long long n) {
+    pdl_wait();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = f2d_exact(x[i]);
 }
 cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t s) {
-    if (n > 0) cast_d2f_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    if (n > 0) return launch_k(cast_d2f_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, x, y, n);
     return cudaGetLastError();
 }
 cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t s) {
-    if (n > 0) cast_f2d_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    if (n > 0) return launch_k(cast_f2d_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, x, y, n);
     return cudaGetLastError();
 }
 
@@ -69,6 +76,7 @@ template <class TIN>
 __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args A, const TIN* __restrict__ x,
                                                               double* __restrict__ y) {
     extern __shared__ float smf[];
+    pdl_wait();
     const int c = blockIdx.y;
     const int tile = blockIdx.x;
     const int tx = tile % A.ntile[0];
@@ -97,8 +105,8 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     const int Lx = L[0], Ly = L[1], Lz = L[2];
     const int nloc = Lx * Ly * Lz;
     float* s1 = s0 + nloc;
-    const int flat = threadIdx.y * 16 + threadIdx.x;
-    for (int t = flat; t < kLMax * kLMax; t += 256) {
+    const int flat = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
+    for (int t = flat; t < kLMax * kLMax; t += nthreads) {
         const int d = (t / kLMax) * kLd + t % kLMax;
         Mx[d] = gmat[0][t];
         My[d] = gmat[1][t];
@@ -153,11 +161,11 @@ cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64
     const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
     const size_t smem = 3 * kLMax * (kLMax + 1) * sizeof(float2) + 2 * (size_t)a.max_nloc * sizeof(float);
     if (ntiles == 0) return cudaSuccess;
+    // one thread per (x, y) position of the largest tile face: no idle rows or columns of a 16 x 16 block
+    const dim3 block(a.max_len[0], a.max_len[1]);
     if (x64)
-        hodge_block_f32_kernel<double><<<dim3(ntiles, 3), dim3(16, 16), smem, s>>>(a, x64, y);
-    else
-        hodge_block_f32_kernel<float><<<dim3(ntiles, 3), dim3(16, 16), smem, s>>>(a, x32, y);
-    return cudaGetLastError();
+        return launch_k(hodge_block_f32_kernel<double>, dim3(ntiles, 3), block, smem, s, a, x64, y);
+    return launch_k(hodge_block_f32_kernel<float>, dim3(ntiles, 3), block, smem, s, a, x32, y);
 }
 
 // ------------------------------------------------------------------ Hodge: quadrature, FP32
@@ -174,6 +182,7 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
                                                                         const double* __restrict__ x,
                                                                         double* __restrict__ y) {
     extern __shared__ float smq[];
+    pdl_wait();
     const int e = blockIdx.x;
     const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
     const int el[3] = {ex, ey, ez};
@@ -287,7 +296,7 @@ cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, do
         cudaFuncSetAttribute(hodge_quad_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    if (nel > 0) hodge_quad_f32_kernel<<<nel, kQuadF32Threads, smem, s>>>(a, x, y);
+    if (nel > 0) return launch_k(hodge_quad_f32_kernel, dim3(nel), dim3(kQuadF32Threads), smem, s, a, x, y);
     return cudaGetLastError();
 }
 
@@ -445,6 +454,7 @@ template <int KL, bool MASS, class TIN>
 __global__ void __launch_bounds__(kSolveLines) line_f32_kernel(LineF32Args A, const TIN* __restrict__ in,
                                                                float* __restrict__ out) {
     extern __shared__ float smf[];
+    pdl_wait();
     if (!MASS) {
         line_body_f<KL, 0, false, TIN>(A, in, out, smf);
         return;
@@ -479,7 +489,8 @@ static cudaError_t launch_line_t(const LineF32Args& a, const TIN* in, float* out
         attr = true;
     }
     const long long nb = (maxlines + kSolveLines - 1) / kSolveLines;
-    if (nb > 0) line_f32_kernel<KL, MASS, TIN><<<dim3((unsigned)nb, 3), kSolveLines, smem, s>>>(a, in, out);
+    if (nb > 0)
+        return launch_k(line_f32_kernel<KL, MASS, TIN>, dim3((unsigned)nb, 3), dim3(kSolveLines), smem, s, a, in, out);
     return cudaGetLastError();
 }
 
@@ -528,6 +539,7 @@ template <class TIN, int NOUT>
 __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kernel(ModeF32Args A, const TIN* in,
                                                                                    float* out) {
     extern __shared__ float smf[];
+    pdl_wait();
     const int c = blockIdx.y;
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
@@ -540,14 +552,9 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
     float2* Bt = reinterpret_cast<float2*>(smf);                // n x NPAD (transposed, zero padded)
     float* T = reinterpret_cast<float*>(Bt + n * NPAD);         // n x kModeLd (16-byte aligned rows)
     const int tid = threadIdx.x, nt = blockDim.x;
+    // the table is already transposed and padded: one contiguous copy, 16 bytes per cp.async
     const float2* Bg = A.B[c];
-    for (int t = tid; t < n * NPAD; t += nt) {
-        const int j = t / NPAD, i = t - j * NPAD;
-        if (i < n)
-            cp_async8f(Bt + t, Bg + i * n + j);
-        else
-            Bt[t] = make_float2(0.0f, 0.0f);
-    }
+    for (int t = tid; t < n * NPAD / 2; t += nt) cp_async16f(Bt + 2 * t, Bg + 2 * t);
     const int nx = C.n[0], nxy = C.n[0] * C.n[1];
     const TIN* src = in + C.off;
     if (axis == 0) {
@@ -630,11 +637,12 @@ static cudaError_t launch_mode_t(const ModeF32Args& a, const double* in64, const
     }
     const dim3 grid((unsigned)nb, 3);
     if (in64)
-        mode_f32_kernel<double, NOUT><<<grid, kModeLineGroups * kModeOutGroups, smem, s>>>(a, in64, out);
-    else
-        mode_f32_kernel<float, NOUT><<<grid, kModeLineGroups * kModeOutGroups, smem, s>>>(a, in32, out);
-    return cudaGetLastError();
+        return launch_k(mode_f32_kernel<double, NOUT>, grid, dim3(kModeLineGroups * kModeOutGroups), smem, s, a, in64,
+                        out);
+    return launch_k(mode_f32_kernel<float, NOUT>, grid, dim3(kModeLineGroups * kModeOutGroups), smem, s, a, in32, out);
 }
+
+int mode_f32_npad(int maxn) { return kModeOutGroups * ((maxn + kModeOutGroups - 1) / kModeOutGroups); }
 
 cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const float* in32, float* out, cudaStream_t s) {
     long long maxlines = 0;
@@ -648,10 +656,13 @@ cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const floa
     if (maxn > kModeMaxN) return cudaErrorInvalidValue;
     const long long nb = (maxlines + kModeLines - 1) / kModeLines;
     if (nb == 0) return cudaSuccess;
+    if (a.npad != mode_f32_npad(maxn)) return cudaErrorInvalidValue;
     switch ((maxn + kModeOutGroups - 1) / kModeOutGroups) {
         case 1: return launch_mode_t<1>(a, in64, in32, out, maxn, nb, s);
         case 2: return launch_mode_t<2>(a, in64, in32, out, maxn, nb, s);
         case 3: return launch_mode_t<3>(a, in64, in32, out, maxn, nb, s);
+        case 4: return launch_mode_t<4>(a, in64, in32, out, maxn, nb, s);
+        case 5: return launch_mode_t<5>(a, in64, in32, out, maxn, nb, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -49,6 +49,7 @@
 
 #include "convert.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace smx {
 namespace {
@@ -172,6 +173,7 @@ __constant__ int kTcPairB[6] = {0, 1, 2, 0, 1, 0};
 template <class TIN>
 __global__ void __launch_bounds__(kTcThreads) mode_tc_kernel(ModeTcArgs A, const TIN* in, float* out, double* out64) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();
     const int c = blockIdx.y;
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
@@ -337,6 +339,7 @@ __global__ void __launch_bounds__(kTcThreads) mode_tc_kernel(ModeTcArgs A, const
     tc_fence_before();
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    pdl_trigger();  // after the tensor memory is released
 }
 
 }  // namespace
@@ -366,10 +369,8 @@ cudaError_t launch_mode_tc(const ModeTcArgs& a, const double* in64, const float*
     const dim3 grid((unsigned)((maxlines + kTcLines - 1) / kTcLines), 3);
     const size_t smem = (size_t)tc_smem_bytes(maxpad);
     if (in64)
-        mode_tc_kernel<double><<<grid, kTcThreads, smem, s>>>(a, in64, out, out64);
-    else
-        mode_tc_kernel<float><<<grid, kTcThreads, smem, s>>>(a, in32, out, out64);
-    return cudaGetLastError();
+        return launch_k(mode_tc_kernel<double>, grid, dim3(kTcThreads), smem, s, a, in64, out, out64);
+    return launch_k(mode_tc_kernel<float>, grid, dim3(kTcThreads), smem, s, a, in32, out, out64);
 }
 
 }  // namespace smx
