@@ -109,6 +109,19 @@ def reduce_max(value, world):
     return float(t.item())
 
 
+def job_rate(units_this_rank, seconds_this_rank, world):
+    """Whole-job throughput: all ranks' units / the slowest rank's time (max over ranks)."""
+    return reduce_sum(units_this_rank, world) / reduce_max(seconds_this_rank, world)
+
+
+def init_dist(world):
+    """One process per GPU: NCCL when CUDA is present, gloo otherwise (CPU runs of the host logic)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
 def reduce_sum(value, world):
     if world == 1:
         return value
@@ -193,6 +206,9 @@ NCU_TRAFFIC = {
     "mass_solve_x": 6.90e6, "mass_solve_y": 6.90e6, "mass_solve_z": 6.90e6,
     "solve_x": 6.72e6, "solve_y": 6.72e6, "solve_z": 6.72e6,
     "hodge_block": 13.51e6,
+    # mixed step, CUDA-core line operators (x passes read FP64 input)
+    "line_f32_x": 6.93e6, "line_f32_y": 3.56e6, "line_f32_z": 3.56e6,
+    "hodge_block_f32": 13.51e6,
 }
 
 
@@ -407,9 +423,8 @@ def main():
         return
     if world > 1:
         import torch
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        init_dist(world)
     out = run_ours(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist

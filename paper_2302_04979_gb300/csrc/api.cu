@@ -480,23 +480,29 @@ int run(smx_ctx* C, int cls, int nkernels, F&& f) {
     return SMX_OK;
 }
 
-int curl_primal_impl(smx_ctx* C, const double* e, double* b, double alpha) {
+// zero (optional): the curl also clears this vector over its output range, so the
+// Hodge apply that follows (accumulating into it) needs no zeroing launch.
+int curl_primal_impl(smx_ctx* C, const double* e, double* b, double alpha, double* zero = nullptr) {
     return run(C, 0, 1, [&] {
-        return launch_curl_primal(C->fld[SMX_FIELD_E], C->fld[SMX_FIELD_B], e, b, alpha, C->stream);
+        return launch_curl_primal(C->fld[SMX_FIELD_E], C->fld[SMX_FIELD_B], e, b, alpha, C->stream, zero);
     });
 }
 
 int curl_dual_impl(smx_ctx* C, const double* h, double* d, double alpha, const double* jhat, const double* amp,
-                   int idx, double s) {
+                   int idx, double s, double* zero = nullptr) {
     return run(C, 1, 1, [&] {
-        return launch_curl_dual(C->fld[SMX_FIELD_H], C->fld[SMX_FIELD_D], h, d, alpha, jhat, amp, idx, s, C->stream);
+        return launch_curl_dual(C->fld[SMX_FIELD_H], C->fld[SMX_FIELD_D], h, d, alpha, jhat, amp, idx, s, C->stream,
+                                zero);
     });
 }
 
-int hodge_apply_impl(smx_ctx* C, int h, const double* x, double* y) {
+// y = M x; prezeroed: y is already zero (cleared by the preceding curl)
+int hodge_apply_impl(smx_ctx* C, int h, const double* x, double* y, bool prezeroed = false) {
     const DevField& F = C->fld[kFieldOfHodge[h]];
-    int st = run(C, 20, 1, [&] { return launch_zero(y, F.total, C->stream); });
-    if (st) return st;
+    if (!prezeroed) {
+        const int st = run(C, 20, 1, [&] { return launch_zero(y, F.total, C->stream); });
+        if (st) return st;
+    }
     if (C->hodge[h].mode == 0) return run(C, 2, 1, [&] { return launch_hodge_block(C->hb[h], x, y, C->stream); });
     return run(C, 3, 1, [&] { return launch_hodge_quad(C->hq[h], x, y, C->stream); });
 }
@@ -545,16 +551,19 @@ int pair_impl(smx_ctx* C, const double* z, const double* d, double* out) {
 // scratch = M x: FP32 element (or tile) contributions, summed in FP64 -- with up to
 // (p+1)^3 contributions per coefficient an FP32 sum would lose accuracy where
 // they cancel (block-Kronecker or quadrature Hodge, by the field's mode).
-int mass_f32(smx_ctx* C, int h, const double* x) {
+int mass_f32(smx_ctx* C, int h, const double* x, bool prezeroed) {
     const long long ntot = C->fld[kFieldOfHodge[h]].total;
-    const int st = run(C, 20, 1, [&] { return launch_zero(C->scratch, ntot, C->stream); });
-    if (st) return st;
+    if (!prezeroed) {
+        const int st = run(C, 20, 1, [&] { return launch_zero(C->scratch, ntot, C->stream); });
+        if (st) return st;
+    }
     if (C->hodge[h].mode == 1)
         return run(C, 18, 1, [&] { return launch_hodge_quad_f32(C->hq32[h], x, C->scratch, C->stream); });
     return run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->scratch, C->stream); });
 }
 
-int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* out64 = nullptr) {
+int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* out64 = nullptr,
+                        bool prezeroed = false) {
     int st;
     const long long ntot = C->fld[kFieldOfHodge[h]].total;
     auto widen = [&]() {
@@ -565,7 +574,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         const double* x64 = x;
         const float* x32 = nullptr;
         if (!C->hodge[h].separable) {
-            if ((st = mass_f32(C, h, x))) return st;
+            if ((st = mass_f32(C, h, x, prezeroed))) return st;
             x64 = C->scratch;
         }
         const bool tc = C->mode_kernel == SMX_MODE_TENSOR;
@@ -588,7 +597,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         st = run(C, 16, 1, [&] { return launch_line_f32(C->ln32[h][2], C->p[2] - 1, true, nullptr, out, out, C->stream); });
         return st ? st : widen();
     }
-    if ((st = mass_f32(C, h, x))) return st;
+    if ((st = mass_f32(C, h, x, prezeroed))) return st;
     st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, false, C->scratch, nullptr, out, C->stream); });
     if (st) return st;
     st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, false, nullptr, out, out, C->stream); });
@@ -603,34 +612,48 @@ int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
                    &FD = C->fld[SMX_FIELD_D];
     int st = run(C, 17, 1, [&] { return launch_cast_d2f(e, C->e32, C->N_e, C->stream); });
     if (st) return st;
-    st = run(C, 11, 1, [&] { return launch_curl_f32(false, FE, FB, C->e32, b, -0.5 * dt, nullptr, nullptr, 0, 0.0, C->stream); });
+    // the curl before a star that accumulates a mass apply also clears that accumulator
+    const bool zH = !C->hodge[0].separable, zD = !C->hodge[1].separable;
+    double* zeroH = zH ? C->scratch : nullptr;
+    double* zeroD = zD ? C->scratch : nullptr;
+    st = run(C, 11, 1, [&] {
+        return launch_curl_f32(false, FE, FB, C->e32, b, -0.5 * dt, nullptr, nullptr, 0, 0.0, C->stream, zeroH);
+    });
     if (st) return st;
     for (int n = 0; n < nsteps; ++n) {
         const bool last = n + 1 == nsteps;  // the last stars also write the FP64 1-forms h and e
-        if ((st = hodge_star_f32_impl(C, 0, b, C->h32, last ? h : nullptr))) return st;
-        st = run(C, 12, 1, [&] { return launch_curl_f32(true, FH, FD, C->h32, d, dt, jhat, amp, n, 0.0, C->stream); });
+        if ((st = hodge_star_f32_impl(C, 0, b, C->h32, last ? h : nullptr, zH))) return st;
+        st = run(C, 12, 1, [&] {
+            return launch_curl_f32(true, FH, FD, C->h32, d, dt, jhat, amp, n, 0.0, C->stream, zeroD);
+        });
         if (st) return st;
-        if ((st = hodge_star_f32_impl(C, 1, d, C->e32, last ? e : nullptr))) return st;
+        if ((st = hodge_star_f32_impl(C, 1, d, C->e32, last ? e : nullptr, zD))) return st;
         const double alpha = (n + 1 == nsteps) ? -0.5 * dt : -dt;
-        st = run(C, 11, 1, [&] { return launch_curl_f32(false, FE, FB, C->e32, b, alpha, nullptr, nullptr, 0, 0.0, C->stream); });
+        st = run(C, 11, 1, [&] {
+            return launch_curl_f32(false, FE, FB, C->e32, b, alpha, nullptr, nullptr, 0, 0.0, C->stream, zeroH);
+        });
         if (st) return st;
     }
     return SMX_OK;
 }
 
-int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out);
+int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezeroed = false);
 
 // nsteps kick-drift-kick steps enqueued kernel by kernel (the inner half kicks of b merged).
 int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp, double dt,
                int nsteps) {
     if (C->precision == SMX_MIXED) return step_mixed(C, d, b, e, h, jhat, amp, dt, nsteps);
-    int st = curl_primal_impl(C, e, b, -0.5 * dt);
+    // the curl before a star that accumulates a mass apply also clears that accumulator
+    const bool zH = !C->hodge[0].separable, zD = !C->hodge[1].separable;
+    double* zeroH = zH ? C->scratch : nullptr;
+    double* zeroD = zD ? C->scratch : nullptr;
+    int st = curl_primal_impl(C, e, b, -0.5 * dt, zeroH);
     if (st) return st;
     for (int n = 0; n < nsteps; ++n) {
-        if ((st = hodge_star_impl(C, 0, b, h))) return st;  // h = K~_1^{-1} M^2_{1/mu} b
-        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0))) return st;
-        if ((st = hodge_star_impl(C, 1, d, e))) return st;  // e = K_1^{-1} M~^2_{1/eps} d
-        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt))) return st;
+        if ((st = hodge_star_impl(C, 0, b, h, zH))) return st;  // h = K~_1^{-1} M^2_{1/mu} b
+        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0, zeroD))) return st;
+        if ((st = hodge_star_impl(C, 1, d, e, zD))) return st;  // e = K_1^{-1} M~^2_{1/eps} d
+        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt, zeroH))) return st;
     }
     return SMX_OK;
 }
@@ -639,7 +662,7 @@ int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
 // Eq. discrete2_hodge_eps for h = 1): three fused mass+solve line passes when
 // the field's mass is a single Kronecker product, else mass apply into the
 // scratch vector followed by the three pairing sweeps.
-int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out) {
+int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezeroed) {
     const int which = h == 0 ? 1 : 0;
     if (C->hodge[h].separable) {
         int st = run(C, 8, 1, [&] { return launch_mass_solve_axis(C->ms[h][0], C->p[0] - 1, x, out, C->stream); });
@@ -648,7 +671,7 @@ int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out) {
         if (st) return st;
         return run(C, 10, 1, [&] { return launch_mass_solve_axis(C->ms[h][2], C->p[2] - 1, out, out, C->stream); });
     }
-    const int st = hodge_apply_impl(C, h, x, C->scratch);
+    const int st = hodge_apply_impl(C, h, x, C->scratch, prezeroed);
     if (st) return st;
     return solve_impl(C, which, C->scratch, out);
 }

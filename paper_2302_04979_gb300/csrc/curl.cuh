@@ -42,7 +42,8 @@ template <int C, bool DUAL, class T>
 __device__ __forceinline__ void curl_plane_comp(const DevField& IN, const DevField& OUT, const T* __restrict__ in,
                                                 double* __restrict__ out, double alpha,
                                                 const double* __restrict__ jhat, const double* __restrict__ amp,
-                                                int amp_index, double s_host, int p, int k0) {
+                                                int amp_index, double s_host, int p, int k0,
+                                                double* __restrict__ zero) {
     constexpr int a1 = (C + 1) % 3, a2 = (C + 2) % 3;
     const DevComp& O = OUT.c[C];
     const int nx = O.n[0], nxy = O.n[0] * O.n[1];
@@ -70,7 +71,9 @@ __device__ __forceinline__ void curl_plane_comp(const DevField& IN, const DevFie
         if (kk < nk) {
             double v = widen(d1[kk] - d2[kk]);
             if (DUAL && jhat != nullptr) v = fma(-s, jv[kk], v);
-            out[O.off + p + (long long)nxy * (k0 + kk)] = fma(alpha, v, o[kk]);
+            const long long g = O.off + p + (long long)nxy * (k0 + kk);
+            out[g] = fma(alpha, v, o[kk]);
+            if (zero) zero[g] = 0.0;  // the accumulation target of the next Hodge apply
         }
     }
 }
@@ -80,22 +83,23 @@ __global__ void __launch_bounds__(kCurlThreads) curl_plane_kernel(DevField IN, D
                                                                   double* __restrict__ out, double alpha,
                                                                   const double* __restrict__ jhat,
                                                                   const double* __restrict__ amp, int amp_index,
-                                                                  double s_host) {
+                                                                  double s_host, double* __restrict__ zero) {
     pdl_wait();
     const int p = blockIdx.x * kCurlThreads + threadIdx.x;
     const int k0 = blockIdx.y * kCurlKz;
     if (blockIdx.z == 0)
-        curl_plane_comp<0, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0);
+        curl_plane_comp<0, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0, zero);
     else if (blockIdx.z == 1)
-        curl_plane_comp<1, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0);
+        curl_plane_comp<1, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0, zero);
     else
-        curl_plane_comp<2, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0);
+        curl_plane_comp<2, DUAL, T>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, p, k0, zero);
     pdl_trigger();
 }
 
 template <bool DUAL, class T>
 static cudaError_t launch_curl_t(const DevField& IN, const DevField& OUT, const T* in, double* out, double alpha,
-                                 const double* jhat, const double* amp, int amp_index, double s_host, cudaStream_t s) {
+                                 const double* jhat, const double* amp, int amp_index, double s_host, cudaStream_t s,
+                                 double* zero = nullptr) {
     if (OUT.total == 0) return cudaSuccess;
     int plane = 0, nz = 0;
     for (int c = 0; c < 3; ++c) {
@@ -104,7 +108,7 @@ static cudaError_t launch_curl_t(const DevField& IN, const DevField& OUT, const 
     }
     const dim3 grid((plane + kCurlThreads - 1) / kCurlThreads, (nz + kCurlKz - 1) / kCurlKz, 3);
     return launch_k(curl_plane_kernel<DUAL, T>, grid, dim3(kCurlThreads), 0, s, IN, OUT, in, out, alpha, jhat, amp,
-                    amp_index, s_host);
+                    amp_index, s_host, zero);
 }
 
 }  // namespace smx

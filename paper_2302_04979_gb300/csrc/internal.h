@@ -143,9 +143,11 @@ int mode_tc_npad(int n);
 // out64 (optional): the result also widened to FP64.
 cudaError_t launch_mode_tc(const ModeTcArgs& a, const double* in64, const float* in32, float* out, double* out64,
                            cudaStream_t s);
+// zero (optional): also set zero[i] = 0 for every output index i (the accumulation
+// target of the Hodge apply that follows the curl).
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
-                            cudaStream_t s);
+                            cudaStream_t s, double* zero = nullptr);
 cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
 cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
 cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, double* y,
@@ -218,10 +220,10 @@ size_t batch_line_warp_doubles(int maxn, int kl);  // staging of one line warp
 
 // ---- launchers (kernels.cu); all enqueue on `s` and return cudaGetLastError()
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b,
-                               double alpha, cudaStream_t s);
+                               double alpha, cudaStream_t s, double* zero = nullptr);
 cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double* h, double* d,
                              double alpha, const double* jhat, const double* amp, int amp_index,
-                             double s_host, cudaStream_t s);
+                             double s_host, cudaStream_t s, double* zero = nullptr);
 cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_solve_axis(const SolveArgs& a, int kl, const double* in, double* out, cudaStream_t s);

@@ -15,14 +15,14 @@ namespace smx {
 
 // ------------------------------------------------------------------ curl (see curl.cuh)
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b, double alpha,
-                               cudaStream_t s) {
-    return launch_curl_t<false, double>(E, B, e, b, alpha, nullptr, nullptr, 0, 0.0, s);
+                               cudaStream_t s, double* zero) {
+    return launch_curl_t<false, double>(E, B, e, b, alpha, nullptr, nullptr, 0, 0.0, s, zero);
 }
 
 cudaError_t launch_curl_dual(const DevField& H, const DevField& D, const double* h, double* d, double alpha,
                              const double* jhat, const double* amp, int amp_index, double s_host,
-                             cudaStream_t s) {
-    return launch_curl_t<true, double>(H, D, h, d, alpha, jhat, amp, amp_index, s_host, s);
+                             cudaStream_t s, double* zero) {
+    return launch_curl_t<true, double>(H, D, h, d, alpha, jhat, amp, amp_index, s_host, s, zero);
 }
 
 // ------------------------------------------------------------------ Hodge: block Kronecker
@@ -721,9 +721,12 @@ __device__ __noinline__ void batch_curl(const BatchCavity& K, int unit, const do
     const DevField& IN = DUAL ? K.fH : K.fE;
     const DevField& OUT = DUAL ? K.fD : K.fB;
     const int p = pb * kCurlThreads + threadIdx.x;
-    if (c == 0) curl_plane_comp<0, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz);
-    else if (c == 1) curl_plane_comp<1, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz);
-    else curl_plane_comp<2, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz);
+    if (c == 0)
+        curl_plane_comp<0, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz, nullptr);
+    else if (c == 1)
+        curl_plane_comp<1, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz, nullptr);
+    else
+        curl_plane_comp<2, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz, nullptr);
 }
 
 // Each variant is its own (not inlined) function, so the persistent kernel

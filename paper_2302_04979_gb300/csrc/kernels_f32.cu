@@ -41,9 +41,9 @@ __device__ __forceinline__ float to_f(float v) { return v; }
 // ------------------------------------------------------------------ curl (FP32 differences, FP64 state; curl.cuh)
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
-                            cudaStream_t s) {
-    if (dual) return launch_curl_t<true, float>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, s);
-    return launch_curl_t<false, float>(IN, OUT, in, out, alpha, nullptr, nullptr, 0, 0.0, s);
+                            cudaStream_t s, double* zero) {
+    if (dual) return launch_curl_t<true, float>(IN, OUT, in, out, alpha, jhat, amp, amp_index, s_host, s, zero);
+    return launch_curl_t<false, float>(IN, OUT, in, out, alpha, nullptr, nullptr, 0, 0.0, s, zero);
 }
 
 // ------------------------------------------------------------------ casts

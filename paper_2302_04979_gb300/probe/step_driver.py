@@ -3,8 +3,10 @@
 p = 3, 64^3 elements, identity map, permittivity on a seeded 8^3 block grid,
 mu = 1; one Hodge star and two single steps per form, kernels launched
 eagerly on the default stream (no CUDA graph), so ncu sees every launch.
+"mixed" uses the default (FP32 CUDA-core) line operators, "mixed-tc" the
+tensor-core ones.
 
-  python paper_2302_04979_gb300/probe/step_driver.py [fp64|mixed|both]
+  python paper_2302_04979_gb300/probe/step_driver.py [fp64|mixed|mixed-tc|both]
 """
 import os
 import sys
@@ -16,8 +18,11 @@ def main(forms):
     import torch
     from paper_2302_04979_gb300 import smx, synth
     eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
-    for prec in forms:
+    for form in forms:
+        prec = "mixed" if form.startswith("mixed") else form
         ctx = smx.Context(3, 64, eps=eps, mu=1.0, precision=prec).bind()
+        if form == "mixed-tc":
+            ctx.set_mode_kernel("tensor")
         d = torch.as_tensor(synth.uniform(1, ctx.N_e, -1.0, 1.0)).cuda()
         b = torch.zeros(ctx.N_h, dtype=torch.float64, device="cuda")
         e = torch.empty_like(d)
@@ -26,7 +31,7 @@ def main(forms):
         for _ in range(2):
             ctx.step(d, b, e, h, 1e-3, 1)
         torch.cuda.synchronize()
-        print(prec, "ok", float(d.norm()))
+        print(form, "ok", float(d.norm()))
 
 
 if __name__ == "__main__":

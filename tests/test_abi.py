@@ -99,3 +99,26 @@ def test_mode_kernel_selection(smx):
     ctx.set_mode_kernel("simt")
     ctx.set_mode_kernel("tensor")
     assert smx.library().smx_set_mode_kernel(ctx.h, 7) == smx.EINVAL
+
+
+def test_reverse_mode_and_batch_argument_errors(smx):
+    lib = smx.library()
+    ctx = smx.Context(2, 4, eps=("blocks", np.full((2, 2, 2), 2.0)))
+    v = ctypes.c_void_p(8)
+    # reverse mode needs a bound workspace
+    assert lib.smx_step_adjoint(ctx.h, v, v, v, v, None, None, 0.1, None, None) == smx.ESTATE
+    assert lib.smx_adjoint_terminal(ctx.h, v, v, v, None) == smx.ESTATE
+    assert lib.smx_set_material_blocks(ctx.h, smx.FIELD_D, v) == smx.ESTATE
+    assert lib.smx_receivers_eval(ctx.h, v, v) == smx.ESTATE
+    # receivers: before binding only, points in [0, 1], once
+    assert lib.smx_receivers_set(ctx.h, -1, None) == smx.EINVAL
+    bad = np.array([[0.5, 1.5, 0.5]])
+    assert lib.smx_receivers_set(ctx.h, 1, bad.ctypes.data_as(ctypes.c_void_p)) == smx.EINVAL
+    ok = np.array([[0.5, 0.25, 0.75], [0.1, 0.9, 0.3]])
+    assert lib.smx_receivers_set(ctx.h, 2, ok.ctypes.data_as(ctypes.c_void_p)) == smx.OK
+    assert lib.smx_receivers_set(ctx.h, 2, ok.ctypes.data_as(ctypes.c_void_p)) == smx.ESTATE
+    # a batch needs bound contexts
+    arr = (ctypes.c_void_p * 1)(ctx.h.value)
+    out = ctypes.c_void_p()
+    assert lib.smx_batch_create(1, arr, ctypes.byref(out)) == smx.EINVAL
+    assert lib.smx_batch_create(0, arr, ctypes.byref(out)) == smx.EINVAL
