@@ -190,6 +190,8 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "line_operators": "auto: separable star on the tensor cores (exact BF16 digit products), "
+                                 "pairing sweeps as FP64 banded recurrences",
            "config": workload_config(ne, nh),
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -198,6 +200,8 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ GPU arm
 HBM_PEAK_GBS = 6793.1   # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+BF16_PEAK_TFLOPS = 1992.0  # MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)
+DIGIT_PAIRS = 28           # digit products (levels 0..6 of seven digits) per FP64 dense line product
 
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel at this
 # workload (profiles/fp64_step_p3_64cube.md, profiles/mixed_step_p3_64cube.md; cold
@@ -225,7 +229,8 @@ def kernel_table(ctx, smx, ktimes):
               "mass_solve_x": sep, "mass_solve_y": sep, "mass_solve_z": sep,
               "curl_primal_f32": [smx.FIELD_B], "curl_dual_f32": [smx.FIELD_D],
               "hodge_block_f32": [f for f in (smx.FIELD_B, smx.FIELD_D) if mode[f] == 0],
-              "line_f32_x": both, "line_f32_y": both, "line_f32_z": both}
+              "line_f32_x": both, "line_f32_y": both, "line_f32_z": both,
+              "line_f64tc_x": both, "line_f64tc_y": both, "line_f64tc_z": both}
     kern = {}
     for name, (ms, cnt) in ktimes.items():
         if cnt == 0 or name not in fields:
@@ -370,14 +375,23 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": 8 * (2 * ne + nh), "d2h_bytes_per_step": 8 * (2 * ne + 2 * nh),
            "call": "smx_step_host (pinned host d, b, e in; d, b, e, h out; nsteps=1 per call)"}
 
-    # ---- roofline of the dominant kernel: FP64 form is bound by the FP64 pipe
+    # ---- roofline of the dominant kernel: the FP64 kernels are bound by the FP64 pipe; the
+    # digit-sliced line operators by the BF16 tensor pipe (28 digit products of 2 n flops per entry)
     dom = max(kern, key=lambda n: kern[n]["total_ms"])
-    roof = {"kernel": dom, "bound": "alu", "achieved": kern[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": kern[dom]["fp64_tflops"] / FP64_PEAK_TFLOPS,
-            "traffic": NCU_TRAFFIC.get(dom),
-            "peak_source": "FP64 unit count x clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
-                           "MEASURED_PEAKS.json has no FP64 entry; the FMA probe measured 1.19 TFLOP/s",
-            "hbm_gbs": kern[dom]["gbs"]}
+    if dom.startswith("line_f64tc"):
+        tc = DIGIT_PAIRS * kern[dom]["fp64_tflops"]
+        roof = {"kernel": dom, "bound": "tensor", "achieved": tc, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tc / BF16_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured, burst)",
+                "work": "28 BF16 digit products x 2 n flops per line entry (no padding counted)",
+                "fp64_equivalent_tflops": kern[dom]["fp64_tflops"], "hbm_gbs": kern[dom]["gbs"]}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": kern[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": kern[dom]["fp64_tflops"] / FP64_PEAK_TFLOPS,
+                "traffic": NCU_TRAFFIC.get(dom),
+                "peak_source": "FP64 unit count x clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz); "
+                               "MEASURED_PEAKS.json has no FP64 entry; the FMA probe measured 1.19 TFLOP/s",
+                "hbm_gbs": kern[dom]["gbs"]}
     mdom = max(mkern, key=lambda n: mkern[n]["total_ms"])
     mroof = {"kernel": mdom, "bound": "hbm", "achieved": mkern[mdom]["gbs"], "peak": HBM_PEAK_GBS, "unit": "GB/s",
              "frac": mkern[mdom]["gbs"] / HBM_PEAK_GBS, "traffic": NCU_TRAFFIC.get(mdom),
@@ -388,6 +402,8 @@ def run_ours(args, rank, world, local):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "line_operators": "auto: separable star on the tensor cores (exact BF16 digit products), "
+                                 "pairing sweeps as FP64 banded recurrences",
                "config": workload_config(ne, nh), "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
                "roofline": roof, "kernels": kern,
                "steady_state": {"value": reduce_sum(dof * args.steps, world) / (steady_ms * 1e-3),

@@ -139,16 +139,34 @@ int smx_set_stream(smx_ctx* ctx, void* stream);
  * which cannot be captured.  enable = 0 always launches eagerly. */
 int smx_set_graphs(smx_ctx* ctx, int enable);
 
-/* Kernel for the dense line operators of the mixed step (SMX_MIXED with every
- * line length <= 80; Eq. kroninverse applied as a dense product per axis):
- *   SMX_MODE_TENSOR (default): tcgen05 tensor cores; data and operator split
- *     into three BF16 terms each, six products accumulated in FP32 (the
- *     accuracy of an FP32 dot product);
- *   SMX_MODE_SIMT: FP32 CUDA cores with the operator as FP32 (hi, lo) pairs.
- * Both give the same result to FP32 rounding.  Errors: SMX_EINVAL. */
+/* Kernel for the line operators of the Hodge stars (Eq. kroninverse per axis).
+ * Mixed step (SMX_MIXED, every line length <= 80; dense products):
+ *   SMX_MODE_TENSOR: tcgen05 tensor cores; data and operator split into three
+ *     BF16 terms each, six products accumulated in FP32 (the accuracy of an
+ *     FP32 dot product, with a small accumulation bias over long runs);
+ *   SMX_MODE_SIMT and SMX_MODE_AUTO (default): FP32 CUDA cores with the
+ *     operator as FP32 (hi, lo) pairs.
+ * FP64 step (SMX_FP64):
+ *   SMX_MODE_TENSOR (every line length <= 80): the dense operator applied on
+ *     the tcgen05 tensor cores by exact digit slicing -- lines and operator
+ *     rows as 55-bit fixed-point integers in seven balanced base-256 BF16
+ *     digits, each digit level accumulated exactly in FP32 -- with the
+ *     rounding error bound of an FP64 dot product;
+ *   SMX_MODE_SIMT: banded LU recurrences on the FP64 pipe (any line length);
+ *   SMX_MODE_AUTO (default): per star, the faster of the two on GB300 --
+ *     the tensor-core products for a separable star (fused mass + solve),
+ *     the banded recurrences for the pairing sweeps after a mass apply.
+ * The selection applies where the context has dense operators; elsewhere the
+ * banded recurrences run.  Errors: SMX_EINVAL. */
 #define SMX_MODE_TENSOR 0
 #define SMX_MODE_SIMT 1
+#define SMX_MODE_AUTO 2
 int smx_set_mode_kernel(smx_ctx* ctx, int which);
+/* The line-operator selection in effect: the setting above where the
+ * context has dense operators (every line length <= 80; SMX_MODE_AUTO of a
+ * mixed context reads SMX_MODE_SIMT), else SMX_MODE_SIMT.  Host only.
+ * Errors: SMX_EINVAL. */
+int smx_mode_kernel(const smx_ctx* ctx, int* which);
 
 /* Synchronise the context stream and read the device status word: SMX_OK, or
  * SMX_ETIMEOUT if a kernel of this context gave up a bounded device-side wait
@@ -227,9 +245,10 @@ int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
  *   11 curl_primal and 12 curl_dual of the mixed step (FP32 differences),
  *   13 FP32 block Hodge, 14/15/16 FP32 line passes along x/y/z, 17 casts,
  *   18 FP32 quadrature Hodge, 19 per-block mass derivative (reverse step),
- *   20 receivers and small vector updates.
+ *   20 receivers and small vector updates,
+ *   21/22/23 FP64 dense line operators on the tensor cores along x/y/z.
  * ms[SMX_NCLASS] receives milliseconds, counts[SMX_NCLASS] launches per class. */
-#define SMX_NCLASS 21
+#define SMX_NCLASS 24
 int smx_launch_count(const smx_ctx* ctx, int64_t* n);
 int smx_set_timing(smx_ctx* ctx, int enable);
 int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);

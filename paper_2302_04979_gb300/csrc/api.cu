@@ -124,9 +124,14 @@ struct smx_ctx {
     size_t o_mode32[2][3][3];
     ModeF32Args md32[2][3];  // [field][axis]
     // the same operators as three BF16 parts for the tensor-core kernel (the default)
-    int mode_kernel = SMX_MODE_SIMT;
+    int mode_kernel = SMX_MODE_AUTO;
     size_t o_modetc[2][3][3];
     ModeTcArgs mtc[2][3];
+    // FP64 context: the same dense operators as digit planes for the FP64 tensor-core
+    // mode products (every line length <= kModeMaxN); mode_kernel then selects them
+    bool use_digit = false;
+    size_t o_dig[2][3][3], o_dige[2][3][3];
+    ModeDigitArgs mdg[2][3];  // [field][axis]
     size_t o_status = 0;          // device status word (bit 0: a tensor-core wait gave up)
     unsigned* status = nullptr;
     // reverse step: transposed pairing sweeps, block permittivity, receivers
@@ -577,7 +582,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
             if ((st = mass_f32(C, h, x, prezeroed))) return st;
             x64 = C->scratch;
         }
-        const bool tc = C->mode_kernel == SMX_MODE_TENSOR;
+        const bool tc = C->mode_kernel == SMX_MODE_TENSOR;  // AUTO: the CUDA-core kernel (no accumulation bias)
         auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
             return run(C, 14 + a, 1, [&] {
                 return tc ? launch_mode_tc(C->mtc[h][a], i64, i32, out, o64, C->stream)
@@ -664,6 +669,28 @@ int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
 // scratch vector followed by the three pairing sweeps.
 int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezeroed) {
     const int which = h == 0 ? 1 : 0;
+    // SMX_MODE_AUTO takes, per star, the kernel measured faster on GB300 at the
+    // workload sizes: the tensor-core digit products for a separable star (they
+    // replace fused mass + solve recurrences of 2(2d+1) + 4 KL + 1 flops per
+    // entry), the banded recurrences for the pairing sweeps (4 KL + 1 flops)
+    const bool digit = C->use_digit && (C->mode_kernel == SMX_MODE_TENSOR ||
+                                        (C->mode_kernel == SMX_MODE_AUTO && C->hodge[h].separable));
+    if (digit) {
+        // dense line operators on the tensor cores: A^{-1} M per axis (separable), or
+        // the mass apply followed by A^{-1} per axis
+        const double* src = x;
+        if (!C->hodge[h].separable) {
+            const int st = hodge_apply_impl(C, h, x, C->scratch, prezeroed);
+            if (st) return st;
+            src = C->scratch;
+        }
+        for (int a = 0; a < 3; ++a) {
+            const int st =
+                run(C, 21 + a, 1, [&] { return launch_mode_digit(C->mdg[h][a], a == 0 ? src : out, out, C->stream); });
+            if (st) return st;
+        }
+        return SMX_OK;
+    }
     if (C->hodge[h].separable) {
         int st = run(C, 8, 1, [&] { return launch_mass_solve_axis(C->ms[h][0], C->p[0] - 1, x, out, C->stream); });
         if (st) return st;
@@ -825,36 +852,47 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                         for (int kind = 0; kind < 4; ++kind)
                             C->o_lmass32[h][a][kind] = C->blob.add(split_pairs(H.lmass[a][kind]));
             }
-            // dense line operators for the mode-product sweeps: A^{-1}, or A^{-1} M (separable star)
-            C->use_mode = true;
+        }
+        // dense line operators for the mode-product sweeps: A^{-1}, or A^{-1} M (separable
+        // star) -- as FP32 pairs and BF16 parts (mixed step) or as digit planes (FP64 step)
+        bool dense = true;
+        for (int a = 0; a < 3; ++a)
+            if (kind_dim(P0, C->p[a], C->nel[a]) + 1 > kModeMaxN) dense = false;
+        if (dense) {
+            C->use_mode = C->precision == SMX_MIXED;
+            C->use_digit = C->precision == SMX_FP64;
+            std::vector<double> inv[3][4];
             for (int a = 0; a < 3; ++a)
-                if (kind_dim(P0, C->p[a], C->nel[a]) + 1 > kModeMaxN) C->use_mode = false;
-            if (C->use_mode) {
-                std::vector<double> inv[3][4];
+                for (int w = 0; w < 4; ++w) inv[a][w] = dense_inverse(C->fac[a][w]);
+            for (int h = 0; h < 2; ++h) {
+                const HodgeHost& H = C->hodge[h];
+                const int fld = kFieldOfHodge[h], which = h == 0 ? 1 : 0;
                 for (int a = 0; a < 3; ++a)
-                    for (int w = 0; w < 4; ++w) inv[a][w] = dense_inverse(C->fac[a][w]);
-                for (int h = 0; h < 2; ++h) {
-                    const HodgeHost& H = C->hodge[h];
-                    const int fld = kFieldOfHodge[h], which = h == 0 ? 1 : 0;
-                    for (int a = 0; a < 3; ++a)
-                        for (int c = 0; c < 3; ++c) {
-                            const int w = factor_index(which, c, a), kind = kFieldKinds[fld][c][a];
-                            const int n = C->fac[a][w].n;
-                            const std::vector<double> B =
-                                H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
-                                            : inv[a][w];
-                            // CUDA-core kernel: transposed and zero padded to the kernel's output count,
-                            // Bt[k][i] = B[i][k] for i < npad, so the staging is one contiguous copy
-                            int maxn = 0;
-                            for (int c2 = 0; c2 < 3; ++c2) maxn = std::max(maxn, C->fld[fld].c[c2].n[a]);
-                            const int npad = mode_f32_npad(maxn);
-                            std::vector<double> Bt((size_t)n * npad, 0.0);
-                            for (int i = 0; i < n; ++i)
-                                for (int k = 0; k < n; ++k) Bt[(size_t)k * npad + i] = B[(size_t)i * n + k];
-                            C->o_mode32[h][a][c] = C->blob.add(split_pairs(Bt));
-                            C->o_modetc[h][a][c] = C->blob.add(bf16_split_operator(B, n, mode_tc_npad(n)));
+                    for (int c = 0; c < 3; ++c) {
+                        const int w = factor_index(which, c, a), kind = kFieldKinds[fld][c][a];
+                        const int n = C->fac[a][w].n;
+                        const std::vector<double> B =
+                            H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
+                                        : inv[a][w];
+                        if (C->use_digit) {
+                            std::vector<uint16_t> planes;
+                            std::vector<int32_t> rowexp;
+                            digit_split_operator(B, n, mode_digit_npad(n), planes, rowexp);
+                            C->o_dig[h][a][c] = C->blob.add(planes);
+                            C->o_dige[h][a][c] = C->blob.add(rowexp);
+                            continue;
                         }
-                }
+                        // CUDA-core kernel: transposed and zero padded to the kernel's output count,
+                        // Bt[k][i] = B[i][k] for i < npad, so the staging is one contiguous copy
+                        int maxn = 0;
+                        for (int c2 = 0; c2 < 3; ++c2) maxn = std::max(maxn, C->fld[fld].c[c2].n[a]);
+                        const int npad = mode_f32_npad(maxn);
+                        std::vector<double> Bt((size_t)n * npad, 0.0);
+                        for (int i = 0; i < n; ++i)
+                            for (int k = 0; k < n; ++k) Bt[(size_t)k * npad + i] = B[(size_t)i * n + k];
+                        C->o_mode32[h][a][c] = C->blob.add(split_pairs(Bt));
+                        C->o_modetc[h][a][c] = C->blob.add(bf16_split_operator(B, n, mode_tc_npad(n)));
+                    }
             }
         }
         if (C->eps_blocks) {  // per-block scale of the mass derivative (-1/eps) and the tiles' blocks
@@ -1025,6 +1063,20 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
             A.Qtot = H.Qtot;
         }
     }
+    if (C->use_digit)
+        for (int h = 0; h < 2; ++h)
+            for (int a = 0; a < 3; ++a) {
+                const int fld = kFieldOfHodge[h];
+                ModeDigitArgs& Mg = C->mdg[h][a];
+                Mg.field = C->fld[fld];
+                Mg.axis = a;
+                Mg.status = C->status;
+                for (int c = 0; c < 3; ++c) {
+                    Mg.B[c] = static_cast<const void*>(ws + C->o_dig[h][a][c]);
+                    Mg.rowexp[c] = reinterpret_cast<const int*>(ws + C->o_dige[h][a][c]);
+                    Mg.npad[c] = mode_digit_npad(C->fld[fld].c[c].n[a]);
+                }
+            }
     if (C->precision == SMX_MIXED) {
         C->e32 = reinterpret_cast<float*>(ws + C->o_e32);
         C->h32 = reinterpret_cast<float*>(ws + C->o_h32);
@@ -1202,12 +1254,19 @@ int smx_set_graphs(smx_ctx* C, int enable) {
 }
 
 int smx_set_mode_kernel(smx_ctx* C, int which) {
-    if (!C || (which != SMX_MODE_TENSOR && which != SMX_MODE_SIMT)) return SMX_EINVAL;
+    if (!C || (which != SMX_MODE_TENSOR && which != SMX_MODE_SIMT && which != SMX_MODE_AUTO)) return SMX_EINVAL;
     if (which != C->mode_kernel && C->graph.exec) {  // a captured step launches the other kernel
         cudaGraphExecDestroy(C->graph.exec);
         C->graph.exec = nullptr;
     }
     C->mode_kernel = which;
+    return SMX_OK;
+}
+
+int smx_mode_kernel(const smx_ctx* C, int* which) {
+    if (!C || !which) return SMX_EINVAL;
+    *which = (C->use_mode || C->use_digit) ? C->mode_kernel : SMX_MODE_SIMT;
+    if (*which == SMX_MODE_AUTO && C->use_mode) *which = SMX_MODE_SIMT;  // mixed: AUTO is the CUDA-core kernel
     return SMX_OK;
 }
 
@@ -1435,6 +1494,18 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
             *flops = 0.0;
             *bytes = 12.0 * N;
             return SMX_OK;
+        case 21:
+        case 22:
+        case 23: {  // FP64 dense mode product on the tensor cores: 2 n flops per entry
+            const int h = bside ? 0 : 1, a = cls - 21;
+            if (!C->use_digit) return SMX_EINVAL;
+            const DevField& F = C->fld[kFieldOfHodge[h]];
+            double f = 0.0;
+            for (int c = 0; c < 3; ++c) f += 2.0 * F.c[c].n[a] * ((double)F.c[c].n[0] * F.c[c].n[1] * F.c[c].n[2]);
+            *flops = f;
+            *bytes = 16.0 * N;
+            return SMX_OK;
+        }
         case 18: {  // FP32 quadrature Hodge: the FP64 quadrature kernel's flops, FP32 metric
             const int st = smx_kernel_work(C, 3, field, flops, bytes);
             if (st) return st;

@@ -145,6 +145,26 @@ cudaError_t launch_mode_tc(const ModeTcArgs& a, const double* in64, const float*
                            cudaStream_t s);
 // zero (optional): also set zero[i] = 0 for every output index i (the accumulation
 // target of the Hodge apply that follows the curl).
+// FP64 mode products on the tensor cores (kernels_f64tc.cu): the operator's
+// rows and the lines cut into kDigits balanced base-256 digits (BF16 exact),
+// digit levels 0..kDigitLevels-1 accumulated exactly in FP32 tensor memory.
+// Operator table (digit_split_operator, setup.h): per component, uint16 BF16
+// patterns [plane][npad / 8 k-chunks][rows rounded up to 8][8], plus the rows'
+// exponent fields (int32, one per row).
+constexpr int kDigits = 7;
+constexpr int kDigitLevels = 7;
+struct ModeDigitArgs {
+    DevField field;
+    const void* B[3];       // per component: digit planes of the operator
+    const int* rowexp[3];   // per component: largest exponent field of each operator row (>= 1)
+    int npad[3];            // per component: line length rounded up to a multiple of 16
+    int axis;
+    unsigned* status;       // device word: bit 0 set when an MMA completion wait gave up
+};
+int mode_digit_npad(int n);
+// out = B in along the axis, FP64 in and out (in == out allowed: each tile reads before it writes).
+cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* out, cudaStream_t s);
+
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
                             cudaStream_t s, double* zero = nullptr);

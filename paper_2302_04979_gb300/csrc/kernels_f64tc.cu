@@ -1,0 +1,373 @@
+// FP64 mode products on the 5th-generation tensor cores by exact digit slicing.
+//
+// Along one axis every line x of a component becomes B x, with B the dense
+// n x n line operator -- A^{-1} (pairing sweep, Eq. kroninverse) or A^{-1} M
+// (the fused separable Hodge star).  The FP64 pipe of GB300 issues one warp
+// DFMA per 64 cycles per SM sub-partition, so the FP64 line recurrences are
+// bound by it; here the arithmetic runs on the BF16 tensor pipe instead, with
+// results as accurate as an FP64 dot product.
+//
+// Digits.  Each line L is scaled by its own power of two sigma_L (from the
+// largest exponent on the line) so that every entry becomes an integer
+// X = round(x / sigma_L) with |X| < 2^55, written with seven balanced base-256
+// digits, X = sum_t d_t 256^(6-t), d_t in [-128, 128] (exact in BF16).  Each
+// operator row i is treated the same way on the host (scale tau_i, digits e_s).
+// The digit products
+//   P_ts[i][L] = sum_k e_s[i][k] d_t[L][k]
+// are integers below 80 * 128^2 = 2^20.3; the products of one level
+// l = s + t (at most seven of them) are accumulated in one FP32 tensor-memory
+// accumulator, where every partial sum is an integer below 2^24 and hence exact.
+// Levels 0..6 are formed.  The rounding of each entry to the line's fixed point
+// (2^-55 of the line's largest entry, of the row's largest for the operator)
+// and the dropped levels 7..12 keep the error within a few units of
+// 2^-53 (max |x| sum |B_ik| + max |B_ik| sum |x|): comparable to the error
+// bound of an FP64 dot product, and the same as FP64 wherever the entries of
+// a line have similar size.  The epilogue combines the levels in 64-bit integer arithmetic,
+//   acc = sum_{l<=5} P_l 256^(5-l) + floor(P_6 / 256)   (|acc| < 2^61),
+// and rounds acc * 2^56 * sigma_L * tau_i to the nearest double (sigma_L =
+// 2^(E_L - 1077), tau_i = 2^(F_i - 1077) for the largest exponent fields).  No FP64
+// instruction is issued on the normal path.
+//
+// Tile.  One CTA = 64 lines of one component, 512 threads.  MMA (kind::f16,
+// BF16 in, FP32 accumulate): M = 128 operator rows (zero past n), N = 64
+// lines, K = npad (n rounded up to 16); 28 digit pairs of npad / 16
+// instructions each.  Tensor memory: 7 levels x 64 columns.
+// Shared memory: the operator's seven digit planes and the tile's seven digit
+// planes, both in the canonical K-major no-swizzle layout (8-row x 16-byte
+// core matrices, SBO 128 B, LBO one k-chunk: 16 R + 16 B for R stored rows).
+// The operator planes store only its rows rounded up to 8 (R = r8): an MMA
+// still reads 128 rows, and rows r8..127 are whatever follows in shared
+// memory -- they only feed tensor-memory lanes r8..127, which are never read.
+//   1. warp 0 allocates 512 tensor-memory columns; the operator digits are
+//      copied with cp.async (one contiguous run: the table has this layout);
+//   2. the tile's FP64 values are loaded as bit patterns, the largest
+//      exponent of each line is found with shared-memory atomics, and every
+//      value is cut into its digits: the offset C = 0x80808080808080 turns the
+//      balanced digits of X into the bytes of X + C (d_t = byte - 128, the top
+//      digit from 9 bits), and a biased digit b becomes BF16 through the FP32
+//      value (2^23 + b) - (2^23 + 128);
+//   3. one thread issues the MMAs, cycling through the seven level
+//      accumulators so that consecutive MMAs never wait on each other's
+//      accumulator, and commits them to an mbarrier;
+//   4. the warps of lane quarters 0..2 read tensor-memory lanes 0..95
+//      (operator rows), 16 of the 64 columns each, combine the levels and
+//      write the outputs:
+//      directly for the x sweep (consecutive rows are consecutive addresses),
+//      through shared memory for the y and z sweeps (there consecutive lines
+//      are consecutive addresses).
+// The completion wait gives up after one second: it then sets bit 0 of the
+// status word, skips the epilogue and still frees its tensor memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+#include "pdl.cuh"
+#include "tcgen05.cuh"
+
+namespace smx {
+namespace {
+
+using namespace tc;
+
+constexpr int kDgRows = 128;                 // MMA M: operator rows (TMEM lanes)
+constexpr int kDgLines = 64;                 // MMA N: lines per tile (TMEM columns per level)
+constexpr int kDgThreads = 512;
+constexpr int kDgColGroups = kDgThreads / 128;              // epilogue: warps per TMEM lane quarter
+constexpr int kDgColsPerWarp = kDgLines / kDgColGroups;     // columns (lines) each epilogue warp reads
+constexpr int kDgKcMax = (kModeMaxN + 15) / 16 * 2;                        // k-chunks of 8 at the largest npad
+constexpr int kDgItems = (kDgLines * kDgKcMax + kDgThreads - 1) / kDgThreads;  // (line, k-chunk) items per thread
+constexpr int kDgHeader = 128 + 4 * kDgLines;  // mbarrier, TMEM address holder, line exponents
+constexpr uint32_t kDgTmemCols = 512;        // >= kDigitLevels * kDgLines, a power of two
+constexpr int kDgStageLd = kDgLines + 1;     // staged output rows (doubles), odd to spread banks
+
+static_assert(kDigitLevels * kDgLines <= (int)kDgTmemCols, "tensor memory holds every level");
+
+// Operator planes (r8 + 1 rows of 16 B per k-chunk), then the tile's planes, then
+// 2 KB that the last operator MMA may read past its plane (rows r8..127).
+__host__ __device__ inline int dg_op_bytes(int npad, int r8) { return kDigits * (npad / 8) * 16 * (r8 + 1); }
+__host__ __device__ inline int dg_smem_bytes(int npad, int r8) {
+    return kDgHeader + dg_op_bytes(npad, r8) + kDigits * (npad / 8) * (16 * kDgLines + 16) + 2048;
+}
+
+// The integer image of an FP64 bit pattern relative to the exponent field E
+// (the largest of the line, at least 1): X = round(v / 2^(E - 1077)), |X| < 2^55,
+// returned as X + C with C = 0x80808080808080 (0 < X + C < 2^57).  With d_t the
+// balanced base-256 digits of X (d_1..d_6 in [-128, 127], d_0 in [-128, 128]),
+// bytes 0..5 of X + C are d_6 + 128 .. d_1 + 128 and bits 48..56 are d_0 + 128.
+__device__ __forceinline__ unsigned long long digit_bytes(unsigned long long bits, int E) {
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long frac = bits & 0xFFFFFFFFFFFFFull;
+    const int eff = e ? e : 1;
+    const unsigned long long M = e ? (frac | (1ull << 52)) : frac;
+    const int dsh = E - eff;  // >= 0
+    unsigned long long mag;
+    if (dsh <= 2) {
+        mag = M << (2 - dsh);
+    } else {
+        const int sh = dsh - 2;
+        mag = sh >= 60 ? 0ull : (M + (1ull << (sh - 1))) >> sh;
+    }
+    const unsigned long long x = (bits >> 63) ? (0ull - mag) : mag;
+    return x + 0x80808080808080ull;
+}
+
+// FP32 pattern of (byte j of w) - 128, exact: PRMT builds 0x4B0000bb = 2^23 + b,
+// the subtraction of 2^23 + 128 is exact, and the BF16 pattern of the result
+// is its top half (at most 8 significant bits).
+__device__ __forceinline__ uint32_t digit_f32(uint32_t w, int j) {
+    const uint32_t f = __byte_perm(w, 0x4B000000u, (uint32_t)j | 0x7540u);
+    return __float_as_uint(__uint_as_float(f) - 8388736.0f);
+}
+// The same for the top digit, whose biased value t = bits 48..56 may reach 256.
+__device__ __forceinline__ uint32_t top_digit_f32(unsigned long long u) {
+    return __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)(u >> 48)) - 8388736.0f);
+}
+
+// acc * 2^e2 rounded to the nearest double (ties to even), by integer
+// instructions while the result is a normal number.
+__device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
+    if (acc == 0) return 0.0;
+    const unsigned long long sgn = acc < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
+    int pb = 63 - __clzll((long long)a);  // leading bit
+    unsigned long long m;
+    if (pb <= 52) {
+        m = a << (52 - pb);
+    } else {
+        const int sh = pb - 52;
+        m = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            m += 1;
+            if (m >> 53) {
+                m >>= 1;
+                pb += 1;
+            }
+        }
+    }
+    const int be = pb + e2 + 1023;  // biased exponent of the result
+    if (be >= 1 && be <= 2046)
+        return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+    // outside the normal range: exact m times 2^k in two power-of-two factors
+    const int k = pb - 52 + e2;
+    const int k1 = max(-1022, min(1023, k / 2)), k2 = max(-1022, min(1023, k - k1));
+    const double f1 = __longlong_as_double((long long)(k1 + 1023) << 52);
+    const double f2 = __longlong_as_double((long long)(k2 + 1023) << 52);
+    const double v = (double)(long long)m * f1 * f2;
+    return sgn ? -v : v;
+}
+
+__global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs A, const double* in, double* out) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();
+    const int c = blockIdx.y;
+    const DevComp C = A.field.c[c];
+    const int axis = A.axis;
+    const int n = C.n[axis];
+    if (n <= 0) return;
+    const int nlines = C.n[0] * C.n[1] * C.n[2] / n;
+    const int l0 = blockIdx.x * kDgLines;
+    if (l0 >= nlines) return;  // whole CTA, before any allocation
+    const int npad = A.npad[c], kc = npad / 8, r8 = (n + 7) & ~7;
+    const int lbA = 16 * r8 + 16, lbX = 16 * kDgLines + 16;
+    const int opPlane = kc * lbA, xPlane = kc * lbX;
+    const uint32_t mbar = smem_u32(smem);
+    uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 8);
+    int* sExp = reinterpret_cast<int*>(smem + 128);
+    unsigned char* sOp = smem + kDgHeader;
+    unsigned char* sX = sOp + dg_op_bytes(npad, r8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
+                     "r"(kDgTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) mbar_init(mbar, 1);
+    if (tid < kDgLines) sExp[tid] = 1;
+
+    // operator digits: the table is the shared layout, one contiguous copy
+    const unsigned char* Bg = static_cast<const unsigned char*>(A.B[c]);
+    for (int t = tid; t < kDigits * opPlane / 16; t += kDgThreads) cp_async16(sOp + 16 * t, Bg + 16 * (size_t)t);
+
+    // data tile as bit patterns: items (line r, k-chunk q) of 8 values
+    const int nx = C.n[0], nxy = C.n[0] * C.n[1];
+    const int stride = axis == 0 ? 1 : (axis == 1 ? nx : nxy);
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + C.off);
+    const int nitems = kDgLines * kc;
+    unsigned long long val[kDgItems][8];
+#pragma unroll
+    for (int it = 0; it < kDgItems; ++it) {
+        const int g = tid + it * kDgThreads;
+        int r, q;
+        if (axis == 0) {  // k-chunk fastest: a line's values are contiguous
+            r = g / kc;
+            q = g - r * kc;
+        } else {  // line fastest: consecutive lines are consecutive addresses
+            q = g / kDgLines;
+            r = g - q * kDgLines;
+        }
+        const int L = l0 + r;
+        const bool live = g < nitems && L < nlines;
+        const long long base =
+            axis == 0 ? (long long)L * n : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int k = 8 * q + t;
+            val[it][t] = (live && k < n) ? src[base + (long long)k * stride] : 0ull;
+        }
+    }
+    __syncthreads();  // sExp initialised
+#pragma unroll
+    for (int it = 0; it < kDgItems; ++it) {
+        const int g = tid + it * kDgThreads;
+        if (g >= nitems) break;
+        const int r = axis == 0 ? g / kc : g % kDgLines;
+        int emax = 1;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) emax = max(emax, (int)((val[it][t] >> 52) & 0x7FF));
+        atomicMax(sExp + r, emax);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kDgItems; ++it) {
+        const int g = tid + it * kDgThreads;
+        if (g >= nitems) break;
+        int r, q;
+        if (axis == 0) {
+            r = g / kc;
+            q = g - r * kc;
+        } else {
+            q = g / kDgLines;
+            r = g - q * kDgLines;
+        }
+        const int E = sExp[r];
+        uint32_t w[kDigits][4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            const unsigned long long u0 = digit_bytes(val[it][t], E), u1 = digit_bytes(val[it][t + 1], E);
+            const uint32_t lo0 = (uint32_t)u0, hi0 = (uint32_t)(u0 >> 32);
+            const uint32_t lo1 = (uint32_t)u1, hi1 = (uint32_t)(u1 >> 32);
+#pragma unroll
+            for (int j = 0; j < kDigits - 1; ++j) {  // byte j -> digit plane 6 - j; two BF16 per word
+                const uint32_t f0 = digit_f32(j < 4 ? lo0 : hi0, j & 3), f1 = digit_f32(j < 4 ? lo1 : hi1, j & 3);
+                w[kDigits - 1 - j][t >> 1] = __byte_perm(f0, f1, 0x7632);
+            }
+            w[0][t >> 1] = __byte_perm(top_digit_f32(u0), top_digit_f32(u1), 0x7632);
+        }
+        unsigned char* dst = sX + q * lbX + 16 * r;
+#pragma unroll
+        for (int s = 0; s < kDigits; ++s)
+            *reinterpret_cast<uint4*>(dst + s * xPlane) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+
+    if (tid == 0) {
+        // k-step outer, then data digit t, then operator digit s (t + s < kDigitLevels):
+        // consecutive MMAs go to different level accumulators; the first MMA into level
+        // l (k-step 0, t = 0, s = l) overwrites it
+        const uint32_t idesc = idesc_bf16_f32(kDgRows, kDgLines);
+        const uint32_t a0 = smem_u32(sOp), b0 = smem_u32(sX);
+        for (int ks = 0; ks < kc / 2; ++ks)
+            for (int t = 0; t < kDigitLevels; ++t)
+                for (int s = 0; t + s < kDigitLevels; ++s)
+                    mma_bf16(tmem + (uint32_t)((t + s) * kDgLines),
+                             smem_desc(a0 + s * opPlane + 2 * ks * lbA, lbA, 128),
+                             smem_desc(b0 + t * xPlane + 2 * ks * lbX, lbX, 128), idesc, (ks | t) ? 1u : 0u);
+        mma_commit(mbar);
+    }
+    // every thread's wait is bounded, so all reach the barrier; the verdict is uniform
+    const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, 0)) != 0;
+    tc_fence_after();
+    if (!ok) {
+        if (lane == 0) atomicOr(A.status, 1u);
+    } else {
+        const int quarter = warp & 3, group = warp >> 2;
+        const int i = 32 * quarter + lane;  // operator row = output entry along the line
+        double* dst = out + C.off;
+        double* stage = reinterpret_cast<double*>(sX);  // y/z sweeps: n x kDgStageLd, the digit planes are consumed
+        if (32 * quarter < n) {  // warp-uniform
+            const int Fi = i < n ? A.rowexp[c][i] : 0;
+            const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+            for (int ch = 0; ch < kDgColsPerWarp / 8; ++ch) {
+                const int col0 = group * kDgColsPerWarp + 8 * ch;
+                uint32_t v[kDigitLevels][8];
+#pragma unroll
+                for (int lv = 0; lv < kDigitLevels; ++lv) tmem_ld8_issue(trow + (uint32_t)(lv * kDgLines + col0), v[lv]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int lv = 0; lv < kDigitLevels; ++lv) tmem_pin8(v[lv]);
+                if (i < n) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = col0 + j, L = l0 + col;
+                        // exact: the accumulators hold integers below 2^24
+                        long long acc = __float2int_rn(__uint_as_float(v[0][j]));
+#pragma unroll
+                        for (int lv = 1; lv < kDigitLevels - 1; ++lv)
+                            acc = acc * 256 + __float2int_rn(__uint_as_float(v[lv][j]));
+                        acc += __float2int_rn(__uint_as_float(v[kDigitLevels - 1][j])) >> 8;
+                        const double y = scaled_to_double(acc, sExp[col] + Fi - 2098);
+                        if (axis == 0) {
+                            if (L < nlines) dst[(long long)L * n + i] = y;
+                        } else {
+                            stage[i * kDgStageLd + col] = y;
+                        }
+                    }
+                }
+            }
+        }
+        if (axis != 0) {
+            __syncthreads();
+            const int nl = min(kDgLines, nlines - l0);
+            for (int g = tid; g < n * kDgLines; g += kDgThreads) {
+                const int ii = g / kDgLines, col = g - ii * kDgLines;
+                if (col >= nl) continue;
+                const int L = l0 + col;
+                const long long base = axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L;
+                dst[base + (long long)ii * stride] = stage[ii * kDgStageLd + col];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kDgTmemCols) : "memory");
+    pdl_trigger();  // after the tensor memory is released
+}
+
+}  // namespace
+
+int mode_digit_npad(int n) { return (n + 15) / 16 * 16; }
+
+cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* out, cudaStream_t s) {
+    long long maxlines = 0;
+    int smem = 0;
+    for (int c = 0; c < 3; ++c) {
+        const long long nc = (long long)a.field.c[c].n[0] * a.field.c[c].n[1] * a.field.c[c].n[2];
+        const int n = a.field.c[c].n[a.axis];
+        if (n <= 0) continue;
+        if (n > kModeMaxN || a.npad[c] != mode_digit_npad(n) || !a.B[c] || !a.rowexp[c]) return cudaErrorInvalidValue;
+        maxlines = std::max(maxlines, nc / n);
+        smem = std::max(smem, dg_smem_bytes(a.npad[c], (n + 7) & ~7));
+    }
+    if (maxlines == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mode_digit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dg_smem_bytes(mode_digit_npad(kModeMaxN), kModeMaxN));
+        attr = true;
+    }
+    const dim3 grid((unsigned)((maxlines + kDgLines - 1) / kDgLines), 3);
+    return launch_k(mode_digit_kernel, grid, dim3(kDgThreads), (size_t)smem, s, a, in, out);
+}
+
+}  // namespace smx

@@ -235,4 +235,52 @@ std::vector<uint16_t> bf16_split_operator(const std::vector<double>& B, int n, i
     return out;
 }
 
+void digits56(double v, int F, int d[7]) {
+    uint64_t bits;
+    std::memcpy(&bits, &v, sizeof bits);
+    const int e = static_cast<int>((bits >> 52) & 0x7FF);
+    const uint64_t frac = bits & 0xFFFFFFFFFFFFFull;
+    const int eff = e ? e : 1;
+    const uint64_t M = e ? (frac | (1ull << 52)) : frac;
+    const int dsh = F - eff;
+    uint64_t mag;
+    if (dsh <= 2) {
+        mag = M << (2 - dsh);
+    } else {
+        const int sh = dsh - 2;
+        mag = sh >= 60 ? 0 : (M + (1ull << (sh - 1))) >> sh;
+    }
+    int64_t a = (bits >> 63) ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
+    for (int t = 6; t >= 1; --t) {
+        const int dg = static_cast<int>((static_cast<uint64_t>(a) + 128) & 255) - 128;
+        d[t] = dg;
+        a = (a - dg) / 256;  // exact
+    }
+    d[0] = static_cast<int>(a);
+}
+
+void digit_split_operator(const std::vector<double>& B, int n, int npad, std::vector<uint16_t>& planes,
+                          std::vector<int32_t>& rowexp) {
+    const int r8 = (n + 7) / 8 * 8, kc = npad / 8;
+    const size_t chunk = static_cast<size_t>(r8 + 1) * 8, plane = static_cast<size_t>(kc) * chunk;
+    planes.assign(7 * plane, 0);
+    rowexp.assign(r8, 1);
+    for (int i = 0; i < n; ++i) {
+        int F = 1;
+        for (int k = 0; k < n; ++k) {
+            uint64_t bits;
+            std::memcpy(&bits, &B[static_cast<size_t>(i) * n + k], sizeof bits);
+            F = std::max(F, static_cast<int>((bits >> 52) & 0x7FF));
+        }
+        rowexp[i] = F;
+        for (int k = 0; k < n; ++k) {
+            int d[7];
+            digits56(B[static_cast<size_t>(i) * n + k], F, d);
+            for (int s = 0; s < 7; ++s)
+                planes[s * plane + static_cast<size_t>(k / 8) * chunk + static_cast<size_t>(8) * i + k % 8] =
+                    bf16_nearest(static_cast<float>(d[s]));
+        }
+    }
+}
+
 }  // namespace smx

@@ -4,9 +4,10 @@ p = 3, 64^3 elements, identity map, permittivity on a seeded 8^3 block grid,
 mu = 1; one Hodge star and two single steps per form, kernels launched
 eagerly on the default stream (no CUDA graph), so ncu sees every launch.
 "mixed" uses the default (FP32 CUDA-core) line operators, "mixed-tc" the
-tensor-core ones.
+tensor-core ones; "fp64-tc" the FP64 form with the digit-sliced tensor-core
+line operators, "fp64-banded" the FP64 line recurrences.
 
-  python paper_2302_04979_gb300/probe/step_driver.py [fp64|mixed|mixed-tc|both]
+  python paper_2302_04979_gb300/probe/step_driver.py [fp64|fp64-tc|fp64-banded|mixed|mixed-tc|both]
 """
 import os
 import sys
@@ -19,10 +20,12 @@ def main(forms):
     from paper_2302_04979_gb300 import smx, synth
     eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
     for form in forms:
-        prec = "mixed" if form.startswith("mixed") else form
+        prec = "mixed" if form.startswith("mixed") else "fp64"
         ctx = smx.Context(3, 64, eps=eps, mu=1.0, precision=prec).bind()
-        if form == "mixed-tc":
+        if form in ("mixed-tc", "fp64-tc"):
             ctx.set_mode_kernel("tensor")
+        elif form == "fp64-banded":
+            ctx.set_mode_kernel("simt")
         d = torch.as_tensor(synth.uniform(1, ctx.N_e, -1.0, 1.0)).cuda()
         b = torch.zeros(ctx.N_h, dtype=torch.float64, device="cuda")
         e = torch.empty_like(d)

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsmx.so")
 # ---- constants mirrored from include/smx.h
 OK, EINVAL, EGEOM, EMAT, ECUDA, ENONFINITE, ESTATE, ENOMEM, ESINGULAR, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 ETIMEOUT = -10
-MODE_TENSOR, MODE_SIMT = 0, 1
+MODE_TENSOR, MODE_SIMT, MODE_AUTO = 0, 1, 2
 GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
 MAT_CONST, MAT_BLOCKS, MAT_POINTWISE = 0, 1, 2
 FIELD_E, FIELD_B, FIELD_H, FIELD_D = 0, 1, 2, 3
@@ -57,6 +57,7 @@ _SIGS = {
     "smx_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
     "smx_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "smx_set_mode_kernel": [ctypes.c_void_p, ctypes.c_int],
+    "smx_mode_kernel": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)],
     "smx_device_status": [ctypes.c_void_p],
     "smx_hodge_star_mixed": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_receivers_set": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
@@ -96,11 +97,12 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)],
 }
 
-NCLASS = 21
+NCLASS = 24
 KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
                   "reduction", "mass_solve_x", "mass_solve_y", "mass_solve_z",
                   "curl_primal_f32", "curl_dual_f32", "hodge_block_f32", "line_f32_x", "line_f32_y", "line_f32_z",
-                  "cast", "hodge_quad_f32", "mass_derivative", "receivers")
+                  "cast", "hodge_quad_f32", "mass_derivative", "receivers",
+                  "line_f64tc_x", "line_f64tc_y", "line_f64tc_z")
 
 
 def _lib():
@@ -228,9 +230,19 @@ class Context:
         _check(_lib().smx_set_graphs(self.h, 1 if on else 0), "smx_set_graphs")
 
     def set_mode_kernel(self, which):
-        """Dense line operators of the mixed step on "tensor" cores (default) or FP32 "simt" cores."""
-        _check(_lib().smx_set_mode_kernel(self.h, {"tensor": MODE_TENSOR, "simt": MODE_SIMT}[which]),
+        """Line operators of the Hodge stars.  Mixed context: dense products on the "tensor" cores
+        (BF16 split) or on FP32 "simt" cores ("auto", the default, is "simt").  FP64 context:
+        dense products on the "tensor" cores by exact digit slicing (lines of at most 80 entries),
+        banded LU recurrences on the FP64 "simt" pipe, or "auto" (default): per star the faster
+        of the two -- tensor cores for a separable star, recurrences for the pairing sweeps."""
+        _check(_lib().smx_set_mode_kernel(self.h, {"tensor": MODE_TENSOR, "simt": MODE_SIMT, "auto": MODE_AUTO}[which]),
                "smx_set_mode_kernel")
+
+    def mode_kernel(self):
+        """The line-operator kernel the Hodge stars run: "tensor" or "simt"."""
+        w = ctypes.c_int()
+        _check(_lib().smx_mode_kernel(self.h, ctypes.byref(w)), "smx_mode_kernel")
+        return {MODE_TENSOR: "tensor", MODE_SIMT: "simt", MODE_AUTO: "auto"}[w.value]
 
     def device_status(self):
         """Synchronise; raise SmxError(ETIMEOUT) if a bounded device-side wait gave up since the last call."""

@@ -96,9 +96,24 @@ def test_calls_without_workspace_are_rejected(smx):
 
 def test_mode_kernel_selection(smx):
     ctx = smx.Context(3, 4, precision="mixed")
-    ctx.set_mode_kernel("simt")
+    assert ctx.mode_kernel() == "simt"  # the mixed default: FP32 CUDA cores
     ctx.set_mode_kernel("tensor")
+    assert ctx.mode_kernel() == "tensor"
+    ctx.set_mode_kernel("simt")
     assert smx.library().smx_set_mode_kernel(ctx.h, 7) == smx.EINVAL
+    ctx.set_mode_kernel("auto")
+    assert ctx.mode_kernel() == "simt"  # mixed: "auto" is the CUDA-core kernel
+    # FP64: per-star choice by default; digit-sliced tensor-core products or recurrences on request
+    f64 = smx.Context(3, 20)
+    assert f64.mode_kernel() == "auto"
+    f64.set_mode_kernel("tensor")
+    assert f64.mode_kernel() == "tensor"
+    f64.set_mode_kernel("simt")
+    assert f64.mode_kernel() == "simt"
+    long_lines = smx.Context(2, (90, 3, 3))
+    long_lines.set_mode_kernel("tensor")
+    assert long_lines.mode_kernel() == "simt"  # lines of 91 entries: banded recurrences only
+    assert smx.library().smx_mode_kernel(None, None) == smx.EINVAL
 
 
 def test_reverse_mode_and_batch_argument_errors(smx):
