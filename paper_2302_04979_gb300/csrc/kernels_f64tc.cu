@@ -22,22 +22,26 @@
 // and the dropped levels 7..12 keep the error within a few units of
 // 2^-53 (max |x| sum |B_ik| + max |B_ik| sum |x|): comparable to the error
 // bound of an FP64 dot product, and the same as FP64 wherever the entries of
-// a line have similar size.  The epilogue combines the levels in 64-bit integer arithmetic,
+// a line have similar size.  The levels are combined by Horner's rule in
+// 64-bit integer arithmetic as they arrive,
 //   acc = sum_{l<=5} P_l 256^(5-l) + floor(P_6 / 256)   (|acc| < 2^61),
-// and rounds acc * 2^56 * sigma_L * tau_i to the nearest double (sigma_L =
-// 2^(E_L - 1077), tau_i = 2^(F_i - 1077) for the largest exponent fields).  No FP64
-// instruction is issued on the normal path.
+// and acc * 2^56 * sigma_L * tau_i is rounded once to the nearest double
+// (sigma_L = 2^(E_L - 1077), tau_i = 2^(F_i - 1077) for the largest exponent
+// fields).  No FP64 instruction is issued on the normal path.
 //
-// Tile.  One CTA = 64 lines of one component, 512 threads.  MMA (kind::f16,
-// BF16 in, FP32 accumulate): M = 128 operator rows (zero past n), N = 64
-// lines, K = npad (n rounded up to 16); 28 digit pairs of npad / 16
-// instructions each.  Tensor memory: 7 levels x 64 columns.
+// Tile.  One CTA = NL lines of one component (NL = 128, or 96 when the
+// operator's rows do not leave room for 128), 512 threads.  MMA (kind::f16,
+// BF16 in, FP32 accumulate): M = 128 operator rows, N = NL lines, K = npad
+// (n rounded up to 16); 28 digit pairs of npad / 16 instructions each.  An
+// MMA of M = 128, K = 16 costs about the same tensor-pipe time for any N up
+// to 256, so lines per MMA is what counts.  Tensor memory holds a ring of
+// 512 / NL level accumulators of NL columns.
 // Shared memory: the operator's seven digit planes and the tile's seven digit
 // planes, both in the canonical K-major no-swizzle layout (8-row x 16-byte
 // core matrices, SBO 128 B, LBO one k-chunk: 16 R + 16 B for R stored rows).
 // The operator planes store only its rows rounded up to 8 (R = r8): an MMA
 // still reads 128 rows, and rows r8..127 are whatever follows in shared
-// memory -- they only feed tensor-memory lanes r8..127, which are never read.
+// memory -- they only feed tensor-memory lanes r8..127, which are never used.
 //   1. warp 0 allocates 512 tensor-memory columns; the operator digits are
 //      copied with cp.async (one contiguous run: the table has this layout);
 //   2. the tile's FP64 values are loaded as bit patterns, the largest
@@ -46,17 +50,19 @@
 //      balanced digits of X into the bytes of X + C (d_t = byte - 128, the top
 //      digit from 9 bits), and a biased digit b becomes BF16 through the FP32
 //      value (2^23 + b) - (2^23 + 128);
-//   3. one thread issues the MMAs, cycling through the seven level
-//      accumulators so that consecutive MMAs never wait on each other's
-//      accumulator, and commits them to an mbarrier;
-//   4. the warps of lane quarters 0..2 read tensor-memory lanes 0..95
-//      (operator rows), 16 of the 64 columns each, combine the levels and
-//      write the outputs:
-//      directly for the x sweep (consecutive rows are consecutive addresses),
-//      through shared memory for the y and z sweeps (there consecutive lines
-//      are consecutive addresses).
-// The completion wait gives up after one second: it then sets bit 0 of the
-// status word, skips the epilogue and still frees its tensor memory.
+//   3. one thread of warp 3 issues the MMAs level by level into the ring and
+//      commits each level to that buffer's "full" mbarrier; before reusing a
+//      buffer it waits on the buffer's "drained" mbarrier;
+//   4. meanwhile the warps of lane quarters 0..2 (operator rows 0..95; 4
+//      warps per quarter, NL / 4 columns each) take each level as it
+//      completes, fold it into their Horner accumulators and release the
+//      buffer; after level 6 they round and write the outputs: directly for
+//      the x sweep (consecutive rows are consecutive addresses), through
+//      shared memory for the y and z sweeps (there consecutive lines are
+//      consecutive addresses).
+// Every mbarrier wait gives up after one second: the thread then sets bit 0
+// of the status word and skips the rest of its work; the CTA still meets at
+// its final barrier and frees its tensor memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,24 +77,21 @@ namespace {
 
 using namespace tc;
 
-constexpr int kDgRows = 128;                 // MMA M: operator rows (TMEM lanes)
-constexpr int kDgLines = 64;                 // MMA N: lines per tile (TMEM columns per level)
-constexpr int kDgThreads = 512;
-constexpr int kDgColGroups = kDgThreads / 128;              // epilogue: warps per TMEM lane quarter
-constexpr int kDgColsPerWarp = kDgLines / kDgColGroups;     // columns (lines) each epilogue warp reads
-constexpr int kDgKcMax = (kModeMaxN + 15) / 16 * 2;                        // k-chunks of 8 at the largest npad
-constexpr int kDgItems = (kDgLines * kDgKcMax + kDgThreads - 1) / kDgThreads;  // (line, k-chunk) items per thread
-constexpr int kDgHeader = 128 + 4 * kDgLines;  // mbarrier, TMEM address holder, line exponents
-constexpr uint32_t kDgTmemCols = 512;        // >= kDigitLevels * kDgLines, a power of two
-constexpr int kDgStageLd = kDgLines + 1;     // staged output rows (doubles), odd to spread banks
+constexpr int kDgRows = 128;       // MMA M: operator rows (TMEM lanes)
+constexpr int kDgThreads = 512;    // 16 warps: lane quarter = warp % 4, column group = warp / 4
+constexpr int kDgGroups = kDgThreads / 128;
+constexpr int kDgIssuer = 3;       // the warp (lane quarter 3: rows 96..127, never an output) issuing MMAs
+constexpr int kDgKcMax = (kModeMaxN + 15) / 16 * 2;  // k-chunks of 8 at the largest npad
+constexpr uint32_t kDgTmemCols = 512;
+constexpr int kDgHeader = 1024;    // 8 full + 8 drained mbarriers, TMEM address, line exponents (<= 128)
+constexpr int kDgSmemMax = 232448;  // opt-in shared memory per CTA
 
-static_assert(kDigitLevels * kDgLines <= (int)kDgTmemCols, "tensor memory holds every level");
+static_assert(kModeMaxN <= 96, "operator rows must stay in lane quarters 0..2");
 
-// Operator planes (r8 + 1 rows of 16 B per k-chunk), then the tile's planes, then
-// 2 KB that the last operator MMA may read past its plane (rows r8..127).
 __host__ __device__ inline int dg_op_bytes(int npad, int r8) { return kDigits * (npad / 8) * 16 * (r8 + 1); }
-__host__ __device__ inline int dg_smem_bytes(int npad, int r8) {
-    return kDgHeader + dg_op_bytes(npad, r8) + kDigits * (npad / 8) * (16 * kDgLines + 16) + 2048;
+__host__ __device__ inline int dg_x_bytes(int npad, int nl) { return kDigits * (npad / 8) * (16 * nl + 16); }
+__host__ __device__ inline int dg_smem_bytes(int nl, int npad, int r8) {
+    return kDgHeader + dg_op_bytes(npad, r8) + dg_x_bytes(npad, nl);
 }
 
 // The integer image of an FP64 bit pattern relative to the exponent field E
@@ -159,8 +162,14 @@ __device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
     return sgn ? -v : v;
 }
 
+
+template <int NL>
 __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs A, const double* in, double* out) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int kBufs = (int)kDgTmemCols / NL;                 // level buffers in the ring
+    constexpr int kCpw = NL / kDgGroups;                        // columns (lines) per reader warp
+    constexpr int kItems = (NL * kDgKcMax + kDgThreads - 1) / kDgThreads;
+    static_assert(kCpw % 8 == 0 && kBufs >= 1, "tile shape");
+    extern __shared__ __align__(1024) unsigned char smem[];
     pdl_wait();
     const int c = blockIdx.y;
     const DevComp C = A.field.c[c];
@@ -168,17 +177,20 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     const int n = C.n[axis];
     if (n <= 0) return;
     const int nlines = C.n[0] * C.n[1] * C.n[2] / n;
-    const int l0 = blockIdx.x * kDgLines;
+    const int l0 = blockIdx.x * NL;
     if (l0 >= nlines) return;  // whole CTA, before any allocation
     const int npad = A.npad[c], kc = npad / 8, r8 = (n + 7) & ~7;
-    const int lbA = 16 * r8 + 16, lbX = 16 * kDgLines + 16;
+    const int lbA = 16 * r8 + 16, lbX = 16 * NL + 16;
     const int opPlane = kc * lbA, xPlane = kc * lbX;
-    const uint32_t mbar = smem_u32(smem);
-    uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 8);
-    int* sExp = reinterpret_cast<int*>(smem + 128);
+    const uint32_t full0 = smem_u32(smem), drained0 = full0 + 64;
+    uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 128);
+    int* sExp = reinterpret_cast<int*>(smem + 256);
     unsigned char* sOp = smem + kDgHeader;
     unsigned char* sX = sOp + dg_op_bytes(npad, r8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, group = warp >> 2;
+    const int nquarters = (n + 31) / 32;          // lane quarters holding output rows (<= 3)
+    const bool reader = quarter < nquarters;      // warp-uniform
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
@@ -186,8 +198,12 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) mbar_init(mbar, 1);
-    if (tid < kDgLines) sExp[tid] = 1;
+    if (tid == 0)
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(drained0 + 8 * b, kDgGroups * nquarters);
+        }
+    if (tid < NL) sExp[tid] = 1;
 
     // operator digits: the table is the shared layout, one contiguous copy
     const unsigned char* Bg = static_cast<const unsigned char*>(A.B[c]);
@@ -197,18 +213,18 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     const int nx = C.n[0], nxy = C.n[0] * C.n[1];
     const int stride = axis == 0 ? 1 : (axis == 1 ? nx : nxy);
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + C.off);
-    const int nitems = kDgLines * kc;
-    unsigned long long val[kDgItems][8];
+    const int nitems = NL * kc;
+    unsigned long long val[kItems][8];
 #pragma unroll
-    for (int it = 0; it < kDgItems; ++it) {
+    for (int it = 0; it < kItems; ++it) {
         const int g = tid + it * kDgThreads;
         int r, q;
         if (axis == 0) {  // k-chunk fastest: a line's values are contiguous
             r = g / kc;
             q = g - r * kc;
         } else {  // line fastest: consecutive lines are consecutive addresses
-            q = g / kDgLines;
-            r = g - q * kDgLines;
+            q = g / NL;
+            r = g - q * NL;
         }
         const int L = l0 + r;
         const bool live = g < nitems && L < nlines;
@@ -222,10 +238,10 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     }
     __syncthreads();  // sExp initialised
 #pragma unroll
-    for (int it = 0; it < kDgItems; ++it) {
+    for (int it = 0; it < kItems; ++it) {
         const int g = tid + it * kDgThreads;
         if (g >= nitems) break;
-        const int r = axis == 0 ? g / kc : g % kDgLines;
+        const int r = axis == 0 ? g / kc : g % NL;
         int emax = 1;
 #pragma unroll
         for (int t = 0; t < 8; ++t) emax = max(emax, (int)((val[it][t] >> 52) & 0x7FF));
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < kDgItems; ++it) {
+    for (int it = 0; it < kItems; ++it) {
         const int g = tid + it * kDgThreads;
         if (g >= nitems) break;
         int r, q;
@@ -241,8 +257,8 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
             r = g / kc;
             q = g - r * kc;
         } else {
-            q = g / kDgLines;
-            r = g - q * kDgLines;
+            q = g / NL;
+            r = g - q * NL;
         }
         const int E = sExp[r];
         uint32_t w[kDigits][4];
@@ -269,72 +285,91 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *holder;
+    bool ok = true;
+    double* dst = out + C.off;
+    double* stage = reinterpret_cast<double*>(sX);  // y/z sweeps: n x (NL + 1), after the last MMA
 
-    if (tid == 0) {
-        // k-step outer, then data digit t, then operator digit s (t + s < kDigitLevels):
-        // consecutive MMAs go to different level accumulators; the first MMA into level
-        // l (k-step 0, t = 0, s = l) overwrites it
-        const uint32_t idesc = idesc_bf16_f32(kDgRows, kDgLines);
-        const uint32_t a0 = smem_u32(sOp), b0 = smem_u32(sX);
-        for (int ks = 0; ks < kc / 2; ++ks)
-            for (int t = 0; t < kDigitLevels; ++t)
-                for (int s = 0; t + s < kDigitLevels; ++s)
-                    mma_bf16(tmem + (uint32_t)((t + s) * kDgLines),
-                             smem_desc(a0 + s * opPlane + 2 * ks * lbA, lbA, 128),
-                             smem_desc(b0 + t * xPlane + 2 * ks * lbX, lbX, 128), idesc, (ks | t) ? 1u : 0u);
-        mma_commit(mbar);
-    }
-    // every thread's wait is bounded, so all reach the barrier; the verdict is uniform
-    const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, 0)) != 0;
-    tc_fence_after();
-    if (!ok) {
-        if (lane == 0) atomicOr(A.status, 1u);
-    } else {
-        const int quarter = warp & 3, group = warp >> 2;
+    if (warp == kDgIssuer) {
+        if (lane == 0) {
+            // level l into buffer l % kBufs: every digit pair t + s = l, k-step by k-step;
+            // the first MMA of a level overwrites the buffer
+            const uint32_t idesc = idesc_bf16_f32(kDgRows, NL);
+            const uint32_t a0 = smem_u32(sOp), b0 = smem_u32(sX);
+            for (int lv = 0; lv < kDigitLevels && ok; ++lv) {
+                const int buf = lv % kBufs;
+                if (lv >= kBufs) {
+                    ok = mbar_wait_bounded(drained0 + 8 * buf, ((lv - kBufs) / kBufs) & 1);
+                    tc_fence_after();
+                    if (!ok) break;
+                }
+                for (int t = 0; t <= lv; ++t) {
+                    const int s = lv - t;
+                    for (int ks = 0; ks < kc / 2; ++ks)
+                        mma_bf16(tmem + (uint32_t)(buf * NL), smem_desc(a0 + s * opPlane + 2 * ks * lbA, lbA, 128),
+                                 smem_desc(b0 + t * xPlane + 2 * ks * lbX, lbX, 128), idesc, (t | ks) ? 1u : 0u);
+                }
+                mma_commit(full0 + 8 * buf);
+            }
+            if (!ok) atomicOr(A.status, 1u);
+        }
+        __syncwarp();
+    } else if (reader) {
         const int i = 32 * quarter + lane;  // operator row = output entry along the line
-        double* dst = out + C.off;
-        double* stage = reinterpret_cast<double*>(sX);  // y/z sweeps: n x kDgStageLd, the digit planes are consumed
-        if (32 * quarter < n) {  // warp-uniform
-            const int Fi = i < n ? A.rowexp[c][i] : 0;
-            const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
-            for (int ch = 0; ch < kDgColsPerWarp / 8; ++ch) {
-                const int col0 = group * kDgColsPerWarp + 8 * ch;
-                uint32_t v[kDigitLevels][8];
+        const int Fi = i < n ? A.rowexp[c][i] : 0;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(group * kCpw);
+        unsigned long long acc[kCpw];  // Horner accumulators, two's complement (wraps only on unused rows)
 #pragma unroll
-                for (int lv = 0; lv < kDigitLevels; ++lv) tmem_ld8_issue(trow + (uint32_t)(lv * kDgLines + col0), v[lv]);
-                tmem_wait_ld();
+        for (int j = 0; j < kCpw; ++j) acc[j] = 0;
+        for (int lv = 0; lv < kDigitLevels; ++lv) {
+            const int buf = lv % kBufs;
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(full0 + 8 * buf, (lv / kBufs) & 1));
+            if (!ok) break;
+            tc_fence_after();
+            uint32_t v[kCpw / 8][8];
 #pragma unroll
-                for (int lv = 0; lv < kDigitLevels; ++lv) tmem_pin8(v[lv]);
-                if (i < n) {
+            for (int ch = 0; ch < kCpw / 8; ++ch) tmem_ld8_issue(trow + (uint32_t)(buf * NL + 8 * ch), v[ch]);
+            tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = col0 + j, L = l0 + col;
-                        // exact: the accumulators hold integers below 2^24
-                        long long acc = __float2int_rn(__uint_as_float(v[0][j]));
+            for (int ch = 0; ch < kCpw / 8; ++ch) tmem_pin8(v[ch]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(drained0 + 8 * buf);  // this warp is done with the buffer
 #pragma unroll
-                        for (int lv = 1; lv < kDigitLevels - 1; ++lv)
-                            acc = acc * 256 + __float2int_rn(__uint_as_float(v[lv][j]));
-                        acc += __float2int_rn(__uint_as_float(v[kDigitLevels - 1][j])) >> 8;
-                        const double y = scaled_to_double(acc, sExp[col] + Fi - 2098);
-                        if (axis == 0) {
-                            if (L < nlines) dst[(long long)L * n + i] = y;
-                        } else {
-                            stage[i * kDgStageLd + col] = y;
-                        }
-                    }
+            for (int ch = 0; ch < kCpw / 8; ++ch)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    // exact: the accumulators hold integers below 2^24
+                    const long long p = __float2int_rn(__uint_as_float(v[ch][j]));
+                    unsigned long long& a = acc[8 * ch + j];
+                    a = lv < kDigitLevels - 1 ? a * 256ull + (unsigned long long)p
+                                              : a + (unsigned long long)(p >> 8);
+                }
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(A.status, 1u);
+        } else if (i < n) {
+#pragma unroll
+            for (int j = 0; j < kCpw; ++j) {
+                const int col = group * kCpw + j, L = l0 + col;
+                const double y = scaled_to_double((long long)acc[j], sExp[col] + Fi - 2098);
+                if (axis == 0) {
+                    if (L < nlines) dst[(long long)L * n + i] = y;
+                } else {
+                    stage[i * (NL + 1) + col] = y;  // every MMA has completed: the digit planes are free
                 }
             }
         }
-        if (axis != 0) {
-            __syncthreads();
-            const int nl = min(kDgLines, nlines - l0);
-            for (int g = tid; g < n * kDgLines; g += kDgThreads) {
-                const int ii = g / kDgLines, col = g - ii * kDgLines;
-                if (col >= nl) continue;
-                const int L = l0 + col;
-                const long long base = axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L;
-                dst[base + (long long)ii * stride] = stage[ii * kDgStageLd + col];
-            }
+    }
+    // the staged y/z tile: consecutive threads write consecutive lines
+    ok = __syncthreads_and(ok) != 0;
+    if (ok && axis != 0) {
+        const int nl = min(NL, nlines - l0);
+        for (int g = tid; g < n * NL; g += kDgThreads) {
+            const int ii = g / NL, col = g - ii * NL;
+            if (col >= nl) continue;
+            const int L = l0 + col;
+            const long long base = axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L;
+            dst[base + (long long)ii * stride] = stage[ii * (NL + 1) + col];
         }
     }
     tc_fence_before();
@@ -348,26 +383,46 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
 
 int mode_digit_npad(int n) { return (n + 15) / 16 * 16; }
 
+// Lines per tile for this sweep: 128 where the shared memory allows it for every component, else 96.
+static int digit_tile_lines(const ModeDigitArgs& a) {
+    for (int c = 0; c < 3; ++c) {
+        const int n = a.field.c[c].n[a.axis];
+        if (n > 0 && dg_smem_bytes(128, a.npad[c], (n + 7) & ~7) > kDgSmemMax) return 96;
+    }
+    return 128;
+}
+
+template <int NL>
+static cudaError_t launch_digit_t(const ModeDigitArgs& a, const double* in, double* out, long long maxlines,
+                                  int smem, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mode_digit_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDgSmemMax);
+        attr = true;
+    }
+    const dim3 grid((unsigned)((maxlines + NL - 1) / NL), 3);
+    return launch_k(mode_digit_kernel<NL>, grid, dim3(kDgThreads), (size_t)smem, s, a, in, out);
+}
+
 cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* out, cudaStream_t s) {
     long long maxlines = 0;
-    int smem = 0;
     for (int c = 0; c < 3; ++c) {
         const long long nc = (long long)a.field.c[c].n[0] * a.field.c[c].n[1] * a.field.c[c].n[2];
         const int n = a.field.c[c].n[a.axis];
         if (n <= 0) continue;
         if (n > kModeMaxN || a.npad[c] != mode_digit_npad(n) || !a.B[c] || !a.rowexp[c]) return cudaErrorInvalidValue;
         maxlines = std::max(maxlines, nc / n);
-        smem = std::max(smem, dg_smem_bytes(a.npad[c], (n + 7) & ~7));
     }
     if (maxlines == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mode_digit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             dg_smem_bytes(mode_digit_npad(kModeMaxN), kModeMaxN));
-        attr = true;
+    const int nl = digit_tile_lines(a);
+    int smem = 0;
+    for (int c = 0; c < 3; ++c) {
+        const int n = a.field.c[c].n[a.axis];
+        if (n > 0) smem = std::max(smem, dg_smem_bytes(nl, a.npad[c], (n + 7) & ~7));
     }
-    const dim3 grid((unsigned)((maxlines + kDgLines - 1) / kDgLines), 3);
-    return launch_k(mode_digit_kernel, grid, dim3(kDgThreads), (size_t)smem, s, a, in, out);
+    if (smem > kDgSmemMax) return cudaErrorInvalidValue;
+    return nl == 128 ? launch_digit_t<128>(a, in, out, maxlines, smem, s)
+                     : launch_digit_t<96>(a, in, out, maxlines, smem, s);
 }
 
 }  // namespace smx

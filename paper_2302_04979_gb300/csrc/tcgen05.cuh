@@ -66,6 +66,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
     return ok != 0;
 }
 
+// One arrival on the mbarrier (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
 // Wait for phase `parity` of the mbarrier, for at most kWaitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
     if (mbar_try_wait(a, parity)) return true;
