@@ -29,19 +29,19 @@
 // (sigma_L = 2^(E_L - 1077), tau_i = 2^(F_i - 1077) for the largest exponent
 // fields).  No FP64 instruction is issued on the normal path.
 //
-// Tile.  One CTA = NL lines of one component (NL = 128, or 96 when the
-// operator's rows do not leave room for 128), 512 threads.  MMA (kind::f16,
+// Tile.  One CTA = NL lines of one component (NL = 96, or 128 where that
+// still gives every SM a tile), 512 threads.  MMA (kind::f16,
 // BF16 in, FP32 accumulate): M = 128 operator rows, N = NL lines, K = npad
-// (n rounded up to 16); 28 digit pairs of npad / 16 instructions each.  An
-// MMA of M = 128, K = 16 costs about the same tensor-pipe time for any N up
-// to 256, so lines per MMA is what counts.  Tensor memory holds a ring of
-// 512 / NL level accumulators of NL columns.
+// (n rounded up to 16); 28 digit pairs of npad / 16 instructions each.
+// Tensor memory holds a ring of 512 / NL level accumulators of NL columns.
 // Shared memory: the operator's seven digit planes and the tile's seven digit
-// planes, both in the canonical K-major no-swizzle layout (8-row x 16-byte
-// core matrices, SBO 128 B, LBO one k-chunk: 16 R + 16 B for R stored rows).
-// The operator planes store only its rows rounded up to 8 (R = r8): an MMA
-// still reads 128 rows, and rows r8..127 are whatever follows in shared
-// memory -- they only feed tensor-memory lanes r8..127, which are never used.
+// planes, both K-major in the 32-byte swizzle layout: per atom column of 16 K
+// values, R rows of 32 bytes (8-row groups of 256 bytes, SBO 256), the two
+// 16-byte halves of row r exchanged when bit 2 of r is set; atom columns
+// follow each other (R x 32 bytes apart).  The operator planes store only its
+// rows rounded up to 8 (R = r8): an MMA still reads 128 rows, and rows
+// r8..127 are whatever follows in shared memory -- they only feed
+// tensor-memory lanes r8..127, which are never used.
 //   1. warp 0 allocates 512 tensor-memory columns; the operator digits are
 //      copied with cp.async (one contiguous run: the table has this layout);
 //   2. the tile's FP64 values are loaded as bit patterns, the largest
@@ -88,10 +88,11 @@ constexpr int kDgSmemMax = 232448;  // opt-in shared memory per CTA
 
 static_assert(kModeMaxN <= 96, "operator rows must stay in lane quarters 0..2");
 
-__host__ __device__ inline int dg_op_bytes(int npad, int r8) { return kDigits * (npad / 8) * 16 * (r8 + 1); }
-__host__ __device__ inline int dg_x_bytes(int npad, int nl) { return kDigits * (npad / 8) * (16 * nl + 16); }
+__host__ __device__ inline int dg_op_bytes(int npad, int r8) { return kDigits * (npad / 16) * r8 * 32; }
+__host__ __device__ inline int dg_x_bytes(int npad, int nl) { return kDigits * (npad / 16) * nl * 32; }
+// header, 256 bytes of slack to align the planes to the swizzle pattern, operator and tile planes
 __host__ __device__ inline int dg_smem_bytes(int nl, int npad, int r8) {
-    return kDgHeader + dg_op_bytes(npad, r8) + dg_x_bytes(npad, nl);
+    return kDgHeader + 256 + dg_op_bytes(npad, r8) + dg_x_bytes(npad, nl);
 }
 
 // The integer image of an FP64 bit pattern relative to the exponent field E
@@ -180,12 +181,12 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     const int l0 = blockIdx.x * NL;
     if (l0 >= nlines) return;  // whole CTA, before any allocation
     const int npad = A.npad[c], kc = npad / 8, r8 = (n + 7) & ~7;
-    const int lbA = 16 * r8 + 16, lbX = 16 * NL + 16;
-    const int opPlane = kc * lbA, xPlane = kc * lbX;
+    const int colA = 32 * r8, colX = 32 * NL;  // bytes per atom column (16 K values)
+    const int opPlane = (npad / 16) * colA, xPlane = (npad / 16) * colX;
     const uint32_t full0 = smem_u32(smem), drained0 = full0 + 64;
     uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 128);
     int* sExp = reinterpret_cast<int*>(smem + 256);
-    unsigned char* sOp = smem + kDgHeader;
+    unsigned char* sOp = smem + kDgHeader + ((256u - ((smem_u32(smem) + kDgHeader) & 255u)) & 255u);
     unsigned char* sX = sOp + dg_op_bytes(npad, r8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, group = warp >> 2;
@@ -274,7 +275,8 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
             }
             w[0][t >> 1] = __byte_perm(top_digit_f32(u0), top_digit_f32(u1), 0x7632);
         }
-        unsigned char* dst = sX + q * lbX + 16 * r;
+        // atom column q / 2, row r, 16-byte half (q & 1) exchanged by bit 2 of r
+        unsigned char* dst = sX + (q >> 1) * colX + 32 * r + 16 * ((q & 1) ^ ((r >> 2) & 1));
 #pragma unroll
         for (int s = 0; s < kDigits; ++s)
             *reinterpret_cast<uint4*>(dst + s * xPlane) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
@@ -305,8 +307,8 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
                 for (int t = 0; t <= lv; ++t) {
                     const int s = lv - t;
                     for (int ks = 0; ks < kc / 2; ++ks)
-                        mma_bf16(tmem + (uint32_t)(buf * NL), smem_desc(a0 + s * opPlane + 2 * ks * lbA, lbA, 128),
-                                 smem_desc(b0 + t * xPlane + 2 * ks * lbX, lbX, 128), idesc, (t | ks) ? 1u : 0u);
+                        mma_bf16(tmem + (uint32_t)(buf * NL), smem_desc_sw32(a0 + s * opPlane + ks * colA, 256),
+                                 smem_desc_sw32(b0 + t * xPlane + ks * colX, 256), idesc, (t | ks) ? 1u : 0u);
                 }
                 mma_commit(full0 + 8 * buf);
             }
@@ -383,13 +385,18 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
 
 int mode_digit_npad(int n) { return (n + 15) / 16 * 16; }
 
-// Lines per tile for this sweep: 128 where the shared memory allows it for every component, else 96.
-static int digit_tile_lines(const ModeDigitArgs& a) {
+// Lines per tile for this sweep.  The MMA time is proportional to N (about 2 cycles
+// per column of an M = 128, K = 16 instruction on GB300), so the tile only decides
+// how the lines spread over the SMs: 128-line tiles while they still fill all 152
+// SMs with one wave, else 96 (one wave of 135 CTAs at p = 3, 64^3 instead of 102).
+static int digit_tile_lines(const ModeDigitArgs& a, long long maxlines) {
+    const long long tiles128 = 3 * ((maxlines + 127) / 128);
+    bool fits128 = true;
     for (int c = 0; c < 3; ++c) {
         const int n = a.field.c[c].n[a.axis];
-        if (n > 0 && dg_smem_bytes(128, a.npad[c], (n + 7) & ~7) > kDgSmemMax) return 96;
+        if (n > 0 && dg_smem_bytes(128, a.npad[c], (n + 7) & ~7) > kDgSmemMax) fits128 = false;
     }
-    return 128;
+    return (fits128 && tiles128 >= 152) ? 128 : 96;
 }
 
 template <int NL>
@@ -414,7 +421,7 @@ cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* 
         maxlines = std::max(maxlines, nc / n);
     }
     if (maxlines == 0) return cudaSuccess;
-    const int nl = digit_tile_lines(a);
+    const int nl = digit_tile_lines(a, maxlines);
     int smem = 0;
     for (int c = 0; c < 3; ++c) {
         const int n = a.field.c[c].n[a.axis];

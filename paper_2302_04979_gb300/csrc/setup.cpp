@@ -261,8 +261,8 @@ void digits56(double v, int F, int d[7]) {
 
 void digit_split_operator(const std::vector<double>& B, int n, int npad, std::vector<uint16_t>& planes,
                           std::vector<int32_t>& rowexp) {
-    const int r8 = (n + 7) / 8 * 8, kc = npad / 8;
-    const size_t chunk = static_cast<size_t>(r8 + 1) * 8, plane = static_cast<size_t>(kc) * chunk;
+    const int r8 = (n + 7) / 8 * 8;
+    const size_t col = static_cast<size_t>(r8) * 16, plane = static_cast<size_t>(npad / 16) * col;
     planes.assign(7 * plane, 0);
     rowexp.assign(r8, 1);
     for (int i = 0; i < n; ++i) {
@@ -277,7 +277,8 @@ void digit_split_operator(const std::vector<double>& B, int n, int npad, std::ve
             int d[7];
             digits56(B[static_cast<size_t>(i) * n + k], F, d);
             for (int s = 0; s < 7; ++s)
-                planes[s * plane + static_cast<size_t>(k / 8) * chunk + static_cast<size_t>(8) * i + k % 8] =
+                planes[s * plane + static_cast<size_t>(k / 16) * col + static_cast<size_t>(16) * i +
+                       8 * (((k / 8) & 1) ^ ((i >> 2) & 1)) + k % 8] =
                     bf16_nearest(static_cast<float>(d[s]));
         }
     }

@@ -64,10 +64,10 @@ std::vector<uint16_t> bf16_split_operator(const std::vector<double>& B, int n, i
 // largest exponent field (at least 1), rounded to an integer X with
 // |X| < 2^55 and written as seven balanced base-256 digits
 // X = sum_s e_s 256^(6-s), e_s in [-128, 128] (integer arithmetic only).
-// planes: BF16 patterns, digit s, element (row i, column k) at uint16 index
-//   s * (npad / 8) * (r8 + 1) * 8 + (k / 8) * (r8 + 1) * 8 + 8 i + k % 8,
-// r8 = n rounded up to 8 (each k-chunk padded by one 16-byte row), zero
-// outside n x n.  rowexp: F_i for i < n.
+// planes: BF16 patterns in the K-major 32-byte swizzle layout, digit s,
+// element (row i, column k) at uint16 index
+//   s * (npad / 16) * r8 * 16 + (k / 16) * r8 * 16 + 16 i + 8 (((k / 8) & 1) ^ ((i / 4) & 1)) + k % 8,
+// r8 = n rounded up to 8, zero outside n x n.  rowexp: F_i for i < n.
 void digit_split_operator(const std::vector<double>& B, int n, int npad, std::vector<uint16_t>& planes,
                           std::vector<int32_t>& rowexp);
 // The same digits of one value for a given F (the host reference of the device cut).

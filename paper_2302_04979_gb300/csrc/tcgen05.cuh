@@ -29,6 +29,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for a K-major operand in the 32-byte swizzle layout (layout type 6
+// in bits 61-63): rows of 32 bytes (16 BF16 values of K), 8-row groups of
+// 256 bytes SBO apart, the two 16-byte halves of row r exchanged when bit 2 of
+// r is set (address bit 4 ^= bit 7); one K = 16 step per swizzle atom, so the
+// leading-dimension offset is unused.  addr must be 256-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
 // B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
