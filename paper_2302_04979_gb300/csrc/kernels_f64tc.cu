@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     constexpr int kItems = (NL * kDgKcMax + kDgThreads - 1) / kDgThreads;
     static_assert(kCpw % 8 == 0 && kBufs >= 1, "tile shape");
     extern __shared__ __align__(1024) unsigned char smem[];
-    pdl_wait();
+    // nothing before pdl_wait reads what the previous kernel of the stream writes:
+    // the operator table, tensor memory and the barriers are set up while it drains
     const int c = blockIdx.y;
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     // operator digits: the table is the shared layout, one contiguous copy
     const unsigned char* Bg = static_cast<const unsigned char*>(A.B[c]);
     for (int t = tid; t < kDigits * opPlane / 16; t += kDgThreads) cp_async16(sOp + 16 * t, Bg + 16 * (size_t)t);
+    pdl_wait();  // the input lines are the previous kernel's output
 
     // data tile as bit patterns: items (line r, k-chunk q) of 8 values
     const int nx = C.n[0], nxy = C.n[0] * C.n[1];
@@ -364,6 +366,7 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     }
     // the staged y/z tile: consecutive threads write consecutive lines
     ok = __syncthreads_and(ok) != 0;
+    pdl_trigger();  // the next kernel may be scheduled; its pdl_wait still waits for this grid
     if (ok && axis != 0) {
         const int nl = min(NL, nlines - l0);
         for (int g = tid; g < n * NL; g += kDgThreads) {
@@ -378,7 +381,6 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kDgTmemCols) : "memory");
-    pdl_trigger();  // after the tensor memory is released
 }
 
 }  // namespace
