@@ -351,7 +351,7 @@ def run_ours(args, rank, world, local):
     m_ms = reduce_max(m_ms, world)
     m_steady, mkern = steady_and_kernels(mctx, smx, mstate, dt, args.steps, flush, stream)
     m_steady = reduce_max(m_steady, world)
-    # the same mixed step with the dense line operators on the tensor cores (tcgen05, BF16 split)
+    # the same mixed step with the dense line operators on the tensor cores (exact four-digit slicing)
     mctx.set_mode_kernel("tensor")
     for _ in range(args.warmup):
         mctx.step(*mstate, dt, 1)
@@ -416,7 +416,7 @@ def run_ours(args, rank, world, local):
                          "tensor_line_operators": {"value": reduce_sum(dof * args.steps, world) / (s_ms * 1e-3),
                                                    "ms_per_step": s_ms / args.steps,
                                                    "note": "same step, dense line operators on the tcgen05 tensor "
-                                                           "cores (BF16 three-term split, FP32 accumulate)"},
+                                                           "cores (exact four-digit slicing, one FP32 rounding)"},
                          "speedup_vs_fp64": total_ms / m_ms,
                          "steady_state": {"value": reduce_sum(dof * args.steps, world) / (m_steady * 1e-3),
                                           "ms_per_step": m_steady / args.steps}}}

@@ -141,11 +141,12 @@ int smx_set_graphs(smx_ctx* ctx, int enable);
 
 /* Kernel for the line operators of the Hodge stars (Eq. kroninverse per axis).
  * Mixed step (SMX_MIXED, every line length <= 80; dense products):
- *   SMX_MODE_TENSOR: tcgen05 tensor cores; data and operator split into three
- *     BF16 terms each, six products accumulated in FP32 (the accuracy of an
- *     FP32 dot product, with a small accumulation bias over long runs);
+ *   SMX_MODE_TENSOR: tcgen05 tensor cores by exact digit slicing with four
+ *     digits -- lines and operator rows as 31-bit fixed-point integers, the
+ *     four digit levels accumulated exactly, one rounding to FP32 at the end
+ *     (more accurate than an FP32 dot product, no accumulation bias);
  *   SMX_MODE_SIMT and SMX_MODE_AUTO (default): FP32 CUDA cores with the
- *     operator as FP32 (hi, lo) pairs.
+ *     operator as FP32 (hi, lo) pairs (the faster of the two at p = 3, 64^3).
  * FP64 step (SMX_FP64):
  *   SMX_MODE_TENSOR (every line length <= 80): the dense operator applied on
  *     the tcgen05 tensor cores by exact digit slicing -- lines and operator

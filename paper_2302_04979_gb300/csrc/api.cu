@@ -125,8 +125,6 @@ struct smx_ctx {
     ModeF32Args md32[2][3];  // [field][axis]
     // the same operators as three BF16 parts for the tensor-core kernel (the default)
     int mode_kernel = SMX_MODE_AUTO;
-    size_t o_modetc[2][3][3];
-    ModeTcArgs mtc[2][3];
     // FP64 context: the same dense operators as digit planes for the FP64 tensor-core
     // mode products (every line length <= kModeMaxN); mode_kernel then selects them
     bool use_digit = false;
@@ -585,7 +583,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         const bool tc = C->mode_kernel == SMX_MODE_TENSOR;  // AUTO: the CUDA-core kernel (no accumulation bias)
         auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
             return run(C, 14 + a, 1, [&] {
-                return tc ? launch_mode_tc(C->mtc[h][a], i64, i32, out, o64, C->stream)
+                return tc ? launch_mode_digit_f32(C->mdg[h][a], i64, i32, out, o64, C->stream)
                           : launch_mode_f32(C->md32[h][a], i64, i32, out, C->stream);
             });
         };
@@ -673,7 +671,7 @@ int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezer
     // workload sizes: the tensor-core digit products for a separable star (they
     // replace fused mass + solve recurrences of 2(2d+1) + 4 KL + 1 flops per
     // entry), the banded recurrences for the pairing sweeps (4 KL + 1 flops)
-    const bool digit = C->use_digit && (C->mode_kernel == SMX_MODE_TENSOR ||
+    const bool digit = C->use_digit && C->precision == SMX_FP64 && (C->mode_kernel == SMX_MODE_TENSOR ||
                                         (C->mode_kernel == SMX_MODE_AUTO && C->hodge[h].separable));
     if (digit) {
         // dense line operators on the tensor cores: A^{-1} M per axis (separable), or
@@ -860,7 +858,8 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             if (kind_dim(P0, C->p[a], C->nel[a]) + 1 > kModeMaxN) dense = false;
         if (dense) {
             C->use_mode = C->precision == SMX_MIXED;
-            C->use_digit = C->precision == SMX_FP64;
+            C->use_digit = true;  // digit planes: 7 digits (FP64 step) or 4 (mixed step)
+            const int nd = C->precision == SMX_FP64 ? kDigits : kDigitsF32;
             std::vector<double> inv[3][4];
             for (int a = 0; a < 3; ++a)
                 for (int w = 0; w < 4; ++w) inv[a][w] = dense_inverse(C->fac[a][w]);
@@ -874,14 +873,14 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                         const std::vector<double> B =
                             H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
                                         : inv[a][w];
-                        if (C->use_digit) {
+                        {
                             std::vector<uint16_t> planes;
                             std::vector<int32_t> rowexp;
-                            digit_split_operator(B, n, mode_digit_npad(n), planes, rowexp);
+                            digit_split_operator(B, n, mode_digit_npad(n), nd, planes, rowexp);
                             C->o_dig[h][a][c] = C->blob.add(planes);
                             C->o_dige[h][a][c] = C->blob.add(rowexp);
-                            continue;
                         }
+                        if (!C->use_mode) continue;
                         // CUDA-core kernel: transposed and zero padded to the kernel's output count,
                         // Bt[k][i] = B[i][k] for i < npad, so the staging is one contiguous copy
                         int maxn = 0;
@@ -891,7 +890,6 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                         for (int i = 0; i < n; ++i)
                             for (int k = 0; k < n; ++k) Bt[(size_t)k * npad + i] = B[(size_t)i * n + k];
                         C->o_mode32[h][a][c] = C->blob.add(split_pairs(Bt));
-                        C->o_modetc[h][a][c] = C->blob.add(bf16_split_operator(B, n, mode_tc_npad(n)));
                     }
             }
         }
@@ -1134,14 +1132,6 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                 int maxn = 0;
                 for (int c = 0; c < 3; ++c) maxn = std::max(maxn, C->fld[fld].c[c].n[a]);
                 Md.npad = mode_f32_npad(maxn);
-                ModeTcArgs& Mt = C->mtc[h][a];
-                Mt.field = C->fld[fld];
-                Mt.axis = a;
-                Mt.status = C->status;
-                for (int c = 0; c < 3; ++c) {
-                    Mt.B[c] = C->use_mode ? static_cast<const void*>(ws + C->o_modetc[h][a][c]) : nullptr;
-                    Mt.npad[c] = mode_tc_npad(C->fld[fld].c[c].n[a]);
-                }
             }
             for (int a = 0; a < 3; ++a) {
                 LineF32Args& Lg = C->ln32[h][a];
@@ -1265,7 +1255,7 @@ int smx_set_mode_kernel(smx_ctx* C, int which) {
 
 int smx_mode_kernel(const smx_ctx* C, int* which) {
     if (!C || !which) return SMX_EINVAL;
-    *which = (C->use_mode || C->use_digit) ? C->mode_kernel : SMX_MODE_SIMT;
+    *which = C->use_digit ? C->mode_kernel : SMX_MODE_SIMT;
     if (*which == SMX_MODE_AUTO && C->use_mode) *which = SMX_MODE_SIMT;  // mixed: AUTO is the CUDA-core kernel
     return SMX_OK;
 }

@@ -129,30 +129,14 @@ constexpr int kModeMaxN = 80;  // largest line length the mode-product kernel ha
 cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const float* in32, float* out, cudaStream_t s);
 int mode_f32_npad(int maxn);  // padded output count of the CUDA-core kernel for lines up to maxn
 
-// The same mode products on the tensor cores (kernels_tc.cu): the operator as
-// three BF16 parts in the shared-memory layout of that file, built on the host
-// by bf16_split_operator (setup.h).
-struct ModeTcArgs {
-    DevField field;
-    const void* B[3];   // per component: 3 parts x (npad / 8) chunks x (16 npad + 16) bytes
-    int npad[3];        // per component: line length rounded up to a multiple of 16
-    int axis;
-    unsigned* status;   // device word: bit 0 set when an MMA completion wait gave up
-};
-int mode_tc_npad(int n);
-// out64 (optional): the result also widened to FP64.
-cudaError_t launch_mode_tc(const ModeTcArgs& a, const double* in64, const float* in32, float* out, double* out64,
-                           cudaStream_t s);
-// zero (optional): also set zero[i] = 0 for every output index i (the accumulation
-// target of the Hodge apply that follows the curl).
-// FP64 mode products on the tensor cores (kernels_f64tc.cu): the operator's
-// rows and the lines cut into kDigits balanced base-256 digits (BF16 exact),
-// digit levels 0..kDigitLevels-1 accumulated exactly in FP32 tensor memory.
+// Mode products on the tensor cores by exact digit slicing (kernels_f64tc.cu):
+// the operator's rows and the lines cut into balanced base-256 digits (BF16
+// exact), digit levels accumulated exactly in FP32 tensor memory.
 // Operator table (digit_split_operator, setup.h): per component, uint16 BF16
-// patterns [plane][npad / 8 k-chunks][rows rounded up to 8][8], plus the rows'
-// exponent fields (int32, one per row).
-constexpr int kDigits = 7;
-constexpr int kDigitLevels = 7;
+// patterns of the digit planes in the K-major 32-byte swizzle layout, plus the
+// rows' exponent fields (int32, one per row).
+constexpr int kDigits = 7;     // FP64 step: 55-bit fixed point, levels 0..6
+constexpr int kDigitsF32 = 4;  // mixed step: 31-bit fixed point, levels 0..3
 struct ModeDigitArgs {
     DevField field;
     const void* B[3];       // per component: digit planes of the operator
@@ -162,9 +146,15 @@ struct ModeDigitArgs {
     unsigned* status;       // device word: bit 0 set when an MMA completion wait gave up
 };
 int mode_digit_npad(int n);
-// out = B in along the axis, FP64 in and out (in == out allowed: each tile reads before it writes).
+// out = B in along the axis, FP64 in and out (in == out allowed: each tile reads before it writes);
+// the operator table of kDigits planes.
 cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* out, cudaStream_t s);
-
+// The mixed step's version with kDigitsF32 planes: input FP64 (in64) or FP32 (in32), output FP32,
+// and optionally the result also widened to FP64 (out64).
+cudaError_t launch_mode_digit_f32(const ModeDigitArgs& a, const double* in64, const float* in32, float* out,
+                                  double* out64, cudaStream_t s);
+// zero (optional): also set zero[i] = 0 for every output index i (the accumulation
+// target of the Hodge apply that follows the curl).
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
                             cudaStream_t s, double* zero = nullptr);

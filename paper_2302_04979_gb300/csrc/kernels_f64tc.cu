@@ -68,6 +68,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "convert.cuh"
 #include "internal.h"
 #include "pdl.cuh"
 #include "tcgen05.cuh"
@@ -78,8 +79,6 @@ namespace {
 using namespace tc;
 
 constexpr int kDgRows = 128;       // MMA M: operator rows (TMEM lanes)
-constexpr int kDgThreads = 512;    // 16 warps: lane quarter = warp % 4, column group = warp / 4
-constexpr int kDgGroups = kDgThreads / 128;
 constexpr int kDgIssuer = 3;       // the warp (lane quarter 3: rows 96..127, never an output) issuing MMAs
 constexpr int kDgKcMax = (kModeMaxN + 15) / 16 * 2;  // k-chunks of 8 at the largest npad
 constexpr uint32_t kDgTmemCols = 512;
@@ -88,33 +87,67 @@ constexpr int kDgSmemMax = 232448;  // opt-in shared memory per CTA
 
 static_assert(kModeMaxN <= 96, "operator rows must stay in lane quarters 0..2");
 
-__host__ __device__ inline int dg_op_bytes(int npad, int r8) { return kDigits * (npad / 16) * r8 * 32; }
-__host__ __device__ inline int dg_x_bytes(int npad, int nl) { return kDigits * (npad / 16) * nl * 32; }
+__host__ __device__ inline int dg_op_bytes(int npad, int r8, int nd) { return nd * (npad / 16) * r8 * 32; }
+__host__ __device__ inline int dg_x_bytes(int npad, int nl, int nd) { return nd * (npad / 16) * nl * 32; }
 // header, 256 bytes of slack to align the planes to the swizzle pattern, operator and tile planes
-__host__ __device__ inline int dg_smem_bytes(int nl, int npad, int r8) {
-    return kDgHeader + 256 + dg_op_bytes(npad, r8) + dg_x_bytes(npad, nl);
+__host__ __device__ inline int dg_smem_bytes(int nl, int npad, int r8, int nd) {
+    return kDgHeader + 256 + dg_op_bytes(npad, r8, nd) + dg_x_bytes(npad, nl, nd);
 }
 
-// The integer image of an FP64 bit pattern relative to the exponent field E
-// (the largest of the line, at least 1): X = round(v / 2^(E - 1077)), |X| < 2^55,
-// returned as X + C with C = 0x80808080808080 (0 < X + C < 2^57).  With d_t the
-// balanced base-256 digits of X (d_1..d_6 in [-128, 127], d_0 in [-128, 128]),
-// bytes 0..5 of X + C are d_6 + 128 .. d_1 + 128 and bits 48..56 are d_0 + 128.
-__device__ __forceinline__ unsigned long long digit_bytes(unsigned long long bits, int E) {
-    const int e = (int)((bits >> 52) & 0x7FF);
-    const unsigned long long frac = bits & 0xFFFFFFFFFFFFFull;
+// Bit-pattern layout of the two input formats.
+template <class T>
+struct Fmt;
+template <>
+struct Fmt<double> {
+    using U = unsigned long long;
+    static constexpr int kMant = 52, kBias = 1023;
+    static constexpr unsigned kExpMask = 0x7FF;
+    static __device__ __forceinline__ U bits(const double* p, long long i) {
+        return reinterpret_cast<const unsigned long long*>(p)[i];
+    }
+};
+template <>
+struct Fmt<float> {
+    using U = uint32_t;
+    static constexpr int kMant = 23, kBias = 127;
+    static constexpr unsigned kExpMask = 0xFF;
+    static __device__ __forceinline__ U bits(const float* p, long long i) {
+        return reinterpret_cast<const uint32_t*>(p)[i];
+    }
+};
+
+// The integer image of a bit pattern relative to the exponent field E (the
+// largest of the line, at least 1) for ND digits: X = round(v / sigma) with
+// |X| < 2^(8 ND - 1), the line's largest significand shifted left by
+// kTop = 8 ND - 1 - (kMant + 1) (negative: right), sigma = 2^(E - kBias - kMant -
+// kTop).  Returned as X + C with C = 128 (256^ND - 1) / 255 (0x80...80):
+// 0 < X + C < 2^(8 ND + 1).  With d_t the balanced base-256 digits of X (d_1..
+// d_(ND-1) in [-128, 127], d_0 in [-128, 128]), bytes 0..ND-2 of X + C are
+// d_(ND-1) + 128 .. d_1 + 128 and bits 8(ND-1)..8ND are d_0 + 128.
+template <class TIN, int ND>
+__device__ __forceinline__ unsigned long long digit_word(typename Fmt<TIN>::U bits, int E) {
+    using F = Fmt<TIN>;
+    constexpr int kTop = 8 * ND - 1 - (F::kMant + 1);
+    const int e = (int)((bits >> F::kMant) & F::kExpMask);
+    const unsigned long long frac = (unsigned long long)bits & ((1ull << F::kMant) - 1);
     const int eff = e ? e : 1;
-    const unsigned long long M = e ? (frac | (1ull << 52)) : frac;
-    const int dsh = E - eff;  // >= 0
+    const unsigned long long M = e ? (frac | (1ull << F::kMant)) : frac;
+    const int sh = E - eff - kTop;  // right shift of the significand (negative: left)
     unsigned long long mag;
-    if (dsh <= 2) {
-        mag = M << (2 - dsh);
+    if (sh <= 0) {
+        mag = M << (-sh);
     } else {
-        const int sh = dsh - 2;
         mag = sh >= 60 ? 0ull : (M + (1ull << (sh - 1))) >> sh;
     }
-    const unsigned long long x = (bits >> 63) ? (0ull - mag) : mag;
-    return x + 0x80808080808080ull;
+    const bool neg = (bits >> (8 * sizeof(bits) - 1)) != 0;
+    const unsigned long long x = neg ? (0ull - mag) : mag;
+    return x + (0x8080808080808080ull >> (64 - 8 * ND));
+}
+
+// log2 of sigma for an exponent field E (see digit_word).
+template <class TIN, int ND>
+__device__ __forceinline__ int digit_scale(int E) {
+    return E - Fmt<TIN>::kBias - Fmt<TIN>::kMant - (8 * ND - 1 - (Fmt<TIN>::kMant + 1));
 }
 
 // FP32 pattern of (byte j of w) - 128, exact: PRMT builds 0x4B0000bb = 2^23 + b,
@@ -124,9 +157,10 @@ __device__ __forceinline__ uint32_t digit_f32(uint32_t w, int j) {
     const uint32_t f = __byte_perm(w, 0x4B000000u, (uint32_t)j | 0x7540u);
     return __float_as_uint(__uint_as_float(f) - 8388736.0f);
 }
-// The same for the top digit, whose biased value t = bits 48..56 may reach 256.
+// The same for the top digit, whose biased value (bits 8(ND-1)..8ND) may reach 256.
+template <int ND>
 __device__ __forceinline__ uint32_t top_digit_f32(unsigned long long u) {
-    return __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)(u >> 48)) - 8388736.0f);
+    return __float_as_uint(__uint_as_float(0x4B000000u | (uint32_t)(u >> (8 * (ND - 1)))) - 8388736.0f);
 }
 
 // acc * 2^e2 rounded to the nearest double (ties to even), by integer
@@ -164,12 +198,49 @@ __device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
 }
 
 
-template <int NL>
-__global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs A, const double* in, double* out) {
-    constexpr int kBufs = (int)kDgTmemCols / NL;                 // level buffers in the ring
-    constexpr int kCpw = NL / kDgGroups;                        // columns (lines) per reader warp
-    constexpr int kItems = (NL * kDgKcMax + kDgThreads - 1) / kDgThreads;
-    static_assert(kCpw % 8 == 0 && kBufs >= 1, "tile shape");
+// acc * 2^e2 rounded to the nearest float (ties to even), by integer
+// instructions while the result is a normal number (else through FP64).
+__device__ __forceinline__ float scaled_to_float(long long acc, int e2) {
+    if (acc == 0) return 0.0f;
+    const uint32_t sgn = acc < 0 ? 0x80000000u : 0u;
+    const unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
+    int pb = 63 - __clzll((long long)a);
+    unsigned long long m;
+    if (pb <= 23) {
+        m = a << (23 - pb);
+    } else {
+        const int sh = pb - 23;
+        m = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            m += 1;
+            if (m >> 24) {
+                m >>= 1;
+                pb += 1;
+            }
+        }
+    }
+    const int be = pb + e2 + 127;
+    if (be >= 1 && be <= 254) return __uint_as_float(sgn | ((uint32_t)be << 23) | ((uint32_t)m & 0x7FFFFFu));
+    return (float)scaled_to_double(acc, e2);
+}
+
+// Output of a tile entry: FP64, or FP32 with an optional exact FP64 copy.
+__device__ __forceinline__ double digit_out(long long acc, int e2, double*) { return scaled_to_double(acc, e2); }
+__device__ __forceinline__ float digit_out(long long acc, int e2, float*) { return scaled_to_float(acc, e2); }
+
+
+template <int NL, int ND, int THREADS, class TIN, class TOUT>
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
+    mode_digit_kernel(ModeDigitArgs A, const TIN* in, TOUT* out, double* out64) {
+    using U = typename Fmt<TIN>::U;
+    constexpr int kGroups = THREADS / 128;                     // reader warps per lane quarter
+    constexpr int kBufs = ND < (int)kDgTmemCols / NL ? ND : (int)kDgTmemCols / NL;  // level buffers in the ring
+    constexpr uint32_t kCols = kBufs * NL <= 128 ? 128u : (kBufs * NL <= 256 ? 256u : 512u);
+    constexpr int kCpw = NL / kGroups;                         // columns (lines) per reader warp
+    constexpr int kItems = (NL * kDgKcMax + THREADS - 1) / THREADS;
+    constexpr int kTopOp = 8 * ND - 1 - 53;                    // operator rows: FP64 significands
+    static_assert(kCpw % 8 == 0 && kBufs >= 1 && kBufs * NL <= (int)kDgTmemCols, "tile shape");
     extern __shared__ __align__(1024) unsigned char smem[];
     // nothing before pdl_wait reads what the previous kernel of the stream writes:
     // the operator table, tensor memory and the barriers are set up while it drains
@@ -188,7 +259,7 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 128);
     int* sExp = reinterpret_cast<int*>(smem + 256);
     unsigned char* sOp = smem + kDgHeader + ((256u - ((smem_u32(smem) + kDgHeader) & 255u)) & 255u);
-    unsigned char* sX = sOp + dg_op_bytes(npad, r8);
+    unsigned char* sX = sOp + dg_op_bytes(npad, r8, ND);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, group = warp >> 2;
     const int nquarters = (n + 31) / 32;          // lane quarters holding output rows (<= 3)
@@ -196,31 +267,31 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
-                     "r"(kDgTmemCols)
+                     "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0)
         for (int b = 0; b < kBufs; ++b) {
             mbar_init(full0 + 8 * b, 1);
-            mbar_init(drained0 + 8 * b, kDgGroups * nquarters);
+            mbar_init(drained0 + 8 * b, kGroups * nquarters);
         }
     if (tid < NL) sExp[tid] = 1;
 
     // operator digits: the table is the shared layout, one contiguous copy
     const unsigned char* Bg = static_cast<const unsigned char*>(A.B[c]);
-    for (int t = tid; t < kDigits * opPlane / 16; t += kDgThreads) cp_async16(sOp + 16 * t, Bg + 16 * (size_t)t);
+    for (int t = tid; t < ND * opPlane / 16; t += THREADS) cp_async16(sOp + 16 * t, Bg + 16 * (size_t)t);
     pdl_wait();  // the input lines are the previous kernel's output
 
     // data tile as bit patterns: items (line r, k-chunk q) of 8 values
     const int nx = C.n[0], nxy = C.n[0] * C.n[1];
     const int stride = axis == 0 ? 1 : (axis == 1 ? nx : nxy);
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + C.off);
+    const TIN* src = in + C.off;
     const int nitems = NL * kc;
-    unsigned long long val[kItems][8];
+    U val[kItems][8];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        const int g = tid + it * kDgThreads;
+        const int g = tid + it * THREADS;
         int r, q;
         if (axis == 0) {  // k-chunk fastest: a line's values are contiguous
             r = g / kc;
@@ -236,24 +307,24 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const int k = 8 * q + t;
-            val[it][t] = (live && k < n) ? src[base + (long long)k * stride] : 0ull;
+            val[it][t] = (live && k < n) ? Fmt<TIN>::bits(src, base + (long long)k * stride) : (U)0;
         }
     }
     __syncthreads();  // sExp initialised
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        const int g = tid + it * kDgThreads;
+        const int g = tid + it * THREADS;
         if (g >= nitems) break;
         const int r = axis == 0 ? g / kc : g % NL;
         int emax = 1;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) emax = max(emax, (int)((val[it][t] >> 52) & 0x7FF));
+        for (int t = 0; t < 8; ++t) emax = max(emax, (int)((val[it][t] >> Fmt<TIN>::kMant) & Fmt<TIN>::kExpMask));
         atomicMax(sExp + r, emax);
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        const int g = tid + it * kDgThreads;
+        const int g = tid + it * THREADS;
         if (g >= nitems) break;
         int r, q;
         if (axis == 0) {
@@ -264,23 +335,24 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
             r = g - q * NL;
         }
         const int E = sExp[r];
-        uint32_t w[kDigits][4];
+        uint32_t w[ND][4];
 #pragma unroll
         for (int t = 0; t < 8; t += 2) {
-            const unsigned long long u0 = digit_bytes(val[it][t], E), u1 = digit_bytes(val[it][t + 1], E);
+            const unsigned long long u0 = digit_word<TIN, ND>(val[it][t], E);
+            const unsigned long long u1 = digit_word<TIN, ND>(val[it][t + 1], E);
             const uint32_t lo0 = (uint32_t)u0, hi0 = (uint32_t)(u0 >> 32);
             const uint32_t lo1 = (uint32_t)u1, hi1 = (uint32_t)(u1 >> 32);
 #pragma unroll
-            for (int j = 0; j < kDigits - 1; ++j) {  // byte j -> digit plane 6 - j; two BF16 per word
+            for (int j = 0; j < ND - 1; ++j) {  // byte j -> digit plane ND-1-j; two BF16 per word
                 const uint32_t f0 = digit_f32(j < 4 ? lo0 : hi0, j & 3), f1 = digit_f32(j < 4 ? lo1 : hi1, j & 3);
-                w[kDigits - 1 - j][t >> 1] = __byte_perm(f0, f1, 0x7632);
+                w[ND - 1 - j][t >> 1] = __byte_perm(f0, f1, 0x7632);
             }
-            w[0][t >> 1] = __byte_perm(top_digit_f32(u0), top_digit_f32(u1), 0x7632);
+            w[0][t >> 1] = __byte_perm(top_digit_f32<ND>(u0), top_digit_f32<ND>(u1), 0x7632);
         }
         // atom column q / 2, row r, 16-byte half (q & 1) exchanged by bit 2 of r
         unsigned char* dst = sX + (q >> 1) * colX + 32 * r + 16 * ((q & 1) ^ ((r >> 2) & 1));
 #pragma unroll
-        for (int s = 0; s < kDigits; ++s)
+        for (int s = 0; s < ND; ++s)
             *reinterpret_cast<uint4*>(dst + s * xPlane) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -290,8 +362,9 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     tc_fence_after();
     const uint32_t tmem = *holder;
     bool ok = true;
-    double* dst = out + C.off;
-    double* stage = reinterpret_cast<double*>(sX);  // y/z sweeps: n x (NL + 1), after the last MMA
+    TOUT* dst = out + C.off;
+    double* dst64 = out64 ? out64 + C.off : nullptr;
+    TOUT* stage = reinterpret_cast<TOUT*>(sX);  // y/z sweeps: n x (NL + 1), after the last MMA
 
     if (warp == kDgIssuer) {
         if (lane == 0) {
@@ -299,7 +372,7 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
             // the first MMA of a level overwrites the buffer
             const uint32_t idesc = idesc_bf16_f32(kDgRows, NL);
             const uint32_t a0 = smem_u32(sOp), b0 = smem_u32(sX);
-            for (int lv = 0; lv < kDigitLevels && ok; ++lv) {
+            for (int lv = 0; lv < ND && ok; ++lv) {
                 const int buf = lv % kBufs;
                 if (lv >= kBufs) {
                     ok = mbar_wait_bounded(drained0 + 8 * buf, ((lv - kBufs) / kBufs) & 1);
@@ -324,7 +397,7 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
         unsigned long long acc[kCpw];  // Horner accumulators, two's complement (wraps only on unused rows)
 #pragma unroll
         for (int j = 0; j < kCpw; ++j) acc[j] = 0;
-        for (int lv = 0; lv < kDigitLevels; ++lv) {
+        for (int lv = 0; lv < ND; ++lv) {
             const int buf = lv % kBufs;
             ok = __all_sync(0xffffffffu, mbar_wait_bounded(full0 + 8 * buf, (lv / kBufs) & 1));
             if (!ok) break;
@@ -345,19 +418,22 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
                     // exact: the accumulators hold integers below 2^24
                     const long long p = __float2int_rn(__uint_as_float(v[ch][j]));
                     unsigned long long& a = acc[8 * ch + j];
-                    a = lv < kDigitLevels - 1 ? a * 256ull + (unsigned long long)p
-                                              : a + (unsigned long long)(p >> 8);
+                    a = lv < ND - 1 ? a * 256ull + (unsigned long long)p : a + (unsigned long long)(p >> 8);
                 }
         }
         if (!ok) {
             if (lane == 0) atomicOr(A.status, 1u);
         } else if (i < n) {
+            const int eRow = 8 * ND + Fi - 1075 - kTopOp;  // 2^(8 ND) tau_i
 #pragma unroll
             for (int j = 0; j < kCpw; ++j) {
                 const int col = group * kCpw + j, L = l0 + col;
-                const double y = scaled_to_double((long long)acc[j], sExp[col] + Fi - 2098);
+                const TOUT y = digit_out((long long)acc[j], eRow + digit_scale<TIN, ND>(sExp[col]), (TOUT*)nullptr);
                 if (axis == 0) {
-                    if (L < nlines) dst[(long long)L * n + i] = y;
+                    if (L < nlines) {
+                        dst[(long long)L * n + i] = y;
+                        if (dst64) dst64[(long long)L * n + i] = f2d_exact(y);
+                    }
                 } else {
                     stage[i * (NL + 1) + col] = y;  // every MMA has completed: the digit planes are free
                 }
@@ -369,69 +445,95 @@ __global__ void __launch_bounds__(kDgThreads, 1) mode_digit_kernel(ModeDigitArgs
     pdl_trigger();  // the next kernel may be scheduled; its pdl_wait still waits for this grid
     if (ok && axis != 0) {
         const int nl = min(NL, nlines - l0);
-        for (int g = tid; g < n * NL; g += kDgThreads) {
+        for (int g = tid; g < n * NL; g += THREADS) {
             const int ii = g / NL, col = g - ii * NL;
             if (col >= nl) continue;
             const int L = l0 + col;
-            const long long base = axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L;
-            dst[base + (long long)ii * stride] = stage[ii * (NL + 1) + col];
+            const long long o = (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L) + (long long)ii * stride;
+            const TOUT y = stage[ii * (NL + 1) + col];
+            dst[o] = y;
+            if (dst64) dst64[o] = f2d_exact(y);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kDgTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
 }  // namespace
 
 int mode_digit_npad(int n) { return (n + 15) / 16 * 16; }
 
-// Lines per tile for this sweep.  The MMA time is proportional to N (about 2 cycles
-// per column of an M = 128, K = 16 instruction on GB300), so the tile only decides
-// how the lines spread over the SMs: 128-line tiles while they still fill all 152
-// SMs with one wave, else 96 (one wave of 135 CTAs at p = 3, 64^3 instead of 102).
+// Lines per tile of an FP64 sweep.  The MMA time is proportional to N (about 2
+// cycles per column of an M = 128, K = 16 instruction on GB300), so the tile only
+// decides how the lines spread over the SMs: 128-line tiles while they still
+// fill all 152 SMs with one wave, else 96 (one wave of 135 CTAs at p = 3, 64^3).
 static int digit_tile_lines(const ModeDigitArgs& a, long long maxlines) {
     const long long tiles128 = 3 * ((maxlines + 127) / 128);
     bool fits128 = true;
     for (int c = 0; c < 3; ++c) {
         const int n = a.field.c[c].n[a.axis];
-        if (n > 0 && dg_smem_bytes(128, a.npad[c], (n + 7) & ~7) > kDgSmemMax) fits128 = false;
+        if (n > 0 && dg_smem_bytes(128, a.npad[c], (n + 7) & ~7, kDigits) > kDgSmemMax) fits128 = false;
     }
     return (fits128 && tiles128 >= 152) ? 128 : 96;
 }
 
-template <int NL>
-static cudaError_t launch_digit_t(const ModeDigitArgs& a, const double* in, double* out, long long maxlines,
-                                  int smem, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mode_digit_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDgSmemMax);
-        attr = true;
-    }
-    const dim3 grid((unsigned)((maxlines + NL - 1) / NL), 3);
-    return launch_k(mode_digit_kernel<NL>, grid, dim3(kDgThreads), (size_t)smem, s, a, in, out);
-}
-
-cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* out, cudaStream_t s) {
+// Largest line count of the sweep (0: nothing to do; -1: invalid arguments).
+static long long digit_lines(const ModeDigitArgs& a) {
     long long maxlines = 0;
     for (int c = 0; c < 3; ++c) {
         const long long nc = (long long)a.field.c[c].n[0] * a.field.c[c].n[1] * a.field.c[c].n[2];
         const int n = a.field.c[c].n[a.axis];
         if (n <= 0) continue;
-        if (n > kModeMaxN || a.npad[c] != mode_digit_npad(n) || !a.B[c] || !a.rowexp[c]) return cudaErrorInvalidValue;
+        if (n > kModeMaxN || a.npad[c] != mode_digit_npad(n) || !a.B[c] || !a.rowexp[c]) return -1;
         maxlines = std::max(maxlines, nc / n);
     }
-    if (maxlines == 0) return cudaSuccess;
-    const int nl = digit_tile_lines(a, maxlines);
+    return maxlines;
+}
+
+static int digit_smem(const ModeDigitArgs& a, int nl, int nd) {
     int smem = 0;
     for (int c = 0; c < 3; ++c) {
         const int n = a.field.c[c].n[a.axis];
-        if (n > 0) smem = std::max(smem, dg_smem_bytes(nl, a.npad[c], (n + 7) & ~7));
+        if (n > 0) smem = std::max(smem, dg_smem_bytes(nl, a.npad[c], (n + 7) & ~7, nd));
     }
+    return smem;
+}
+
+template <int NL, int ND, int THREADS, class TIN, class TOUT>
+static cudaError_t launch_digit_t(const ModeDigitArgs& a, const TIN* in, TOUT* out, double* out64,
+                                  long long maxlines, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mode_digit_kernel<NL, ND, THREADS, TIN, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kDgSmemMax);
+        attr = true;
+    }
+    const int smem = digit_smem(a, NL, ND);
     if (smem > kDgSmemMax) return cudaErrorInvalidValue;
-    return nl == 128 ? launch_digit_t<128>(a, in, out, maxlines, smem, s)
-                     : launch_digit_t<96>(a, in, out, maxlines, smem, s);
+    const dim3 grid((unsigned)((maxlines + NL - 1) / NL), 3);
+    return launch_k(mode_digit_kernel<NL, ND, THREADS, TIN, TOUT>, grid, dim3(THREADS), (size_t)smem, s, a, in, out,
+                    out64);
+}
+
+cudaError_t launch_mode_digit(const ModeDigitArgs& a, const double* in, double* out, cudaStream_t s) {
+    const long long maxlines = digit_lines(a);
+    if (maxlines < 0) return cudaErrorInvalidValue;
+    if (maxlines == 0) return cudaSuccess;
+    return digit_tile_lines(a, maxlines) == 128
+               ? launch_digit_t<128, kDigits, 512, double, double>(a, in, out, nullptr, maxlines, s)
+               : launch_digit_t<96, kDigits, 512, double, double>(a, in, out, nullptr, maxlines, s);
+}
+
+// The mixed step's line operators: four digits, the FP64 kernel's tile shape.
+cudaError_t launch_mode_digit_f32(const ModeDigitArgs& a, const double* in64, const float* in32, float* out,
+                                  double* out64, cudaStream_t s) {
+    const long long maxlines = digit_lines(a);
+    if (maxlines < 0) return cudaErrorInvalidValue;
+    if (maxlines == 0) return cudaSuccess;
+    if (in64) return launch_digit_t<96, kDigitsF32, 512, double, float>(a, in64, out, out64, maxlines, s);
+    return launch_digit_t<96, kDigitsF32, 512, float, float>(a, in32, out, out64, maxlines, s);
 }
 
 }  // namespace smx

@@ -213,45 +213,22 @@ static uint16_t bf16_nearest(float f) {
     return static_cast<uint16_t>(u >> 16);
 }
 
-static double bf16_to_double(uint16_t h) {
-    const uint32_t u = static_cast<uint32_t>(h) << 16;
-    float f;
-    std::memcpy(&f, &u, sizeof f);
-    return f;
-}
-
-std::vector<uint16_t> bf16_split_operator(const std::vector<double>& B, int n, int npad) {
-    const size_t chunk = static_cast<size_t>(8) * npad + 8, part = static_cast<size_t>(npad / 8) * chunk;
-    std::vector<uint16_t> out(3 * part, 0);
-    for (int i = 0; i < n; ++i)
-        for (int k = 0; k < n; ++k) {
-            double r = B[static_cast<size_t>(i) * n + k];
-            for (int q = 0; q < 3; ++q) {
-                const uint16_t h = bf16_nearest(static_cast<float>(r));
-                out[q * part + (k / 8) * chunk + static_cast<size_t>(8) * i + k % 8] = h;
-                r -= bf16_to_double(h);  // exact: r and h agree in their leading bits
-            }
-        }
-    return out;
-}
-
-void digits56(double v, int F, int d[7]) {
+void digits_fixed(double v, int F, int nd, int* d) {
     uint64_t bits;
     std::memcpy(&bits, &v, sizeof bits);
     const int e = static_cast<int>((bits >> 52) & 0x7FF);
     const uint64_t frac = bits & 0xFFFFFFFFFFFFFull;
     const int eff = e ? e : 1;
     const uint64_t M = e ? (frac | (1ull << 52)) : frac;
-    const int dsh = F - eff;
+    const int sh = F - eff - (8 * nd - 1 - 53);  // right shift of the significand (negative: left)
     uint64_t mag;
-    if (dsh <= 2) {
-        mag = M << (2 - dsh);
+    if (sh <= 0) {
+        mag = M << (-sh);
     } else {
-        const int sh = dsh - 2;
         mag = sh >= 60 ? 0 : (M + (1ull << (sh - 1))) >> sh;
     }
     int64_t a = (bits >> 63) ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
-    for (int t = 6; t >= 1; --t) {
+    for (int t = nd - 1; t >= 1; --t) {
         const int dg = static_cast<int>((static_cast<uint64_t>(a) + 128) & 255) - 128;
         d[t] = dg;
         a = (a - dg) / 256;  // exact
@@ -259,12 +236,13 @@ void digits56(double v, int F, int d[7]) {
     d[0] = static_cast<int>(a);
 }
 
-void digit_split_operator(const std::vector<double>& B, int n, int npad, std::vector<uint16_t>& planes,
+void digit_split_operator(const std::vector<double>& B, int n, int npad, int nd, std::vector<uint16_t>& planes,
                           std::vector<int32_t>& rowexp) {
     const int r8 = (n + 7) / 8 * 8;
     const size_t col = static_cast<size_t>(r8) * 16, plane = static_cast<size_t>(npad / 16) * col;
-    planes.assign(7 * plane, 0);
+    planes.assign(nd * plane, 0);
     rowexp.assign(r8, 1);
+    std::vector<int> d(nd);
     for (int i = 0; i < n; ++i) {
         int F = 1;
         for (int k = 0; k < n; ++k) {
@@ -274,12 +252,10 @@ void digit_split_operator(const std::vector<double>& B, int n, int npad, std::ve
         }
         rowexp[i] = F;
         for (int k = 0; k < n; ++k) {
-            int d[7];
-            digits56(B[static_cast<size_t>(i) * n + k], F, d);
-            for (int s = 0; s < 7; ++s)
+            digits_fixed(B[static_cast<size_t>(i) * n + k], F, nd, d.data());
+            for (int s = 0; s < nd; ++s)
                 planes[s * plane + static_cast<size_t>(k / 16) * col + static_cast<size_t>(16) * i +
-                       8 * (((k / 8) & 1) ^ ((i >> 2) & 1)) + k % 8] =
-                    bf16_nearest(static_cast<float>(d[s]));
+                       8 * (((k / 8) & 1) ^ ((i >> 2) & 1)) + k % 8] = bf16_nearest(static_cast<float>(d[s]));
         }
     }
 }

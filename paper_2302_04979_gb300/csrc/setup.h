@@ -52,25 +52,21 @@ std::vector<double> band_lu_dense(const BandLU& f);
 // int_e phi_i phi_j with q = p+1 Gauss points.
 std::vector<double> element_mass(int kind, int p, int nel, int e);
 
-// Three-term BF16 split of a dense n x n row-major FP64 operator B,
-// B ~= B0 + B1 + B2 (each remainder taken exactly in FP64), laid out for the
-// tensor-core mode products: part q, element (row i, column k) at uint16 index
-//   q * (npad / 8) * (8 npad + 8) + (k / 8) * (8 npad + 8) + 8 i + k % 8,
-// zero outside n x n (npad a multiple of 16, >= n).
-std::vector<uint16_t> bf16_split_operator(const std::vector<double>& B, int n, int npad);
 
-// Digit planes of a dense n x n row-major FP64 operator B for the FP64
-// tensor-core mode products: every row i is scaled by 2^(F_i - 1077), F_i its
-// largest exponent field (at least 1), rounded to an integer X with
-// |X| < 2^55 and written as seven balanced base-256 digits
-// X = sum_s e_s 256^(6-s), e_s in [-128, 128] (integer arithmetic only).
+// Digit planes of a dense n x n row-major FP64 operator B for the tensor-core
+// mode products with nd digits (7: FP64 step, 4: mixed step): every row i is
+// scaled by a power of two from F_i, its largest exponent field (at least 1),
+// rounded to an integer X with |X| < 2^(8 nd - 1) (the row's largest
+// significand shifted left by 8 nd - 1 - 53) and written as nd balanced
+// base-256 digits X = sum_s e_s 256^(nd-1-s), e_s in [-128, 127] (e_0 in
+// [-128, 128]), integer arithmetic only.
 // planes: BF16 patterns in the K-major 32-byte swizzle layout, digit s,
 // element (row i, column k) at uint16 index
 //   s * (npad / 16) * r8 * 16 + (k / 16) * r8 * 16 + 16 i + 8 (((k / 8) & 1) ^ ((i / 4) & 1)) + k % 8,
 // r8 = n rounded up to 8, zero outside n x n.  rowexp: F_i for i < n.
-void digit_split_operator(const std::vector<double>& B, int n, int npad, std::vector<uint16_t>& planes,
+void digit_split_operator(const std::vector<double>& B, int n, int npad, int nd, std::vector<uint16_t>& planes,
                           std::vector<int32_t>& rowexp);
-// The same digits of one value for a given F (the host reference of the device cut).
-void digits56(double v, int F, int d[7]);
+// The digits of one value for a given F (d[0..nd-1], most significant first).
+void digits_fixed(double v, int F, int nd, int* d);
 
 }  // namespace smx

@@ -231,7 +231,7 @@ class Context:
 
     def set_mode_kernel(self, which):
         """Line operators of the Hodge stars.  Mixed context: dense products on the "tensor" cores
-        (BF16 split) or on FP32 "simt" cores ("auto", the default, is "simt").  FP64 context:
+        (exact four-digit slicing) or on FP32 "simt" cores ("auto", the default, is "simt").  FP64 context:
         dense products on the "tensor" cores by exact digit slicing (lines of at most 80 entries),
         banded LU recurrences on the FP64 "simt" pipe, or "auto" (default): per star the faster
         of the two -- tensor cores for a separable star, recurrences for the pairing sweeps."""
