@@ -204,8 +204,9 @@ BF16_PEAK_TFLOPS = 1992.0  # MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)
 DIGIT_PAIRS = 28           # digit products (levels 0..6 of seven digits) per FP64 dense line product
 
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel at this
-# workload (profiles/fp64_step_p3_64cube.md, profiles/mixed_step_p3_64cube.md; cold
-# caches, outputs stay in L2).  Kept only while the kernel is unchanged since the capture.
+# workload (profiles/fp64_step_p3_64cube.md, profiles/mixed_step_p3_64cube.md,
+# profiles/digit_line_p3_64cube.md; cold caches, outputs stay in L2).  Kept only while
+# the kernel is unchanged since the capture.
 NCU_TRAFFIC = {
     "mass_solve_x": 6.90e6, "mass_solve_y": 6.90e6, "mass_solve_z": 6.90e6,
     "solve_x": 6.72e6, "solve_y": 6.72e6, "solve_z": 6.72e6,
@@ -213,6 +214,8 @@ NCU_TRAFFIC = {
     # mixed step, CUDA-core line operators (x passes read FP64 input)
     "line_f32_x": 6.93e6, "line_f32_y": 3.56e6, "line_f32_z": 3.56e6,
     "hodge_block_f32": 13.51e6,
+    # FP64 line operators on the tensor cores (profiles/digit_line_p3_64cube.md)
+    "line_f64tc_x": 7.15e6, "line_f64tc_y": 7.15e6, "line_f64tc_z": 7.15e6,
 }
 
 
