@@ -154,9 +154,10 @@ int smx_set_graphs(smx_ctx* ctx, int enable);
  *     digits, each digit level accumulated exactly in FP32 -- with the
  *     rounding error bound of an FP64 dot product;
  *   SMX_MODE_SIMT: banded LU recurrences on the FP64 pipe (any line length);
- *   SMX_MODE_AUTO (default): per star, the faster of the two on GB300 --
- *     the tensor-core products for a separable star (fused mass + solve),
- *     the banded recurrences for the pairing sweeps after a mass apply.
+ *   SMX_MODE_AUTO (default): per star, the faster of the two as measured on
+ *     GB300 -- the tensor-core products once lines reach 48 entries, for a
+ *     separable star (fused mass + solve) and, from degree 4, for the pairing
+ *     sweeps after a mass apply; the banded recurrences otherwise.
  * The selection applies where the context has dense operators; elsewhere the
  * banded recurrences run.  Errors: SMX_EINVAL. */
 #define SMX_MODE_TENSOR 0

@@ -667,12 +667,20 @@ int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
 // scratch vector followed by the three pairing sweeps.
 int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezeroed) {
     const int which = h == 0 ? 1 : 0;
-    // SMX_MODE_AUTO takes, per star, the kernel measured faster on GB300 at the
-    // workload sizes: the tensor-core digit products for a separable star (they
-    // replace fused mass + solve recurrences of 2(2d+1) + 4 KL + 1 flops per
-    // entry), the banded recurrences for the pairing sweeps (4 KL + 1 flops)
-    const bool digit = C->use_digit && C->precision == SMX_FP64 && (C->mode_kernel == SMX_MODE_TENSOR ||
-                                        (C->mode_kernel == SMX_MODE_AUTO && C->hodge[h].separable));
+    // SMX_MODE_AUTO takes, per star, the kernel measured faster on GB300.  The
+    // banded recurrences cost about n (2(2d+1) + 4 KL + 1) dependent FP64 steps
+    // per line (fused mass + solve) or n (4 KL + 1) (pairing sweep); the digit
+    // kernel costs about 15 us of fixed latency plus time proportional to the
+    // lines.  Measured: the digit passes win for a separable star once lines
+    // reach about 48 entries, and for the pairing sweeps too from p = 4 (KL = 3).
+    int maxlen = 0, maxkl = 0;
+    for (int a = 0; a < 3; ++a) {
+        maxlen = std::max(maxlen, kind_dim(P0, C->p[a], C->nel[a]) + 1);
+        maxkl = std::max(maxkl, C->p[a] - 1);
+    }
+    const bool auto_digit = maxlen >= 48 && (C->hodge[h].separable || maxkl >= 3);
+    const bool digit = C->use_digit && C->precision == SMX_FP64 &&
+                       (C->mode_kernel == SMX_MODE_TENSOR || (C->mode_kernel == SMX_MODE_AUTO && auto_digit));
     if (digit) {
         // dense line operators on the tensor cores: A^{-1} M per axis (separable), or
         // the mass apply followed by A^{-1} per axis
