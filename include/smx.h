@@ -236,6 +236,26 @@ int smx_cfl(smx_ctx* ctx, int iters, double tol, double* v, double* w, double* t
 int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
                   const double* jhat, const double* amp, double dt, int nsteps);
 
+/* Host callback for smx_project: out[3i + c] = component c of the physical
+ * vector proxy of a 2-form at the physical point (xyz[3i], xyz[3i+1],
+ * xyz[3i+2]), i < n. */
+typedef void (*smx_field_fn)(int64_t n, const double* xyz, double* out, void* user);
+
+/* L2 projection of a physical 2-form (initial data and the source profile by
+ * projection, Sec. 5.1.1) onto X~^2 (field = SMX_FIELD_D, coefficients d or
+ * jhat; N_e values) or X^2_{h,0} (SMX_FIELD_B, coefficients b; N_h values).
+ * Through the Piola map of 2-forms the right-hand side is
+ * r_i = int (J^T V) . vhat_i dxhat and the coefficients solve M_1 x = r with
+ * the unweighted 2-form mass (Sec. 3.4 with gamma = 1); Gauss-Legendre with
+ * p + 1 points per element and axis.  Solved on the host in FP64 by conjugate
+ * gradients preconditioned with the identity-map mass (exact on the identity
+ * map), to a relative residual of 1e-14.  fn is called once per slab of
+ * elements along z.  Host only: no workspace or GPU needed; coeffs is a host
+ * array.  Errors: SMX_EINVAL (field, null pointers), SMX_ENONFINITE (fn
+ * returned a non-finite value), SMX_ESINGULAR (no convergence in 500
+ * iterations). */
+int smx_project(const smx_ctx* ctx, int field, smx_field_fn fn, void* user, double* coeffs);
+
 /* Kernel accounting for benchmarks.  smx_launch_count returns the number of
  * device kernels this context has launched so far (memsets and copies are not
  * counted).  smx_set_timing(ctx, 1) brackets every later launch with CUDA

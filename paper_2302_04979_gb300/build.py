@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsmx.so")
-SOURCES = ["setup.cpp", "kernels.cu", "kernels_f32.cu", "kernels_f64tc.cu", "kernels_adj.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "project.cpp", "kernels.cu", "kernels_f32.cu", "kernels_f64tc.cu", "kernels_adj.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -151,27 +151,6 @@ const int kFieldOfHodge[2] = {SMX_FIELD_B, SMX_FIELD_D};
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-// map, Jacobian and determinant at a parametric point
-void geometry_eval(int geom, double a, const double xh[3], double X[3], double J[9]) {
-    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0) ? 1.0 : 0.0;
-    for (int i = 0; i < 3; ++i) X[i] = xh[i];
-    if (geom == SMX_GEOM_SINE_BUMP) {
-        const double pi = 3.14159265358979323846;
-        const double sx = std::sin(pi * xh[0]), sy = std::sin(pi * xh[1]), sz = std::sin(pi * xh[2]);
-        const double cx = std::cos(pi * xh[0]), cy = std::cos(pi * xh[1]), cz = std::cos(pi * xh[2]);
-        const double S = sx * sy * sz;
-        const double g[3] = {pi * cx * sy * sz, pi * sx * cy * sz, pi * sx * sy * cz};
-        for (int i = 0; i < 3; ++i) {
-            X[i] += a * S;
-            for (int j = 0; j < 3; ++j) J[3 * i + j] += a * g[j];
-        }
-    }
-}
-
-double det3(const double J[9]) {
-    return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
-}
-
 int check_material(const smx_material& m, const int nel[3]) {
     if (m.kind == SMX_MAT_CONST) return finite_pos(m.value) ? SMX_OK : SMX_EMAT;
     if (m.kind == SMX_MAT_BLOCKS) {
@@ -1259,6 +1238,16 @@ int smx_set_mode_kernel(smx_ctx* C, int which) {
     }
     C->mode_kernel = which;
     return SMX_OK;
+}
+
+int smx_project(const smx_ctx* C, int field, smx_field_fn fn, void* user, double* coeffs) {
+    if (!C || !fn || !coeffs || (field != SMX_FIELD_B && field != SMX_FIELD_D)) return SMX_EINVAL;
+    try {
+        int iters = 0;
+        return l2_project_2form(C->p, C->nel, C->geometry, C->amp, field, fn, user, coeffs, 1e-14, 500, &iters);
+    } catch (const std::bad_alloc&) {
+        return SMX_ENOMEM;
+    }
 }
 
 int smx_mode_kernel(const smx_ctx* C, int* which) {

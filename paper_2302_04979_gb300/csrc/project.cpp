@@ -1,0 +1,275 @@
+// L2 projection of a physical 2-form onto X~^2 or X^2_{h,0} (initial data and
+// the source profile by projection, Sec. 5.1.1), on the host in FP64.
+//
+// A 2-form with physical vector proxy V is pulled back through the Piola map
+// v = J vhat / det J (Sec. 2.2), so the right-hand side of the projection is
+//   r_i = int_Omega V . (J vhat_i / det J) dx = int_Omegahat (J^T V) . vhat_i dxhat,
+// and the coefficients solve M_1 x = r with the unweighted 2-form mass
+//   (M_1)_ij = int_Omegahat vhat_i^T (J^T J / det J) vhat_j dxhat.
+// Both integrals use the Gauss-Legendre rule with p_a + 1 points per element
+// and axis, the rule of the Hodge masses.  The system is solved by conjugate
+// gradients preconditioned with the identity-map mass, which is the Kronecker
+// product of 1D masses per component and is solved exactly by banded sweeps:
+// on the identity map the preconditioner is M_1 itself.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "setup.h"
+#include "smx.h"
+
+namespace smx {
+namespace {
+
+struct Axis1D {
+    int q = 0;                 // Gauss points per element
+    std::vector<double> x, w;  // on [0, 1]
+};
+
+// One component of the 2-form space: kinds and extents per axis.
+struct Comp {
+    int kind[3], deg[3], dim[3], off[3];
+    long long base;
+};
+
+struct Space {
+    int p[3], nel[3], geom;
+    double amp;
+    Comp c[3];
+    long long total;
+    Axis1D ax[3];
+    // basis values: per axis and kind, [element][point][r], r = 0..deg
+    std::vector<double> bval[3][4];
+};
+
+void build_space(Space& S, const int p[3], const int nel[3], int geom, double amp, int field) {
+    for (int a = 0; a < 3; ++a) {
+        S.p[a] = p[a];
+        S.nel[a] = nel[a];
+        S.ax[a].q = p[a] + 1;
+        gauss_legendre01(S.ax[a].q, S.ax[a].x, S.ax[a].w);
+        for (int kind = 0; kind < 4; ++kind) {
+            const int d = kind_degree(kind, p[a]);
+            S.bval[a][kind].assign((size_t)nel[a] * S.ax[a].q * (d + 1), 0.0);
+            for (int e = 0; e < nel[a]; ++e)
+                for (int k = 0; k < S.ax[a].q; ++k) {
+                    double v[16];
+                    local_basis(kind, p[a], nel[a], e, (e + S.ax[a].x[k]) / nel[a], v);
+                    for (int r = 0; r <= d; ++r) S.bval[a][kind][((size_t)e * S.ax[a].q + k) * (d + 1) + r] = v[r];
+                }
+        }
+    }
+    S.geom = geom;
+    S.amp = amp;
+    long long off = 0;
+    for (int c = 0; c < 3; ++c) {
+        Comp& C = S.c[c];
+        long long n = 1;
+        for (int a = 0; a < 3; ++a) {
+            C.kind[a] = kFieldKinds[field][c][a];
+            C.deg[a] = kind_degree(C.kind[a], p[a]);
+            C.dim[a] = kind_dim(C.kind[a], p[a], nel[a]);
+            C.off[a] = kind_offset(C.kind[a]);
+            n *= C.dim[a];
+        }
+        C.base = off;
+        off += n;
+    }
+    S.total = off;
+}
+
+// Visit every quadrature point of the element slab at z-element ez: for each
+// point, its parametric position, weight (without det J) and element indices.
+template <class F>
+void for_slab_points(const Space& S, int ez, F&& f) {
+    const int qx = S.ax[0].q, qy = S.ax[1].q, qz = S.ax[2].q;
+    for (int kz = 0; kz < qz; ++kz)
+        for (int ey = 0; ey < S.nel[1]; ++ey)
+            for (int ky = 0; ky < qy; ++ky)
+                for (int ex = 0; ex < S.nel[0]; ++ex)
+                    for (int kx = 0; kx < qx; ++kx) {
+                        const double xh[3] = {(ex + S.ax[0].x[kx]) / S.nel[0], (ey + S.ax[1].x[ky]) / S.nel[1],
+                                              (ez + S.ax[2].x[kz]) / S.nel[2]};
+                        const double w = S.ax[0].w[kx] / S.nel[0] * S.ax[1].w[ky] / S.nel[1] * S.ax[2].w[kz] / S.nel[2];
+                        const int e[3] = {ex, ey, ez}, k[3] = {kx, ky, kz};
+                        f(xh, w, e, k);
+                    }
+}
+
+// Visit the basis functions of component C that live on element e at point k:
+// g(stored index, value).
+template <class G>
+void for_local(const Space& S, const Comp& C, const int e[3], const int k[3], G&& g) {
+    const double* b[3];
+    for (int a = 0; a < 3; ++a)
+        b[a] = &S.bval[a][C.kind[a]][((size_t)e[a] * S.ax[a].q + k[a]) * (C.deg[a] + 1)];
+    for (int rz = 0; rz <= C.deg[2]; ++rz) {
+        const int iz = e[2] + rz + C.off[2];
+        if (iz < 0 || iz >= C.dim[2]) continue;
+        for (int ry = 0; ry <= C.deg[1]; ++ry) {
+            const int iy = e[1] + ry + C.off[1];
+            if (iy < 0 || iy >= C.dim[1]) continue;
+            const double byz = b[1][ry] * b[2][rz];
+            for (int rx = 0; rx <= C.deg[0]; ++rx) {
+                const int ix = e[0] + rx + C.off[0];
+                if (ix < 0 || ix >= C.dim[0]) continue;
+                g(C.base + ix + (long long)C.dim[0] * (iy + (long long)C.dim[1] * iz), b[0][rx] * byz);
+            }
+        }
+    }
+}
+
+// y = M_1 x (matrix-free, point by point).
+void mass_apply(const Space& S, const std::vector<double>& x, std::vector<double>& y) {
+    std::fill(y.begin(), y.end(), 0.0);
+    for (int ez = 0; ez < S.nel[2]; ++ez)
+        for_slab_points(S, ez, [&](const double* xh, double w, const int* e, const int* k) {
+            double X[3], J[9];
+            geometry_eval(S.geom, S.amp, xh, X, J);
+            const double s = w / det3(J);
+            double u[3];
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for_local(S, S.c[c], e, k, [&](long long i, double v) { acc += x[i] * v; });
+                u[c] = acc;
+            }
+            double g[3];
+            for (int i = 0; i < 3; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < 3; ++j)
+                    acc += (J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j]) * u[j];
+                g[i] = s * acc;
+            }
+            for (int c = 0; c < 3; ++c) for_local(S, S.c[c], e, k, [&](long long i, double v) { y[i] += g[c] * v; });
+        });
+}
+
+// The identity-map mass: per component the Kronecker product of the 1D masses
+// of its kinds; its inverse by banded sweeps along x, y and z.
+struct KronMass {
+    BandLU f[3][3];  // [component][axis]
+};
+
+bool build_kron(const Space& S, KronMass& K) {
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a) {
+            const Comp& C = S.c[c];
+            const int n = C.dim[a], d = C.deg[a];
+            std::vector<double> M((size_t)n * n, 0.0);
+            for (int e = 0; e < S.nel[a]; ++e) {
+                const std::vector<double> Me = element_mass(C.kind[a], S.p[a], S.nel[a], e);
+                for (int r = 0; r <= d; ++r)
+                    for (int t = 0; t <= d; ++t) {
+                        const int i = e + r + C.off[a], j = e + t + C.off[a];
+                        if (i >= 0 && i < n && j >= 0 && j < n) M[(size_t)i * n + j] += Me[r * (d + 1) + t];
+                    }
+            }
+            if (!band_lu(M, n, d, d, K.f[c][a])) return false;
+        }
+    return true;
+}
+
+void band_solve(const BandLU& F, double* v, long long stride) {
+    const int n = F.n;
+    for (int m = 0; m < n; ++m) {
+        double u = v[m * stride];
+        for (int k = 1; k <= F.kl && k <= m; ++k) u -= F.L[m * F.kl + k - 1] * v[(m - k) * stride];
+        v[m * stride] = u;
+    }
+    for (int m = n - 1; m >= 0; --m) {
+        double u = v[m * stride] * F.dinv[m];
+        for (int k = 1; k <= F.ku && m + k < n; ++k) u -= F.U[m * F.ku + k - 1] * v[(m + k) * stride];
+        v[m * stride] = u;
+    }
+}
+
+void kron_solve(const Space& S, const KronMass& K, std::vector<double>& v) {
+    for (int c = 0; c < 3; ++c) {
+        const Comp& C = S.c[c];
+        const long long nx = C.dim[0], ny = C.dim[1], nz = C.dim[2];
+        double* base = v.data() + C.base;
+        for (long long k = 0; k < nz; ++k)
+            for (long long j = 0; j < ny; ++j) band_solve(K.f[c][0], base + nx * (j + ny * k), 1);
+        for (long long k = 0; k < nz; ++k)
+            for (long long i = 0; i < nx; ++i) band_solve(K.f[c][1], base + i + nx * ny * k, nx);
+        for (long long j = 0; j < ny; ++j)
+            for (long long i = 0; i < nx; ++i) band_solve(K.f[c][2], base + i + nx * j, nx * ny);
+    }
+}
+
+double dot(const std::vector<double>& a, const std::vector<double>& b) {
+    double s = 0.0;
+    for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+    return s;
+}
+
+}  // namespace
+
+int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int field, project_fn fn, void* user,
+                     double* out, double rtol, int maxit, int* iters) {
+    Space S;
+    build_space(S, p, nel, geom, amp, field);
+    const long long N = S.total;
+    // right-hand side, one callback per slab of elements along z
+    std::vector<double> r(N, 0.0), X3, V3;
+    for (int ez = 0; ez < S.nel[2]; ++ez) {
+        X3.clear();
+        for_slab_points(S, ez, [&](const double* xh, double, const int*, const int*) {
+            double X[3], J[9];
+            geometry_eval(S.geom, S.amp, xh, X, J);
+            X3.insert(X3.end(), X, X + 3);
+        });
+        const long long n = (long long)X3.size() / 3;
+        V3.assign(3 * n, 0.0);
+        fn(n, X3.data(), V3.data(), user);
+        long long pt = 0;
+        bool finite = true;
+        for_slab_points(S, ez, [&](const double* xh, double w, const int* e, const int* k) {
+            double X[3], J[9];
+            geometry_eval(S.geom, S.amp, xh, X, J);
+            const double* V = &V3[3 * pt++];
+            for (int c = 0; c < 3; ++c) {
+                if (!std::isfinite(V[c])) finite = false;
+                const double jtv = w * (J[c] * V[0] + J[3 + c] * V[1] + J[6 + c] * V[2]);  // w (J^T V)_c
+                for_local(S, S.c[c], e, k, [&](long long i, double v) { r[i] += jtv * v; });
+            }
+        });
+        if (!finite) return SMX_ENONFINITE;
+    }
+    KronMass K;
+    if (!build_kron(S, K)) return SMX_ESINGULAR;
+    // preconditioned conjugate gradients from x = P^{-1} r
+    std::vector<double> x = r, res(N), z(N), d(N), Ad(N);
+    kron_solve(S, K, x);
+    mass_apply(S, x, Ad);
+    for (long long i = 0; i < N; ++i) res[i] = r[i] - Ad[i];
+    const double rnorm0 = std::sqrt(dot(r, r));
+    int it = 0;
+    if (rnorm0 > 0.0 && std::sqrt(dot(res, res)) > rtol * rnorm0) {
+        z = res;
+        kron_solve(S, K, z);
+        d = z;
+        double rz = dot(res, z);
+        for (it = 1; it <= maxit; ++it) {
+            mass_apply(S, d, Ad);
+            const double alpha = rz / dot(d, Ad);
+            for (long long i = 0; i < N; ++i) {
+                x[i] += alpha * d[i];
+                res[i] -= alpha * Ad[i];
+            }
+            if (std::sqrt(dot(res, res)) <= rtol * rnorm0) break;
+            z = res;
+            kron_solve(S, K, z);
+            const double rz1 = dot(res, z);
+            const double beta = rz1 / rz;
+            rz = rz1;
+            for (long long i = 0; i < N; ++i) d[i] = z[i] + beta * d[i];
+        }
+        if (it > maxit) return SMX_ESINGULAR;
+    }
+    if (iters) *iters = it;
+    std::copy(x.begin(), x.end(), out);
+    return SMX_OK;
+}
+
+}  // namespace smx

@@ -2,6 +2,8 @@
 // their banded LU, element masses.  See setup.h for the conventions.
 #include "setup.h"
 
+#include "smx.h"
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -202,6 +204,27 @@ std::vector<double> element_mass(int kind, int p, int nel, int e) {
             for (int b = 0; b < m; ++b) Me[a * m + b] += w * v[a] * v[b];
     }
     return Me;
+}
+
+// Map F and its Jacobian J (row-major, J[3 i + j] = dF_i / dxhat_j) at a parametric point.
+void geometry_eval(int geom, double a, const double xh[3], double X[3], double J[9]) {
+    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int i = 0; i < 3; ++i) X[i] = xh[i];
+    if (geom == SMX_GEOM_SINE_BUMP) {
+        const double pi = 3.14159265358979323846;
+        const double sx = std::sin(pi * xh[0]), sy = std::sin(pi * xh[1]), sz = std::sin(pi * xh[2]);
+        const double cx = std::cos(pi * xh[0]), cy = std::cos(pi * xh[1]), cz = std::cos(pi * xh[2]);
+        const double S = sx * sy * sz;
+        const double g[3] = {pi * cx * sy * sz, pi * sx * cy * sz, pi * sx * sy * cz};
+        for (int i = 0; i < 3; ++i) {
+            X[i] += a * S;
+            for (int j = 0; j < 3; ++j) J[3 * i + j] += a * g[j];
+        }
+    }
+}
+
+double det3(const double J[9]) {
+    return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
 }
 
 // Round an FP32 value to BF16, nearest even (IEEE rounding on the 16 dropped bits).

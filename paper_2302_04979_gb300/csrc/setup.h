@@ -48,6 +48,21 @@ bool band_lu(const std::vector<double>& A, int n, int kl, int ku, BandLU& out);
 // Rebuild the dense matrix L * U (row-major) from a factor.
 std::vector<double> band_lu_dense(const BandLU& f);
 
+// Geometry map F (SMX_GEOM_IDENTITY, or SMX_GEOM_SINE_BUMP with amplitude a)
+// and its Jacobian, J[3 i + j] = dF_i / dxhat_j, at a parametric point; det3 of J.
+void geometry_eval(int geom, double a, const double xh[3], double X[3], double J[9]);
+double det3(const double J[9]);
+
+// L2 projection of a physical 2-form onto X~^2 (field SMX_FIELD_D) or X^2_{h,0}
+// (SMX_FIELD_B) (project.cpp): fn(n, xyz, out) fills out[3 i + c] with the
+// vector proxy at the physical points xyz[3 i ..]; out (host, the field's
+// length) receives the coefficients.  Preconditioned CG to ||r|| <= rtol ||b||.
+// Returns SMX_OK, SMX_ENONFINITE (fn gave a non-finite value) or
+// SMX_ESINGULAR (no convergence in maxit iterations).
+typedef void (*project_fn)(int64_t n, const double* xyz, double* out, void* user);
+int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int field, project_fn fn, void* user,
+                     double* out, double rtol, int maxit, int* iters);
+
 // Element mass matrix of one kind on element e: (d+1) x (d+1), row-major,
 // int_e phi_i phi_j with q = p+1 Gauss points.
 std::vector<double> element_mass(int kind, int p, int nel, int e);

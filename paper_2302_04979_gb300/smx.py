@@ -27,6 +27,9 @@ MATERIAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.POINTER(ctypes.c_dou
                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
+FIELD_FN = MATERIAL_FN  # smx_field_fn: the same C signature, 3 values per point
+
+
 class Material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("value", ctypes.c_double), ("blocks", ctypes.c_int * 3),
                 ("block_values", ctypes.POINTER(ctypes.c_double)), ("fn", MATERIAL_FN),
@@ -58,6 +61,7 @@ _SIGS = {
     "smx_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "smx_set_mode_kernel": [ctypes.c_void_p, ctypes.c_int],
     "smx_mode_kernel": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)],
+    "smx_project": [ctypes.c_void_p, ctypes.c_int, FIELD_FN, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
     "smx_device_status": [ctypes.c_void_p],
     "smx_hodge_star_mixed": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_receivers_set": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
@@ -237,6 +241,25 @@ class Context:
         of the two -- tensor cores for a separable star, recurrences for the pairing sweeps."""
         _check(_lib().smx_set_mode_kernel(self.h, {"tensor": MODE_TENSOR, "simt": MODE_SIMT, "auto": MODE_AUTO}[which]),
                "smx_set_mode_kernel")
+
+    def project(self, field, V):
+        """L2 projection (host, FP64) of a physical 2-form with vector proxy V(x, y, z) -> (3, n)
+        onto the coefficients of FIELD_D (X~^2: d or jhat) or FIELD_B (X^2_{h,0}: b); numpy array."""
+        n = self.N_e if field == FIELD_D else self.N_h
+        out = np.empty(n, dtype=np.float64)
+
+        def cb(m, xyz, res, _user):
+            pts = np.ctypeslib.as_array(xyz, shape=(m, 3))
+            r = np.ctypeslib.as_array(res, shape=(m, 3))
+            try:
+                r[:] = np.asarray(V(pts[:, 0], pts[:, 1], pts[:, 2]), dtype=np.float64).T
+            except Exception:  # reported as SMX_ENONFINITE by the library
+                r[:] = np.nan
+
+        fn = FIELD_FN(cb)
+        _check(_lib().smx_project(self.h, field, fn, None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "smx_project")
+        return out
 
     def mode_kernel(self):
         """The line-operator kernel the Hodge stars run: "tensor" or "simt"."""
