@@ -88,8 +88,9 @@ def test_mixed_against_oracle(name, kernel):
 def test_mixed_hodge_star_against_oracle(name, kernel):
     """One mixed-precision Hodge star (K_1^{-1} M~ d and K~_1^{-1} M b) against the oracle's FP64 one.
 
-    Every stage rounds its data to FP32 once (the operators carry FP64 accuracy in
-    their split terms), so one star stays within a few FP32 roundings: 2e-6."""
+    Every stage rounds its data to FP32 once (the CUDA-core operators carry FP64 accuracy in
+    their (hi, lo) terms; the tensor-core digit products are exact on 31-bit fixed-point lines
+    and round once), so one star stays within a few FP32 roundings: 2e-6."""
     import torch
     from paper_2302_04979_gb300 import smx
     case = CASES[name]
@@ -109,7 +110,8 @@ def test_mixed_hodge_star_against_oracle(name, kernel):
 
 
 def test_mixed_kernels_agree_at_64cube():
-    """The benchmark workload's mixed Hodge stars: tensor-core and FP32 CUDA-core kernels agree to FP32 rounding."""
+    """The benchmark workload's mixed Hodge stars: tensor-core (four-digit) and FP32 CUDA-core kernels
+    agree to FP32 rounding."""
     import torch
     from paper_2302_04979_gb300 import smx
     eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
