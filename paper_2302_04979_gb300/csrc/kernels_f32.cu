@@ -372,7 +372,7 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, const TIN* __r
     if (l0 >= nlines) return;
     const int nl = min(kSolveLines, nlines - l0);
     constexpr int W = 2 * D + 1;
-    const int Dp = MASS ? D : 0;
+    constexpr int Dp = MASS ? D : 0;
     float2* fL = reinterpret_cast<float2*>(sm);
     float2* fU = fL + n * KL;
     float2* fD = fU + n * KL;
@@ -394,7 +394,7 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, const TIN* __r
         for (int t = tid; t < n * W; t += nt) cp_async8f(fM + t, A.mass[c] + t);
     const int sL = axis == 0 ? ldin : 1;
     const int sM = axis == 0 ? 1 : kSolveLines;
-    if (MASS) {
+    if constexpr (Dp > 0) {  // zero pads (no pads, and no loop, without the mass)
         for (int t = tid; t < kSolveLines * Dp; t += nt) {
             const int line = t / Dp, q = t - line * Dp;
             Sin[line * sL + q * sM] = 0.0f;
