@@ -190,8 +190,6 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "line_operators": "auto: separable star on the tensor cores (exact BF16 digit products), "
-                                 "pairing sweeps as FP64 banded recurrences",
            "config": workload_config(ne, nh),
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -405,8 +403,9 @@ def run_ours(args, rank, world, local):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "line_operators": "auto: separable star on the tensor cores (exact BF16 digit products), "
-                                 "pairing sweeps as FP64 banded recurrences",
+               "line_operators": "auto: at this size the separable star of B on the tensor cores (exact BF16 "
+                                 "digit products), the sweeps after the block Hodge apply of D as FP64 banded "
+                                 "recurrences",
                "config": workload_config(ne, nh), "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
                "roofline": roof, "kernels": kern,
                "steady_state": {"value": reduce_sum(dof * args.steps, world) / (steady_ms * 1e-3),
