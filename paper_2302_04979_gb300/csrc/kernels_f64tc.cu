@@ -1,4 +1,9 @@
-// FP64 mode products on the 5th-generation tensor cores by exact digit slicing.
+// Mode products on the 5th-generation tensor cores by exact digit slicing: the
+// FP64 step's line operators (seven digits) and the mixed step's tensor-core
+// option (four digits).  The description below is for seven digits; the
+// four-digit instantiation reads FP64 or FP32 lines, forms 31-bit fixed-point
+// images (|X| < 2^31), accumulates levels 0..3 (10 digit products) and rounds
+// the result once to FP32 (optionally also writing it widened to FP64).
 //
 // Along one axis every line x of a component becomes B x, with B the dense
 // n x n line operator -- A^{-1} (pairing sweep, Eq. kroninverse) or A^{-1} M
@@ -42,7 +47,7 @@
 // rows rounded up to 8 (R = r8): an MMA still reads 128 rows, and rows
 // r8..127 are whatever follows in shared memory -- they only feed
 // tensor-memory lanes r8..127, which are never used.
-//   1. warp 0 allocates 512 tensor-memory columns; the operator digits are
+//   1. warp 0 allocates the ring's tensor memory; the operator digits are
 //      copied with cp.async (one contiguous run: the table has this layout);
 //   2. the tile's FP64 values are loaded as bit patterns, the largest
 //      exponent of each line is found with shared-memory atomics, and every
@@ -53,8 +58,9 @@
 //   3. one thread of warp 3 issues the MMAs level by level into the ring and
 //      commits each level to that buffer's "full" mbarrier; before reusing a
 //      buffer it waits on the buffer's "drained" mbarrier;
-//   4. meanwhile the warps of lane quarters 0..2 (operator rows 0..95; 4
-//      warps per quarter, NL / 4 columns each) take each level as it
+//   4. meanwhile the warps of the lane quarters that hold operator rows (at
+//      most quarters 0..2; THREADS / 128 warps per quarter, each owning an
+//      equal share of the NL columns) take each level as it
 //      completes, fold it into their Horner accumulators and release the
 //      buffer; after level 6 they round and write the outputs: directly for
 //      the x sweep (consecutive rows are consecutive addresses), through
