@@ -1,11 +1,13 @@
 """Thin Python binding of the C ABI in include/smx.h (argument marshalling only).
 
-Every computation runs in libsmx.so's CUDA kernels; this module converts
-torch tensors to device pointers and checks status codes.  If the library is
-missing it raises: there is no CPU fallback.
+Every computation runs in libsmx.so: the step's operations in its CUDA
+kernels, the setup (tables, and the L2 projection of initial data) in its
+host C++.  This module converts torch tensors to device pointers and checks
+status codes.  If the library is missing it raises: there is no CPU fallback.
 
 Names follow the C ABI: ``create``, ``sizes``, ``curl_primal``, ``curl_dual``,
-``hodge_apply``, ``pairing_solve``, ``hodge_star``, ``step``, ``energy``, ``cfl``.
+``hodge_apply``, ``pairing_solve``, ``hodge_star``, ``step``, ``energy``, ``cfl``,
+``project``, the reverse-mode calls and the batch.
 """
 import ctypes
 import os
