@@ -22,19 +22,27 @@ CASES = [
     ("identity_p2", dict(p=2, nel=(3, 4, 2))),
     ("identity_aniso", dict(p=(3, 2, 4), nel=(2, 3, 2))),
     ("curved_p3", dict(p=3, nel=(3, 2, 3), geometry="sine_bump")),
+    ("one_element_axis", dict(p=2, nel=(1, 3, 1))),
+    ("high_degree", dict(p=6, nel=(1, 2, 1))),
 ]
 
 
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("field", ["D", "B"])
 def test_projection_matches_oracle(name, case, field):
+    """Both sides solve the same Galerkin system to a relative residual of 1e-14, so their mass
+    residuals agree to round-off; the coefficients agree to that times the condition number of the
+    2-form mass, which grows with the degree (about 1e2 at p <= 4, 1e5 at p = 6)."""
     geom = hodge.SineBumpMap(0.05) if case.get("geometry") == "sine_bump" else hodge.IdentityMap()
     S = mx.Scheme2(case["p"], case["nel"], geometry=geom)
     ctx = smx.Context(case["p"], case["nel"], geometry=case.get("geometry", "identity"), amplitude=0.05)
     got = ctx.project(smx.FIELD_D if field == "D" else smx.FIELD_B, _field)
     want = S.project_2form(field, _field)
     assert got.shape == want.shape
-    assert rel_l2(got, want) < 1e-11
+    M1 = hodge.HodgeMass(field, case["p"], case["nel"], geom, 1.0)
+    assert rel_l2(M1.apply(got), M1.apply(want)) < 1e-13
+    tol = 1e-8 if int(np.max(case["p"])) >= 6 else 1e-11
+    assert rel_l2(got, want) < tol
 
 
 def test_projection_reproduces_a_discrete_field():
