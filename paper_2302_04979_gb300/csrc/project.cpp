@@ -15,6 +15,7 @@
 #include <cmath>
 #include <vector>
 
+#include "internal.h"
 #include "setup.h"
 #include "smx.h"
 
@@ -119,29 +120,109 @@ void for_local(const Space& S, const Comp& C, const int e[3], const int k[3], G&
     }
 }
 
-// y = M_1 x (matrix-free, point by point).
+// y = M_1 x, matrix-free and element by element with sum factorisation: each
+// component's local coefficients are interpolated to the element's q^3 points
+// by three 1D contractions, multiplied by w J^T J / det J there, and
+// integrated back by the transposed contractions.
 void mass_apply(const Space& S, const std::vector<double>& x, std::vector<double>& y) {
     std::fill(y.begin(), y.end(), 0.0);
+    const int qx = S.ax[0].q, qy = S.ax[1].q, qz = S.ax[2].q, nq = qx * qy * qz;
+    constexpr int R = kRMax;  // largest local count per axis (p + 1)
+    std::vector<double> U(3 * (size_t)nq), loc((size_t)R * R * R), t1((size_t)R * R * 16), t2((size_t)R * 16 * 16);
     for (int ez = 0; ez < S.nel[2]; ++ez)
-        for_slab_points(S, ez, [&](const double* xh, double w, const int* e, const int* k) {
-            double X[3], J[9];
-            geometry_eval(S.geom, S.amp, xh, X, J);
-            const double s = w / det3(J);
-            double u[3];
-            for (int c = 0; c < 3; ++c) {
-                double acc = 0.0;
-                for_local(S, S.c[c], e, k, [&](long long i, double v) { acc += x[i] * v; });
-                u[c] = acc;
+        for (int ey = 0; ey < S.nel[1]; ++ey)
+            for (int ex = 0; ex < S.nel[0]; ++ex) {
+                const int e[3] = {ex, ey, ez};
+                const double* bas[3][3];  // [component][axis]: (q x (deg + 1)) values on this element
+                for (int c = 0; c < 3; ++c)
+                    for (int ax = 0; ax < 3; ++ax)
+                        bas[c][ax] = &S.bval[ax][S.c[c].kind[ax]][(size_t)e[ax] * S.ax[ax].q * (S.c[c].deg[ax] + 1)];
+                // interpolate: loc[rz][ry][rx] -> U_c[kz][ky][kx]
+                for (int c = 0; c < 3; ++c) {
+                    const Comp& C = S.c[c];
+                    const int n0 = C.deg[0] + 1, n1 = C.deg[1] + 1, n2 = C.deg[2] + 1;
+                    for (int rz = 0; rz < n2; ++rz)
+                        for (int ry = 0; ry < n1; ++ry)
+                            for (int rx = 0; rx < n0; ++rx) {
+                                const int ix = ex + rx + C.off[0], iy = ey + ry + C.off[1], iz = ez + rz + C.off[2];
+                                const bool in = ix >= 0 && ix < C.dim[0] && iy >= 0 && iy < C.dim[1] && iz >= 0 &&
+                                                iz < C.dim[2];
+                                loc[(rz * R + ry) * R + rx] =
+                                    in ? x[C.base + ix + (long long)C.dim[0] * (iy + (long long)C.dim[1] * iz)] : 0.0;
+                            }
+                    for (int rz = 0; rz < n2; ++rz)
+                        for (int ry = 0; ry < n1; ++ry)
+                            for (int kx = 0; kx < qx; ++kx) {
+                                double acc = 0.0;
+                                for (int rx = 0; rx < n0; ++rx) acc += bas[c][0][kx * n0 + rx] * loc[(rz * R + ry) * R + rx];
+                                t1[(rz * R + ry) * 16 + kx] = acc;
+                            }
+                    for (int rz = 0; rz < n2; ++rz)
+                        for (int ky = 0; ky < qy; ++ky)
+                            for (int kx = 0; kx < qx; ++kx) {
+                                double acc = 0.0;
+                                for (int ry = 0; ry < n1; ++ry) acc += bas[c][1][ky * n1 + ry] * t1[(rz * R + ry) * 16 + kx];
+                                t2[(rz * 16 + ky) * 16 + kx] = acc;
+                            }
+                    for (int kz = 0; kz < qz; ++kz)
+                        for (int ky = 0; ky < qy; ++ky)
+                            for (int kx = 0; kx < qx; ++kx) {
+                                double acc = 0.0;
+                                for (int rz = 0; rz < n2; ++rz) acc += bas[c][2][kz * n2 + rz] * t2[(rz * 16 + ky) * 16 + kx];
+                                U[(size_t)c * nq + (kz * qy + ky) * qx + kx] = acc;
+                            }
+                }
+                // the metric at every point of the element
+                for (int kz = 0; kz < qz; ++kz)
+                    for (int ky = 0; ky < qy; ++ky)
+                        for (int kx = 0; kx < qx; ++kx) {
+                            const double xh[3] = {(ex + S.ax[0].x[kx]) / S.nel[0], (ey + S.ax[1].x[ky]) / S.nel[1],
+                                                  (ez + S.ax[2].x[kz]) / S.nel[2]};
+                            const double w = S.ax[0].w[kx] / S.nel[0] * S.ax[1].w[ky] / S.nel[1] * S.ax[2].w[kz] /
+                                             S.nel[2];
+                            double X[3], J[9];
+                            geometry_eval(S.geom, S.amp, xh, X, J);
+                            const double sc = w / det3(J);
+                            const size_t qi = (size_t)(kz * qy + ky) * qx + kx;
+                            const double u[3] = {U[qi], U[nq + qi], U[2 * (size_t)nq + qi]};
+                            for (int i = 0; i < 3; ++i) {
+                                double acc = 0.0;
+                                for (int j = 0; j < 3; ++j)
+                                    acc += (J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j]) * u[j];
+                                U[(size_t)i * nq + qi] = sc * acc;  // u was copied: overwrite in place
+                            }
+                        }
+                // integrate back: U_c[kz][ky][kx] -> local coefficients, scattered into y
+                for (int c = 0; c < 3; ++c) {
+                    const Comp& C = S.c[c];
+                    const int n0 = C.deg[0] + 1, n1 = C.deg[1] + 1, n2 = C.deg[2] + 1;
+                    for (int rz = 0; rz < n2; ++rz)
+                        for (int ky = 0; ky < qy; ++ky)
+                            for (int kx = 0; kx < qx; ++kx) {
+                                double acc = 0.0;
+                                for (int kz = 0; kz < qz; ++kz)
+                                    acc += bas[c][2][kz * n2 + rz] * U[(size_t)c * nq + (kz * qy + ky) * qx + kx];
+                                t2[(rz * 16 + ky) * 16 + kx] = acc;
+                            }
+                    for (int rz = 0; rz < n2; ++rz)
+                        for (int ry = 0; ry < n1; ++ry)
+                            for (int kx = 0; kx < qx; ++kx) {
+                                double acc = 0.0;
+                                for (int ky = 0; ky < qy; ++ky) acc += bas[c][1][ky * n1 + ry] * t2[(rz * 16 + ky) * 16 + kx];
+                                t1[(rz * R + ry) * 16 + kx] = acc;
+                            }
+                    for (int rz = 0; rz < n2; ++rz)
+                        for (int ry = 0; ry < n1; ++ry)
+                            for (int rx = 0; rx < n0; ++rx) {
+                                const int ix = ex + rx + C.off[0], iy = ey + ry + C.off[1], iz = ez + rz + C.off[2];
+                                if (ix < 0 || ix >= C.dim[0] || iy < 0 || iy >= C.dim[1] || iz < 0 || iz >= C.dim[2])
+                                    continue;
+                                double acc = 0.0;
+                                for (int kx = 0; kx < qx; ++kx) acc += bas[c][0][kx * n0 + rx] * t1[(rz * R + ry) * 16 + kx];
+                                y[C.base + ix + (long long)C.dim[0] * (iy + (long long)C.dim[1] * iz)] += acc;
+                            }
+                }
             }
-            double g[3];
-            for (int i = 0; i < 3; ++i) {
-                double acc = 0.0;
-                for (int j = 0; j < 3; ++j)
-                    acc += (J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j]) * u[j];
-                g[i] = s * acc;
-            }
-            for (int c = 0; c < 3; ++c) for_local(S, S.c[c], e, k, [&](long long i, double v) { y[i] += g[c] * v; });
-        });
 }
 
 // The identity-map mass: per component the Kronecker product of the 1D masses
