@@ -97,26 +97,48 @@ void for_slab_points(const Space& S, int ez, F&& f) {
                     }
 }
 
-// Visit the basis functions of component C that live on element e at point k:
-// g(stored index, value).
-template <class G>
-void for_local(const Space& S, const Comp& C, const int e[3], const int k[3], G&& g) {
-    const double* b[3];
-    for (int a = 0; a < 3; ++a)
-        b[a] = &S.bval[a][C.kind[a]][((size_t)e[a] * S.ax[a].q + k[a]) * (C.deg[a] + 1)];
-    for (int rz = 0; rz <= C.deg[2]; ++rz) {
-        const int iz = e[2] + rz + C.off[2];
-        if (iz < 0 || iz >= C.dim[2]) continue;
-        for (int ry = 0; ry <= C.deg[1]; ++ry) {
-            const int iy = e[1] + ry + C.off[1];
-            if (iy < 0 || iy >= C.dim[1]) continue;
-            const double byz = b[1][ry] * b[2][rz];
-            for (int rx = 0; rx <= C.deg[0]; ++rx) {
-                const int ix = e[0] + rx + C.off[0];
-                if (ix < 0 || ix >= C.dim[0]) continue;
-                g(C.base + ix + (long long)C.dim[0] * (iy + (long long)C.dim[1] * iz), b[0][rx] * byz);
-            }
-        }
+// The element's basis values per component and axis: (q x (deg + 1)) arrays.
+void element_basis(const Space& S, const int e[3], const double* bas[3][3]) {
+    for (int c = 0; c < 3; ++c)
+        for (int ax = 0; ax < 3; ++ax)
+            bas[c][ax] = &S.bval[ax][S.c[c].kind[ax]][(size_t)e[ax] * S.ax[ax].q * (S.c[c].deg[ax] + 1)];
+}
+
+// y += the integrals of U_c (values times weights at the element's q^3 points,
+// component-major, x fastest) against the element's basis functions, by three
+// 1D contractions (t1, t2: scratch of kRMax * 16 * 16 doubles).
+void integrate_element(const Space& S, const int e[3], const double* const bas[3][3], const double* U,
+                       std::vector<double>& y, double* t1, double* t2) {
+    constexpr int R = kRMax;
+    const int qx = S.ax[0].q, qy = S.ax[1].q, qz = S.ax[2].q, nq = qx * qy * qz;
+    const int ex = e[0], ey = e[1], ez = e[2];
+    for (int c = 0; c < 3; ++c) {
+        const Comp& C = S.c[c];
+        const int n0 = C.deg[0] + 1, n1 = C.deg[1] + 1, n2 = C.deg[2] + 1;
+        for (int rz = 0; rz < n2; ++rz)
+            for (int ky = 0; ky < qy; ++ky)
+                for (int kx = 0; kx < qx; ++kx) {
+                    double acc = 0.0;
+                    for (int kz = 0; kz < qz; ++kz)
+                        acc += bas[c][2][kz * n2 + rz] * U[(size_t)c * nq + (kz * qy + ky) * qx + kx];
+                    t2[(rz * 16 + ky) * 16 + kx] = acc;
+                }
+        for (int rz = 0; rz < n2; ++rz)
+            for (int ry = 0; ry < n1; ++ry)
+                for (int kx = 0; kx < qx; ++kx) {
+                    double acc = 0.0;
+                    for (int ky = 0; ky < qy; ++ky) acc += bas[c][1][ky * n1 + ry] * t2[(rz * 16 + ky) * 16 + kx];
+                    t1[(rz * R + ry) * 16 + kx] = acc;
+                }
+        for (int rz = 0; rz < n2; ++rz)
+            for (int ry = 0; ry < n1; ++ry)
+                for (int rx = 0; rx < n0; ++rx) {
+                    const int ix = ex + rx + C.off[0], iy = ey + ry + C.off[1], iz = ez + rz + C.off[2];
+                    if (ix < 0 || ix >= C.dim[0] || iy < 0 || iy >= C.dim[1] || iz < 0 || iz >= C.dim[2]) continue;
+                    double acc = 0.0;
+                    for (int kx = 0; kx < qx; ++kx) acc += bas[c][0][kx * n0 + rx] * t1[(rz * R + ry) * 16 + kx];
+                    y[C.base + ix + (long long)C.dim[0] * (iy + (long long)C.dim[1] * iz)] += acc;
+                }
     }
 }
 
@@ -133,10 +155,8 @@ void mass_apply(const Space& S, const std::vector<double>& x, std::vector<double
         for (int ey = 0; ey < S.nel[1]; ++ey)
             for (int ex = 0; ex < S.nel[0]; ++ex) {
                 const int e[3] = {ex, ey, ez};
-                const double* bas[3][3];  // [component][axis]: (q x (deg + 1)) values on this element
-                for (int c = 0; c < 3; ++c)
-                    for (int ax = 0; ax < 3; ++ax)
-                        bas[c][ax] = &S.bval[ax][S.c[c].kind[ax]][(size_t)e[ax] * S.ax[ax].q * (S.c[c].deg[ax] + 1)];
+                const double* bas[3][3];  // [component][axis]
+                element_basis(S, e, bas);
                 // interpolate: loc[rz][ry][rx] -> U_c[kz][ky][kx]
                 for (int c = 0; c < 3; ++c) {
                     const Comp& C = S.c[c];
@@ -192,36 +212,7 @@ void mass_apply(const Space& S, const std::vector<double>& x, std::vector<double
                                 U[(size_t)i * nq + qi] = sc * acc;  // u was copied: overwrite in place
                             }
                         }
-                // integrate back: U_c[kz][ky][kx] -> local coefficients, scattered into y
-                for (int c = 0; c < 3; ++c) {
-                    const Comp& C = S.c[c];
-                    const int n0 = C.deg[0] + 1, n1 = C.deg[1] + 1, n2 = C.deg[2] + 1;
-                    for (int rz = 0; rz < n2; ++rz)
-                        for (int ky = 0; ky < qy; ++ky)
-                            for (int kx = 0; kx < qx; ++kx) {
-                                double acc = 0.0;
-                                for (int kz = 0; kz < qz; ++kz)
-                                    acc += bas[c][2][kz * n2 + rz] * U[(size_t)c * nq + (kz * qy + ky) * qx + kx];
-                                t2[(rz * 16 + ky) * 16 + kx] = acc;
-                            }
-                    for (int rz = 0; rz < n2; ++rz)
-                        for (int ry = 0; ry < n1; ++ry)
-                            for (int kx = 0; kx < qx; ++kx) {
-                                double acc = 0.0;
-                                for (int ky = 0; ky < qy; ++ky) acc += bas[c][1][ky * n1 + ry] * t2[(rz * 16 + ky) * 16 + kx];
-                                t1[(rz * R + ry) * 16 + kx] = acc;
-                            }
-                    for (int rz = 0; rz < n2; ++rz)
-                        for (int ry = 0; ry < n1; ++ry)
-                            for (int rx = 0; rx < n0; ++rx) {
-                                const int ix = ex + rx + C.off[0], iy = ey + ry + C.off[1], iz = ez + rz + C.off[2];
-                                if (ix < 0 || ix >= C.dim[0] || iy < 0 || iy >= C.dim[1] || iz < 0 || iz >= C.dim[2])
-                                    continue;
-                                double acc = 0.0;
-                                for (int kx = 0; kx < qx; ++kx) acc += bas[c][0][kx * n0 + rx] * t1[(rz * R + ry) * 16 + kx];
-                                y[C.base + ix + (long long)C.dim[0] * (iy + (long long)C.dim[1] * iz)] += acc;
-                            }
-                }
+                integrate_element(S, e, bas, U.data(), y, t1.data(), t2.data());
             }
 }
 
@@ -293,6 +284,8 @@ int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int
     const long long N = S.total;
     // right-hand side, one callback per slab of elements along z
     std::vector<double> r(N, 0.0), X3, V3;
+    std::vector<double> U(3 * (size_t)S.ax[0].q * S.ax[1].q * S.ax[2].q), t1((size_t)kRMax * kRMax * 16),
+        t2((size_t)kRMax * 16 * 16);
     for (int ez = 0; ez < S.nel[2]; ++ez) {
         X3.clear();
         for_slab_points(S, ez, [&](const double* xh, double, const int*, const int*) {
@@ -303,19 +296,33 @@ int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int
         const long long n = (long long)X3.size() / 3;
         V3.assign(3 * n, 0.0);
         fn(n, X3.data(), V3.data(), user);
-        long long pt = 0;
-        bool finite = true;
-        for_slab_points(S, ez, [&](const double* xh, double w, const int* e, const int* k) {
-            double X[3], J[9];
-            geometry_eval(S.geom, S.amp, xh, X, J);
-            const double* V = &V3[3 * pt++];
-            for (int c = 0; c < 3; ++c) {
-                if (!std::isfinite(V[c])) finite = false;
-                const double jtv = w * (J[c] * V[0] + J[3 + c] * V[1] + J[6 + c] * V[2]);  // w (J^T V)_c
-                for_local(S, S.c[c], e, k, [&](long long i, double v) { r[i] += jtv * v; });
+        for (long long i = 0; i < 3 * n; ++i)
+            if (!std::isfinite(V3[i])) return SMX_ENONFINITE;
+        // slab point (ex, kx, ey, ky, kz) sits at ((kz nel_y + ey) q_y + ky) nel_x q_x + ex q_x + kx
+        const int qx = S.ax[0].q, qy = S.ax[1].q, qz = S.ax[2].q, nq = qx * qy * qz;
+        for (int ey = 0; ey < S.nel[1]; ++ey)
+            for (int ex = 0; ex < S.nel[0]; ++ex) {
+                const int e[3] = {ex, ey, ez};
+                for (int kz = 0; kz < qz; ++kz)
+                    for (int ky = 0; ky < qy; ++ky)
+                        for (int kx = 0; kx < qx; ++kx) {
+                            const double xh[3] = {(ex + S.ax[0].x[kx]) / S.nel[0], (ey + S.ax[1].x[ky]) / S.nel[1],
+                                                  (ez + S.ax[2].x[kz]) / S.nel[2]};
+                            const double w = S.ax[0].w[kx] / S.nel[0] * S.ax[1].w[ky] / S.nel[1] * S.ax[2].w[kz] /
+                                             S.nel[2];
+                            double X[3], J[9];
+                            geometry_eval(S.geom, S.amp, xh, X, J);
+                            const long long pt =
+                                (((long long)kz * S.nel[1] + ey) * qy + ky) * ((long long)S.nel[0] * qx) + ex * qx + kx;
+                            const double* V = &V3[3 * pt];
+                            const size_t qi = (size_t)(kz * qy + ky) * qx + kx;
+                            for (int c = 0; c < 3; ++c)  // w (J^T V)_c
+                                U[(size_t)c * nq + qi] = w * (J[c] * V[0] + J[3 + c] * V[1] + J[6 + c] * V[2]);
+                        }
+                const double* bas[3][3];
+                element_basis(S, e, bas);
+                integrate_element(S, e, bas, U.data(), r, t1.data(), t2.data());
             }
-        });
-        if (!finite) return SMX_ENONFINITE;
     }
     KronMass K;
     if (!build_kron(S, K)) return SMX_ESINGULAR;
