@@ -268,9 +268,10 @@ int smx_project(const smx_ctx* ctx, int field, smx_field_fn fn, void* user, doub
  *   13 FP32 block Hodge, 14/15/16 FP32 line passes along x/y/z, 17 casts,
  *   18 FP32 quadrature Hodge, 19 per-block mass derivative (reverse step),
  *   20 receivers and small vector updates,
- *   21/22/23 FP64 dense line operators on the tensor cores along x/y/z.
+ *   21/22/23 FP64 dense line operators on the tensor cores along x/y/z,
+ *   24/25/26 the mixed step's dense line operators on the tensor cores along x/y/z.
  * ms[SMX_NCLASS] receives milliseconds, counts[SMX_NCLASS] launches per class. */
-#define SMX_NCLASS 24
+#define SMX_NCLASS 27
 int smx_launch_count(const smx_ctx* ctx, int64_t* n);
 int smx_set_timing(smx_ctx* ctx, int enable);
 int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);
@@ -307,6 +308,10 @@ int smx_kernel_work(const smx_ctx* ctx, int cls, int field, double* flops, doubl
  *    materials are too large, and the call returns SMX_EINVAL;
  *  - the first call on a device looks up the array's device address (with that
  *    device current); make that first call before any stream capture;
+ *  - the array used is the current device's: the context stream (if not the
+ *    legacy default stream) must belong to the current device, else SMX_EINVAL;
+ *  - a material update (smx_set_material_blocks) takes effect here too: the
+ *    next call re-uploads the context's tables;
  *  - the array is shared by every context and every call on the device and
  *    keeps the last call's contents; a call re-uploads its context's tables
  *    (an asynchronous host-to-device copy on the context stream) when another
@@ -418,8 +423,17 @@ int smx_batch_set_state(smx_batch* batch, int i, double* d, double* b, double* e
 int smx_batch_step(smx_batch* batch, int nsteps);
 
 /* Synchronise; SMX_ETIMEOUT if a grid barrier gave up since the last call
- * (the results of that launch are not valid), else SMX_OK. */
+ * (the results of that launch are not valid), else SMX_OK.  Once a barrier
+ * has given up, every later launch returns at entry without touching the
+ * state until this call clears the status and resets the barrier words. */
 int smx_batch_status(smx_batch* batch);
+
+/* Time limit of each grid-barrier wait of later launches, in seconds (default
+ * 1; 0 to 60).  With 0 every wait that is not already satisfied gives up at
+ * once: the tests use it to run the failure path (SMX_ETIMEOUT from
+ * smx_batch_status, state of that launch invalid) without a hung GPU.
+ * Errors: SMX_EINVAL. */
+int smx_batch_set_wait_limit(smx_batch* batch, double seconds);
 
 /* Autotuner: times `steps` launches for each candidate shape (1, 2, 4, 8
  * line warps per CTA, as shared memory allows) on the contexts' own state

@@ -66,6 +66,10 @@ struct GraphCache {
     long long kernels = 0;  // kernel nodes per replay
 };
 
+// Context ids: the static no-alloc array records which id's tables it holds, so a
+// context whose tables change takes a fresh id and the next no-alloc call re-uploads.
+std::atomic<uint64_t> g_next_uid{1};
+
 uint64_t splitmix64(uint64_t& s) {
     uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -148,6 +152,31 @@ struct smx_ctx {
 namespace {
 
 const int kFieldOfHodge[2] = {SMX_FIELD_B, SMX_FIELD_D};
+
+// Host twin of the device metric rescale: every quadrature point's six metric
+// entries in the blob times ratio[block of its element], and the mixed form's
+// (hi, lo) copy rebuilt from the product.
+void rescale_metric_host(smx_ctx* C, const std::vector<double>& ratio) {
+    const HodgeHost& H = C->hodge[1];
+    const long long Q = H.Qtot;
+    double* G = reinterpret_cast<double*>(C->blob.bytes.data() + H.o_G);
+    float* G32 = C->precision == SMX_MIXED ? reinterpret_cast<float*>(C->blob.bytes.data() + C->o_G32[1]) : nullptr;
+    for (long long i = 0; i < Q; ++i) {
+        const long long qx = i % H.Qn[0], r = i / H.Qn[0], qy = r % H.Qn[1], qz = r / H.Qn[1];
+        const int bx = (int)(qx / H.q[0]) / C->eps_epb[0], by = (int)(qy / H.q[1]) / C->eps_epb[1];
+        const int bz = (int)(qz / H.q[2]) / C->eps_epb[2];
+        const double f = ratio[((size_t)bz * C->eps_nb[1] + by) * C->eps_nb[0] + bx];
+        for (int k = 0; k < 6; ++k) {
+            const double v = f * G[k * Q + i];
+            G[k * Q + i] = v;
+            if (G32) {
+                const float hi = static_cast<float>(v);
+                G32[2 * (k * Q + i)] = hi;
+                G32[2 * (k * Q + i) + 1] = static_cast<float>(v - static_cast<double>(hi));
+            }
+        }
+    }
+}
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
@@ -561,7 +590,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         }
         const bool tc = C->mode_kernel == SMX_MODE_TENSOR;  // AUTO: the CUDA-core kernel (no accumulation bias)
         auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
-            return run(C, 14 + a, 1, [&] {
+            return run(C, (tc ? 24 : 14) + a, 1, [&] {
                 return tc ? launch_mode_digit_f32(C->mdg[h][a], i64, i32, out, o64, C->stream)
                           : launch_mode_f32(C->md32[h][a], i64, i32, out, C->stream);
             });
@@ -724,8 +753,7 @@ int smx_create(const smx_params* P, smx_ctx** out) {
     if (st) return st;
     smx_ctx* C = new (std::nothrow) smx_ctx();
     if (!C) return SMX_ENOMEM;
-    static std::atomic<uint64_t> next_uid{1};
-    C->uid = next_uid.fetch_add(1);
+    C->uid = g_next_uid.fetch_add(1);
     try {
         for (int a = 0; a < 3; ++a) {
             C->p[a] = P->p[a];
@@ -1481,6 +1509,14 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
             *flops = 0.0;
             *bytes = 12.0 * N;
             return SMX_OK;
+        case 24:
+        case 25:
+        case 26: {  // the mixed step's dense mode product on the tensor cores: as the CUDA-core one
+            const int st = smx_kernel_work(C, cls - 10, field, flops, bytes);
+            if (st) return st;
+            if (!C->use_digit) return SMX_EINVAL;
+            return SMX_OK;
+        }
         case 21:
         case 22:
         case 23: {  // FP64 dense mode product on the tensor cores: 2 n flops per entry
@@ -1579,8 +1615,12 @@ int smx_set_material_blocks(smx_ctx* C, int field, const double* values) {
     HodgeHost& H = C->hodge[1];
     std::vector<double> scale(nb);
     for (size_t k = 0; k < nb; ++k) scale[k] = -1.0 / values[k];
+    // The host copy of the tables (the blob) changes with the workspace: a later
+    // smx_bind_workspace and the no-alloc call upload the blob, not the workspace.
+    unsigned char* blob = C->blob.bytes.data();
     if (H.mode == 0) {
         for (size_t t = 0; t < H.gamma.size(); ++t) H.gamma[t] = 1.0 / values[H.tile_block[t]];
+        std::memcpy(blob + H.o_gamma, H.gamma.data(), H.gamma.size() * sizeof(double));
         CK(cudaMemcpyAsync(C->ws + H.o_gamma, H.gamma.data(), H.gamma.size() * sizeof(double), cudaMemcpyHostToDevice,
                            C->stream));
     } else {
@@ -1591,10 +1631,14 @@ int smx_set_material_blocks(smx_ctx* C, int field, const double* values) {
         float2* g32 = C->precision == SMX_MIXED ? reinterpret_cast<float2*>(C->ws + C->o_G32[1]) : nullptr;
         CK(launch_rescale_metric(reinterpret_cast<double*>(C->ws + H.o_G), g32, C->hq[1], C->eps_epb, C->eps_nb,
                                  C->scratch, C->stream));
+        // the same products on the host copy (one FP64 multiply each, so the copies stay bit-identical)
+        rescale_metric_host(C, ratio);
     }
+    std::memcpy(blob + C->o_pair_scale, scale.data(), nb * sizeof(double));
     CK(cudaMemcpyAsync(C->ws + C->o_pair_scale, scale.data(), nb * sizeof(double), cudaMemcpyHostToDevice, C->stream));
     CK(cudaStreamSynchronize(C->stream));
     C->eps_vals.assign(values, values + nb);
+    C->uid = g_next_uid.fetch_add(1);  // tables changed: the no-alloc array no longer holds them
     return SMX_OK;
 }
 
@@ -1660,6 +1704,7 @@ struct smx_batch {
     size_t smem = 0;
     long long steps = 0;  // amplitude index of the next step
     bool state_set = false;
+    unsigned long long wait_ns = 1000000000ull;  // grid-barrier wait limit
 };
 
 namespace {
@@ -1835,6 +1880,7 @@ static int batch_launch(smx_batch* B, int nsteps) {
     A.status = reinterpret_cast<unsigned*>(B->ws + B->o_status);
     A.line_warps = B->line_warps;
     A.warp_smem = (int)batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
+    A.wait_ns = B->wait_ns;
     for (int n = 0; n < nsteps; ++n) {
         A.step = (int)B->steps++;
         CK(launch_batch_step(A, B->grid, B->smem, B->stream));
@@ -1857,6 +1903,12 @@ int smx_batch_status(smx_batch* B) {
     CK(cudaMemsetAsync(B->ws + B->o_bar, 0, 2 * sizeof(unsigned), B->stream));
     CK(cudaStreamSynchronize(B->stream));
     return SMX_ETIMEOUT;
+}
+
+int smx_batch_set_wait_limit(smx_batch* B, double seconds) {
+    if (!B || !(seconds >= 0.0) || seconds > 60.0) return SMX_EINVAL;
+    B->wait_ns = (unsigned long long)(seconds * 1e9);
+    return SMX_OK;
 }
 
 int smx_batch_autotune(smx_batch* B, int steps, int* line_warps) {
@@ -1918,6 +1970,13 @@ int smx_hodge_star_noalloc(smx_ctx* C, int field, const double* x, double* out) 
     // layout of the fixed array: this context's tables (as in the workspace), then one vector
     const size_t o_y = C->tables_bytes;
     if (o_y + (size_t)n * sizeof(double) > (size_t)SMX_NOALLOC_BYTES) return SMX_ENOSPACE;
+    // the array is looked up for the current device; the kernels run on the context stream
+    if (C->stream) {
+        int cur = 0, sdev = 0;
+        CK(cudaGetDevice(&cur));
+        CK(cudaStreamGetDevice(C->stream, &sdev));
+        if (cur != sdev) return SMX_EINVAL;
+    }
     void* basev = nullptr;
     uint64_t* owner = nullptr;
     const int st = noalloc_region(&basev, &owner);

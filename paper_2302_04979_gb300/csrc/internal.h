@@ -219,6 +219,7 @@ struct BatchArgs {
     int line_warps;         // warps of a CTA that take line items
     int warp_smem;          // doubles of shared memory per line warp
     int step;               // index into amp
+    unsigned long long wait_ns;  // limit of each grid-barrier wait (default one second)
 };
 // unit encodings
 __host__ __device__ inline int batch_curl_unit(int c, int pb, int zc) { return (c << 28) | (zc << 14) | pb; }

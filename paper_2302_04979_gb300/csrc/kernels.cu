@@ -682,10 +682,10 @@ __device__ __forceinline__ unsigned long long batch_ns() {
     return t;
 }
 
-// All CTAs are co-resident (cooperative launch).  The wait is bounded (one
-// second); a CTA that gives up sets bit 1 of the status word and the whole
-// launch returns after the barrier.
-__device__ bool batch_barrier(unsigned* bar, unsigned* status, unsigned nblocks) {
+// All CTAs are co-resident (cooperative launch).  The wait is bounded (wait_ns,
+// one second by default); a CTA that gives up sets bit 1 of the status word and
+// the whole launch returns after the barrier.
+__device__ bool batch_barrier(unsigned* bar, unsigned* status, unsigned nblocks, unsigned long long wait_ns) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -700,7 +700,7 @@ __device__ bool batch_barrier(unsigned* bar, unsigned* status, unsigned nblocks)
         } else {
             const unsigned long long t0 = batch_ns();
             while (*gen == g) {
-                if (batch_ns() - t0 > 1000000000ull) {
+                if (batch_ns() - t0 > wait_ns) {
                     ok = 0;
                     atomicOr(status, 2u);
                     break;
@@ -772,6 +772,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs 
     extern __shared__ double smb[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned nblocks = gridDim.x;
+    // a barrier of an earlier launch gave up (its phases are incomplete and the
+    // barrier words are stale until smx_batch_status resets them): do nothing
+    if (*(volatile unsigned*)B.status & 2u) return;
     for (int ph = 0; ph < kBatchPhases; ++ph) {
         const int2* items = B.items[ph];
         const int n = B.nitems[ph];
@@ -817,7 +820,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs 
                 __syncwarp();  // the next unit reuses this warp's staging
             }
         }
-        if (ph + 1 < kBatchPhases && !batch_barrier(B.bar, B.status, nblocks)) return;
+        if (ph + 1 < kBatchPhases && !batch_barrier(B.bar, B.status, nblocks, B.wait_ns)) return;
     }
 }
 

@@ -79,6 +79,7 @@ _SIGS = {
     "smx_batch_set_state": [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6 + [ctypes.c_double],
     "smx_batch_step": [ctypes.c_void_p, ctypes.c_int],
     "smx_batch_status": [ctypes.c_void_p],
+    "smx_batch_set_wait_limit": [ctypes.c_void_p, ctypes.c_double],
     "smx_batch_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "smx_curl_primal": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
     "smx_curl_dual": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -103,12 +104,12 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)],
 }
 
-NCLASS = 24
+NCLASS = 27
 KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
                   "reduction", "mass_solve_x", "mass_solve_y", "mass_solve_z",
                   "curl_primal_f32", "curl_dual_f32", "hodge_block_f32", "line_f32_x", "line_f32_y", "line_f32_z",
                   "cast", "hodge_quad_f32", "mass_derivative", "receivers",
-                  "line_f64tc_x", "line_f64tc_y", "line_f64tc_z")
+                  "line_f64tc_x", "line_f64tc_y", "line_f64tc_z", "line_f32tc_x", "line_f32tc_y", "line_f32tc_z")
 
 
 def _lib():
@@ -419,6 +420,10 @@ class Batch:
 
     def status(self):
         _check(_lib().smx_batch_status(self.h), "smx_batch_status")
+
+    def set_wait_limit(self, seconds):
+        """Limit of each grid-barrier wait (seconds; 0 makes every pending wait give up at once)."""
+        _check(_lib().smx_batch_set_wait_limit(self.h, float(seconds)), "smx_batch_set_wait_limit")
 
     def autotune(self, steps=3):
         lw = ctypes.c_int()

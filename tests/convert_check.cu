@@ -17,7 +17,7 @@
 #include <cstdio>
 #include <cstdint>
 
-#include "../csrc/convert.cuh"
+#include "../paper_2302_04979_gb300/csrc/convert.cuh"
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ULL;

@@ -107,3 +107,29 @@ def test_adjoint_configuration_finite_differences():
         worst = max(worst, abs(fd - an) / abs(an))
         print("direction %d: FD %.10e adjoint %.10e rel %.2e" % (k, fd, an, abs(fd - an) / abs(an)))
     assert worst < 1e-6
+
+
+@pytest.mark.parametrize("geometry", ["identity", "sine_bump"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_material_update_survives_rebind(geometry, precision):
+    """smx_set_material_blocks rewrites the device tables and their host copy: the Hodge apply
+    matches the oracle with the new permittivity (1e-12) right after the update and after the
+    workspace is bound again (which uploads the host copy), for the block-Kronecker (identity)
+    and the quadrature (curved) Hodge; a second update works from the first's values."""
+    import torch
+    from paper_2302_04979_gb300 import smx
+    p, nel, blocks = 2, (4, 6, 4), (2, 3, 2)
+    geom = hodge.SineBumpMap(0.05) if geometry == "sine_bump" else None
+    vals = [synth.uniform(70 + k, int(np.prod(blocks)), 1.0, 6.0).reshape(blocks[::-1]) for k in range(3)]
+    ctx = smx.Context(p, nel, geometry=geometry, eps=("blocks", vals[0]), precision=precision).bind()
+    x = torch.as_tensor(synth.uniform(80, ctx.N_e, -1.0, 1.0)).cuda()
+    y = torch.empty_like(x)
+    for k in (1, 2):
+        ctx.set_material_blocks(vals[k])
+        want = maxwell.Scheme2(p, nel, geometry=geom, eps=("blocks", vals[k])).M_eps.apply(x.cpu().numpy())
+        for rebind in (False, True):
+            if rebind:
+                ctx.bind()
+            ctx.hodge_apply(smx.FIELD_D, x, y)
+            torch.cuda.synchronize()
+            assert rel_l2(y.cpu().numpy(), want) < 1e-12, (k, rebind)

@@ -1,5 +1,7 @@
-"""Batched cavities: one persistent launch per step (smx_batch_*) against the same cavities
-stepped one by one with smx_step (itself pinned to the oracle to 1e-11)."""
+"""Batched cavities: one persistent launch per step (smx_batch_*) against the oracle
+(oracle.maxwell.Scheme2.step, element-wise, 1e-11), against the same cavities stepped one by
+one with smx_step, and the bounded grid barrier's failure path (SMX_ETIMEOUT, then correct
+steps again)."""
 import numpy as np
 import pytest
 
@@ -110,3 +112,81 @@ def test_batched_configuration_64_cavities():
         ctx.step(*mine, dt, nsteps, jhat=jhat, amp=amp)
         errs = [rel_l2(to_host(g), to_host(w)) for g, w in zip(st, mine)]
         assert max(errs) < 1e-12, (k, errs)
+
+
+ORACLE_CASES = [
+    dict(p=2, nel=(5, 7, 4), eps=("blocks", synth.block_material(11, (5, 7, 2), 1.0, 4.0)), source=False),
+    dict(p=4, nel=(6, 4, 5), eps=("blocks", synth.block_material(12, (3, 2, 5), 1.0, 4.0)), source=True),
+    dict(p=3, nel=(7, 6, 9), eps=2.5, mu=1.25, source=True),
+]
+
+
+def _oracle_inputs(spec, seed, nsteps):
+    from oracle import maxwell as mx
+    S = mx.Scheme2(spec["p"], spec["nel"], eps=spec["eps"], mu=spec.get("mu", 1.0))
+    d = synth.uniform(seed, S.N_e, -1.0, 1.0)
+    b = S.D1 @ synth.uniform(seed + 1, S.N_e, -1.0, 1.0)
+    e = S.e_from_d(d)
+    dt = 0.5 * S.cfl(tol=1e-8)[0]
+    jhat = synth.uniform(seed + 2, S.N_e, -1.0, 1.0) if spec["source"] else None
+    amps = synth.uniform(seed + 3, nsteps, -1.0, 1.0) if spec["source"] else None
+    return S, d, b, e, dt, jhat, amps
+
+
+def _set_batch(batch, cases, inputs):
+    import torch
+    states, keep = [], []
+    for k, (S, d, b, e, dt, jhat, amps) in enumerate(inputs):
+        st = [to_dev(d), to_dev(b), to_dev(e), torch.zeros(S.N_h, dtype=torch.float64, device="cuda")]
+        jd = to_dev(jhat) if jhat is not None else None
+        ad = to_dev(amps) if amps is not None else None
+        batch.set_state(k, *st, dt, jhat=jd, amp=ad)
+        states.append(st)
+        keep.append((jd, ad))
+    return states, keep
+
+
+def test_batch_matches_oracle():
+    """Three uneven cavities (p = 2, 4, 3; anisotropic nel; block and constant material; two with a
+    source) stepped together by the persistent kernel, each against the oracle element-wise."""
+    from paper_2302_04979_gb300 import smx
+    nsteps = 12
+    inputs = [_oracle_inputs(s, 300 + 10 * k, nsteps) for k, s in enumerate(ORACLE_CASES)]
+    ctxs = [smx.Context(s["p"], s["nel"], eps=s["eps"], mu=s.get("mu", 1.0)).bind() for s in ORACLE_CASES]
+    batch = smx.Batch(ctxs)
+    states, keep = _set_batch(batch, ORACLE_CASES, inputs)
+    batch.step(nsteps)
+    batch.status()
+    for k, (S, d, b, e, dt, jhat, amps) in enumerate(inputs):
+        want = S.step(d, b, e, dt, nsteps, jhat=jhat, amps=amps)
+        errs = [rel_l2(to_host(g), w) for g, w in zip(states[k], want)]
+        print("\ncavity %d vs oracle: rel L2 d %.2e b %.2e e %.2e h %.2e" % (k, *errs))
+        assert max(errs) < 1e-11, (k, errs)
+
+
+def test_batch_barrier_timeout_then_recovers():
+    """With a zero wait limit the grid barriers give up: smx_batch_status reports SMX_ETIMEOUT
+    (the failure is made on the device by the time limit, not by a fault), later launches of the
+    same call return at entry, and after the status call and the limit restored the batch steps
+    correctly again (against the oracle, 1e-11)."""
+    from paper_2302_04979_gb300 import smx
+    nsteps = 6
+    cases = ORACLE_CASES[:2]
+    inputs = [_oracle_inputs(s, 400 + 10 * k, nsteps) for k, s in enumerate(cases)]
+    ctxs = [smx.Context(s["p"], s["nel"], eps=s["eps"], mu=s.get("mu", 1.0)).bind() for s in cases]
+    batch = smx.Batch(ctxs)
+    states, keep = _set_batch(batch, cases, inputs)
+    batch.set_wait_limit(0.0)
+    batch.step(nsteps)
+    with pytest.raises(smx.SmxError) as err:
+        batch.status()
+    assert err.value.status == smx.ETIMEOUT
+    batch.status()   # cleared
+    batch.set_wait_limit(1.0)
+    states, keep = _set_batch(batch, cases, inputs)   # fresh state; resets the step counter
+    batch.step(nsteps)
+    batch.status()
+    for k, (S, d, b, e, dt, jhat, amps) in enumerate(inputs):
+        want = S.step(d, b, e, dt, nsteps, jhat=jhat, amps=amps)
+        errs = [rel_l2(to_host(g), w) for g, w in zip(states[k], want)]
+        assert max(errs) < 1e-11, (k, errs)

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_integer_conversions_match_hardware(tmp_path):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    src = os.path.join(ROOT, "paper_2302_04979_gb300", "probe", "convert_check.cu")
+    src = os.path.join(ROOT, "tests", "convert_check.cu")
     exe = str(tmp_path / "convert_check")
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
     res = subprocess.run([exe], capture_output=True, text=True, timeout=600)

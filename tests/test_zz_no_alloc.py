@@ -52,6 +52,34 @@ def test_noalloc_switches_between_contexts():
     _compare(a_ref, a, 500)
 
 
+def test_noalloc_after_material_update():
+    """A block-permittivity update (smx_set_material_blocks) must reach the no-alloc call too:
+    its next call re-uploads the context's tables, and matches hodge_star and the oracle with
+    the new permittivity (1e-12), before and after the update, and again after a rebind."""
+    import torch
+    from oracle import maxwell as mx
+    from paper_2302_04979_gb300 import smx
+    p, nel, blocks = 3, (8, 6, 6), (2, 3, 2)
+    eps0 = synth.block_material(31, blocks, 1.0, 4.0)
+    eps1 = synth.block_material(32, blocks, 2.0, 9.0)
+    ctx = _ctx(p, nel, eps=("blocks", eps0), mu=1.0).bind()
+    x = to_dev(synth.uniform(600, ctx.N_e, -1.0, 1.0))
+    got = torch.full((ctx.N_e,), np.nan, dtype=torch.float64, device="cuda")
+    want = torch.empty_like(got)
+    for eps, rebind in ((eps0, False), (eps1, False), (eps1, True)):
+        if eps is eps1 and not rebind:
+            ctx.set_material_blocks(eps1)
+        if rebind:
+            ctx.bind()   # uploads the host copy of the tables again
+        ctx.hodge_star_noalloc(smx.FIELD_D, x, got)
+        ctx.hodge_star(smx.FIELD_D, x, want)
+        torch.cuda.synchronize()
+        ref = mx.Scheme2(p, nel, eps=("blocks", eps)).e_from_d(to_host(x))
+        assert rel_l2(to_host(got), to_host(want)) < 1e-12
+        assert rel_l2(to_host(got), ref) < 1e-12
+        assert rel_l2(to_host(want), ref) < 1e-12
+
+
 def test_noalloc_rejects_what_does_not_fit():
     import torch
     from paper_2302_04979_gb300 import smx
