@@ -92,6 +92,7 @@ KERNEL_FUNCTION = {
     "line_f32tc_y": ("mode_digit_kernel<4 digits>", "tensor4", "tensor"),
     "line_f32tc_z": ("mode_digit_kernel<4 digits>", "tensor4", "tensor"),
     "cast": ("cast kernels", "fp32", "hbm"),
+    "residual": ("band_apply_kernel", "fp64", "alu"),
 }
 # digit products per FP64-equivalent multiply-add of a dense line product: levels 0..6 of seven
 # digits (28) in the FP64 form, levels 0..3 of four digits (10) in the mixed form's tensor option
@@ -381,7 +382,8 @@ def kernel_table(ctx, smx, ktimes):
               "hodge_quad_f32": [f for f in (smx.FIELD_B, smx.FIELD_D) if mode[f] == 1],
               "line_f32_x": both, "line_f32_y": both, "line_f32_z": both,
               "line_f32tc_x": both, "line_f32tc_y": both, "line_f32tc_z": both,
-              "line_f64tc_x": both, "line_f64tc_y": both, "line_f64tc_z": both, "cast": both}
+              "line_f64tc_x": both, "line_f64tc_y": both, "line_f64tc_z": both, "cast": both,
+              "residual": both}
     kern = {}
     for name, (ms, cnt) in ktimes.items():
         if cnt == 0 or name not in fields:
@@ -600,6 +602,17 @@ def run_ours(args, rank, world, local):
     mctx.set_mode_kernel("auto")
     mctx.device_status()
     ctx.device_status()
+    # the refined mixed form: one refinement sweep of each Kronecker solve with an FP64 residual
+    rctx = smx.Context(P, NEL, eps=eps, mu=1.0, precision="mixed_refined").bind(dev)
+    rctx.set_stream(stream)
+    rstate = (d0.clone(), b0.clone(), e0.clone(), torch.zeros(nh, dtype=torch.float64, device=dev))
+    for _ in range(args.warmup):
+        rctx.step(*rstate, dt, 1)
+    r_ms, r_launches = time_steps(rctx, rstate, dt, args.steps, flush, stream, world)
+    r_ms = reduce_max(r_ms, world)
+    _, rkern = steady_and_kernels(rctx, smx, rstate, dt, min(args.steps, 50), flush, stream)
+    rctx.device_status()
+    del rctx
 
     # ---- the other configurations and the batched one (rank 0 of a single-GPU run only)
     configs = batched = None
@@ -652,6 +665,11 @@ def run_ours(args, rank, world, local):
                                                    "note": "same step, dense line operators on the tcgen05 tensor "
                                                            "cores (exact four-digit slicing, one FP32 rounding)"},
                          "speedup_vs_fp64": total_ms / m_ms,
+                         "refined": {"value": reduce_sum(dof * args.steps, world) / (r_ms * 1e-3),
+                                     "ms_per_step": r_ms / args.steps, "gpu_launches": r_launches,
+                                     "dtype": "f32 operators, one refinement sweep per Kronecker solve with an "
+                                              "f64 residual, f64 state and star outputs",
+                                     "kernels_frac": kernel_rooflines(rkern, peaks)[0]},
                          "steady_state": {"value": reduce_sum(dof * args.steps, world) / (m_steady * 1e-3),
                                           "ms_per_step": m_steady / args.steps}}}
         if configs is not None:

@@ -83,7 +83,7 @@ typedef struct {
     double geom_amplitude; /* SMX_GEOM_SINE_BUMP amplitude a; |a| < 1/(3 pi) keeps det J_F > 0 */
     smx_material eps;      /* permittivity: weights M~^2_{1/eps} (Eq. discrete2_hodge_eps) */
     smx_material mu;       /* permeability: weights M^2_{1/mu} (Eq. discrete2_hodge_mu) */
-    int precision;         /* SMX_FP64 or SMX_MIXED: arithmetic of smx_step / smx_step_host */
+    int precision;         /* SMX_FP64, SMX_MIXED or SMX_MIXED_REFINED: arithmetic of smx_step / smx_step_host */
 } smx_params;
 
 /* ---- precision of the leapfrog step ----
@@ -97,6 +97,14 @@ typedef struct {
  * smx_step_host (and smx_hodge_star_mixed) change; every other call stays FP64. */
 #define SMX_FP64 0
 #define SMX_MIXED 1
+/* SMX_MIXED_REFINED: the mixed operators with one refinement sweep of each
+ * Kronecker solve whose residual is formed in FP64.  Every Hodge star runs
+ * y = M x (FP32 element contributions summed in FP64), x0 = K^{-1} y in FP32,
+ * r = y - K x0 in FP64 (banded 1D pairing factors on the FP64 pipe),
+ * c = K^{-1} r in FP32 and writes x0 + c in FP64; the state d, b, e, h and
+ * the curls are FP64.  The line operators are those of SMX_MIXED (CUDA-core
+ * or tensor-core dense A^{-1} products, selected by smx_set_mode_kernel). */
+#define SMX_MIXED_REFINED 2
 
 typedef struct smx_ctx smx_ctx;
 
@@ -269,9 +277,10 @@ int smx_project(const smx_ctx* ctx, int field, smx_field_fn fn, void* user, doub
  *   18 FP32 quadrature Hodge, 19 per-block mass derivative (reverse step),
  *   20 receivers and small vector updates,
  *   21/22/23 FP64 dense line operators on the tensor cores along x/y/z,
- *   24/25/26 the mixed step's dense line operators on the tensor cores along x/y/z.
+ *   24/25/26 the mixed step's dense line operators on the tensor cores along x/y/z,
+ *   27 the refined step's FP64 residual passes.
  * ms[SMX_NCLASS] receives milliseconds, counts[SMX_NCLASS] launches per class. */
-#define SMX_NCLASS 27
+#define SMX_NCLASS 28
 int smx_launch_count(const smx_ctx* ctx, int64_t* n);
 int smx_set_timing(smx_ctx* ctx, int enable);
 int smx_kernel_times(smx_ctx* ctx, double* ms, int64_t* counts);

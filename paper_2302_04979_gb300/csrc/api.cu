@@ -147,6 +147,13 @@ struct smx_ctx {
     std::vector<double> rec_val;
     size_t o_rec_ptr = 0, o_rec_idx = 0, o_rec_val = 0;
     RecArgs rec{};
+    // refined mixed step: band rows of the 1D pairing factors (G, M, G^T, M^T per axis) for the
+    // FP64 residual, a second FP64 vector, and the residual passes [field][axis]
+    std::vector<double> band_rows[3][4];
+    size_t o_band[3][4] = {};
+    size_t o_t64 = 0;
+    double* t64 = nullptr;
+    BandApplyArgs band[2][3];
 };
 
 namespace {
@@ -160,7 +167,7 @@ void rescale_metric_host(smx_ctx* C, const std::vector<double>& ratio) {
     const HodgeHost& H = C->hodge[1];
     const long long Q = H.Qtot;
     double* G = reinterpret_cast<double*>(C->blob.bytes.data() + H.o_G);
-    float* G32 = C->precision == SMX_MIXED ? reinterpret_cast<float*>(C->blob.bytes.data() + C->o_G32[1]) : nullptr;
+    float* G32 = C->precision != SMX_FP64 ? reinterpret_cast<float*>(C->blob.bytes.data() + C->o_G32[1]) : nullptr;
     for (long long i = 0; i < Q; ++i) {
         const long long qx = i % H.Qn[0], r = i / H.Qn[0], qy = r % H.Qn[1], qz = r / H.Qn[1];
         const int bx = (int)(qx / H.q[0]) / C->eps_epb[0], by = (int)(qy / H.q[1]) / C->eps_epb[1];
@@ -457,12 +464,16 @@ void layout(smx_ctx* C) {
     C->o_status = C->o_dots + 256;
     C->o_state = C->o_status + 256;
     C->total_bytes = C->o_state + ((2 * (size_t)(C->N_e + C->N_h) * sizeof(double) + 255) & ~size_t(255));
-    if (C->precision == SMX_MIXED) {
+    if (C->precision != SMX_FP64) {
         auto f32 = [](long long n) { return ((size_t)n * sizeof(float) + 255) & ~size_t(255); };
         C->o_e32 = C->total_bytes;
         C->o_h32 = C->o_e32 + f32(C->N_e);
         C->o_y32 = C->o_h32 + f32(C->N_h);
         C->total_bytes = C->o_y32 + f32((long long)nmax);
+    }
+    if (C->precision == SMX_MIXED_REFINED) {  // a second FP64 vector for the residual passes
+        C->o_t64 = C->total_bytes;
+        C->total_bytes = C->o_t64 + ((nmax * sizeof(double) + 255) & ~size_t(255));
     }
 }
 
@@ -573,6 +584,10 @@ int mass_f32(smx_ctx* C, int h, const double* x, bool prezeroed) {
     return run(C, 13, 1, [&] { return launch_hodge_block_f32(C->hb32[h], x, nullptr, C->scratch, C->stream); });
 }
 
+// The mixed step fuses the mass of a separable star into its line operators (A^{-1} M);
+// the refined step always applies the mass on its own.
+bool fused_star(const smx_ctx* C, int h) { return C->hodge[h].separable && C->precision == SMX_MIXED; }
+
 int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* out64 = nullptr,
                         bool prezeroed = false) {
     int st;
@@ -584,7 +599,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         // dense mode products: A^{-1} M per axis (separable) or block mass + A^{-1} per axis
         const double* x64 = x;
         const float* x32 = nullptr;
-        if (!C->hodge[h].separable) {
+        if (!fused_star(C, h)) {
             if ((st = mass_f32(C, h, x, prezeroed))) return st;
             x64 = C->scratch;
         }
@@ -600,7 +615,7 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
         if ((st = pass(2, nullptr, out, tc ? out64 : nullptr))) return st;
         return tc ? SMX_OK : widen();
     }
-    if (C->hodge[h].separable) {
+    if (fused_star(C, h)) {
         st = run(C, 14, 1, [&] { return launch_line_f32(C->ln32[h][0], C->p[0] - 1, true, x, nullptr, out, C->stream); });
         if (st) return st;
         st = run(C, 15, 1, [&] { return launch_line_f32(C->ln32[h][1], C->p[1] - 1, true, nullptr, out, out, C->stream); });
@@ -624,7 +639,7 @@ int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
     int st = run(C, 17, 1, [&] { return launch_cast_d2f(e, C->e32, C->N_e, C->stream); });
     if (st) return st;
     // the curl before a star that accumulates a mass apply also clears that accumulator
-    const bool zH = !C->hodge[0].separable, zD = !C->hodge[1].separable;
+    const bool zH = !fused_star(C, 0), zD = !fused_star(C, 1);
     double* zeroH = zH ? C->scratch : nullptr;
     double* zeroD = zD ? C->scratch : nullptr;
     st = run(C, 11, 1, [&] {
@@ -648,12 +663,68 @@ int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
     return SMX_OK;
 }
 
+// out (FP32) = K^{-1} y by the mixed step's line operators (dense A^{-1} products on the
+// FP32 CUDA cores or the four-digit tensor-core kernel, or FP32 banded recurrences for
+// lines longer than 80); y is FP64.
+int solve_f32_impl(smx_ctx* C, int h, const double* y, float* out) {
+    int st;
+    if (C->use_mode) {
+        const bool tc = C->mode_kernel == SMX_MODE_TENSOR;
+        for (int a = 0; a < 3; ++a) {
+            st = run(C, (tc ? 24 : 14) + a, 1, [&] {
+                const double* i64 = a == 0 ? y : nullptr;
+                const float* i32 = a == 0 ? nullptr : out;
+                return tc ? launch_mode_digit_f32(C->mdg[h][a], i64, i32, out, nullptr, C->stream)
+                          : launch_mode_f32(C->md32[h][a], i64, i32, out, C->stream);
+            });
+            if (st) return st;
+        }
+        return SMX_OK;
+    }
+    for (int a = 0; a < 3; ++a) {
+        st = run(C, 14 + a, 1, [&] {
+            return launch_line_f32(C->ln32[h][a], C->p[a] - 1, false, a == 0 ? y : nullptr, a == 0 ? nullptr : out,
+                                   out, C->stream);
+        });
+        if (st) return st;
+    }
+    return SMX_OK;
+}
+
+// The refined mixed Hodge star (SMX_MIXED_REFINED): y = M x (FP32 element
+// contributions summed in FP64), x0 = K^{-1} y in FP32, the residual
+// r = y - K x0 formed in FP64 (three banded passes of the 1D pairing factors on
+// the FP64 pipe), one correction c = K^{-1} r in FP32, out = x0 + c in FP64.
+int star_refined(smx_ctx* C, int h, const double* x, double* out, bool prezeroed) {
+    int st;
+    const long long ntot = C->fld[kFieldOfHodge[h]].total;
+    float* x0 = h == 0 ? C->h32 : C->e32;
+    if ((st = mass_f32(C, h, x, prezeroed))) return st;  // y in scratch
+    if ((st = solve_f32_impl(C, h, C->scratch, x0))) return st;
+    // r = y - (A_z (x) A_y (x) A_x) x0: t64 = A_x x0, scratch2 = A_y t64, t64 = y - A_z scratch2
+    if ((st = run(C, 27, 1, [&] { return launch_band_apply(C->band[h][0], nullptr, x0, nullptr, C->t64, C->stream); })))
+        return st;
+    if ((st = run(C, 27, 1, [&] { return launch_band_apply(C->band[h][1], C->t64, nullptr, nullptr, C->scratch2, C->stream); })))
+        return st;
+    if ((st = run(C, 27, 1, [&] {
+             return launch_band_apply(C->band[h][2], C->scratch2, nullptr, C->scratch, C->t64, C->stream);
+         })))
+        return st;
+    if ((st = solve_f32_impl(C, h, C->t64, C->y32))) return st;
+    return run(C, 17, 1, [&] { return launch_refine_sum(x0, C->y32, out, ntot, C->stream); });
+}
+
+// Refined mixed steps: FP64 state and curls (d, b, e, h all FP64), refined stars.
+int step_refined(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp,
+                 double dt, int nsteps);
+
 int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezeroed = false);
 
 // nsteps kick-drift-kick steps enqueued kernel by kernel (the inner half kicks of b merged).
 int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp, double dt,
                int nsteps) {
     if (C->precision == SMX_MIXED) return step_mixed(C, d, b, e, h, jhat, amp, dt, nsteps);
+    if (C->precision == SMX_MIXED_REFINED) return step_refined(C, d, b, e, h, jhat, amp, dt, nsteps);
     // the curl before a star that accumulates a mass apply also clears that accumulator
     const bool zH = !C->hodge[0].separable, zD = !C->hodge[1].separable;
     double* zeroH = zH ? C->scratch : nullptr;
@@ -665,6 +736,20 @@ int step_eager(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
         if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0, zeroD))) return st;
         if ((st = hodge_star_impl(C, 1, d, e, zD))) return st;  // e = K_1^{-1} M~^2_{1/eps} d
         if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt, zeroH))) return st;
+    }
+    return SMX_OK;
+}
+
+int step_refined(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp,
+                 double dt, int nsteps) {
+    double* zero = C->scratch;  // every refined star starts with a mass apply into the scratch vector
+    int st = curl_primal_impl(C, e, b, -0.5 * dt, zero);
+    if (st) return st;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((st = star_refined(C, 0, b, h, true))) return st;
+        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0, zero))) return st;
+        if ((st = star_refined(C, 1, d, e, true))) return st;
+        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt, zero))) return st;
     }
     return SMX_OK;
 }
@@ -796,11 +881,21 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             mats[2] = &Gt;
             mats[3] = &Mt;
             const int ns[4] = {nG, nM, nG, nM};
-            for (int w = 0; w < 4; ++w)
+            for (int w = 0; w < 4; ++w) {
                 if (!band_lu(*mats[w], ns[w], p - 1, p - 1, C->fac[a][w])) {
                     delete C;
                     return SMX_ESINGULAR;
                 }
+                // band rows A(m, m - kl .. m + kl) of the factor itself (the refined step's residual)
+                const int n = ns[w], kl = p - 1, W = 2 * kl + 1;
+                std::vector<double>& R = C->band_rows[a][w];
+                R.assign((size_t)n * W, 0.0);
+                for (int m = 0; m < n; ++m)
+                    for (int q = 0; q < W; ++q) {
+                        const int j = m - kl + q;
+                        if (j >= 0 && j < n) R[(size_t)m * W + q] = (*mats[w])[(size_t)m * n + j];
+                    }
+            }
         }
         // Hodge tables: block Kronecker on the identity map with constant or block material
         const smx_material* mats[2] = {&P->mu, &P->eps};
@@ -814,7 +909,7 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             }
             if (block && mats[h]->kind == SMX_MAT_CONST) build_separable(C, h, 1.0 / mats[h]->value);
         }
-        if (P->precision != SMX_FP64 && P->precision != SMX_MIXED) {
+        if (P->precision != SMX_FP64 && P->precision != SMX_MIXED && P->precision != SMX_MIXED_REFINED) {
             delete C;
             return SMX_EINVAL;
         }
@@ -841,7 +936,7 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             } else {
                 for (int a = 0; a < 3; ++a) H.o_bval[a] = C->blob.add(H.bval[a]);
                 H.o_G = C->blob.add(H.G);
-                if (C->precision == SMX_MIXED) {  // the mixed step's FP32 (hi, lo) copies
+                if (C->precision != SMX_FP64) {  // the mixed step's FP32 (hi, lo) copies
                     for (int a = 0; a < 3; ++a) C->o_bval32[h][a] = C->blob.add(split_pairs(H.bval[a]));
                     C->o_G32[h] = C->blob.add(split_pairs(H.G));
                 }
@@ -849,7 +944,10 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                 H.G.shrink_to_fit();
             }
         }
-        if (C->precision == SMX_MIXED) {
+        if (C->precision == SMX_MIXED_REFINED)
+            for (int a = 0; a < 3; ++a)
+                for (int w = 0; w < 4; ++w) C->o_band[a][w] = C->blob.add(C->band_rows[a][w]);
+        if (C->precision != SMX_FP64) {
             // FP32 (hi, lo) copies of every operator table of the mixed step
             for (int a = 0; a < 3; ++a)
                 for (int w = 0; w < 4; ++w) {
@@ -872,7 +970,7 @@ int smx_create(const smx_params* P, smx_ctx** out) {
         for (int a = 0; a < 3; ++a)
             if (kind_dim(P0, C->p[a], C->nel[a]) + 1 > kModeMaxN) dense = false;
         if (dense) {
-            C->use_mode = C->precision == SMX_MIXED;
+            C->use_mode = C->precision != SMX_FP64;
             C->use_digit = true;  // digit planes: 7 digits (FP64 step) or 4 (mixed step)
             const int nd = C->precision == SMX_FP64 ? kDigits : kDigitsF32;
             std::vector<double> inv[3][4];
@@ -885,9 +983,12 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                     for (int c = 0; c < 3; ++c) {
                         const int w = factor_index(which, c, a), kind = kFieldKinds[fld][c][a];
                         const int n = C->fac[a][w].n;
+                        // a separable star of the FP64 and mixed steps fuses the mass: A^{-1} M; the
+                        // refined step applies the mass on its own and needs A^{-1} for the residual
                         const std::vector<double> B =
-                            H.separable ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
-                                        : inv[a][w];
+                            (H.separable && C->precision != SMX_MIXED_REFINED)
+                                ? dense_times_band(inv[a][w], H.lmass[a][kind], n, kind_degree(kind, C->p[a]))
+                                : inv[a][w];
                         {
                             std::vector<uint16_t> planes;
                             std::vector<int32_t> rowexp;
@@ -1090,7 +1191,21 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                     Mg.npad[c] = mode_digit_npad(C->fld[fld].c[c].n[a]);
                 }
             }
-    if (C->precision == SMX_MIXED) {
+    if (C->precision == SMX_MIXED_REFINED) {
+        C->t64 = reinterpret_cast<double*>(ws + C->o_t64);
+        for (int h = 0; h < 2; ++h) {
+            const int fld = kFieldOfHodge[h], which = h == 0 ? 1 : 0;  // M^2 pairs with K~_1, M~^2 with K_1
+            for (int a = 0; a < 3; ++a) {
+                BandApplyArgs& Ba = C->band[h][a];
+                Ba.field = C->fld[fld];
+                Ba.axis = a;
+                Ba.kl = C->p[a] - 1;
+                for (int c = 0; c < 3; ++c)
+                    Ba.band[c] = reinterpret_cast<const double*>(ws + C->o_band[a][factor_index(which, c, a)]);
+            }
+        }
+    }
+    if (C->precision != SMX_FP64) {
         C->e32 = reinterpret_cast<float*>(ws + C->o_e32);
         C->h32 = reinterpret_cast<float*>(ws + C->o_h32);
         C->y32 = reinterpret_cast<float*>(ws + C->o_y32);
@@ -1300,8 +1415,9 @@ int smx_hodge_star_mixed(smx_ctx* C, int field, const double* x, double* out) {
     NEED_WS(C);
     if (!x || !out) return SMX_EINVAL;
     if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
-    if (C->precision != SMX_MIXED) return SMX_ESTATE;
+    if (C->precision == SMX_FP64) return SMX_ESTATE;
     const int h = field == SMX_FIELD_B ? 0 : 1;
+    if (C->precision == SMX_MIXED_REFINED) return star_refined(C, h, x, out, false);
     float* o32 = h == 0 ? C->h32 : C->e32;
     return hodge_star_f32_impl(C, h, x, o32, out);
 }
@@ -1529,6 +1645,16 @@ int smx_kernel_work(const smx_ctx* C, int cls, int field, double* flops, double*
             *bytes = 16.0 * N;
             return SMX_OK;
         }
+        case 27: {  // refinement residual: one banded pass of 2 KL + 1 FMAs per entry (the mean over the axes)
+            const int h = bside ? 0 : 1;
+            if (C->precision != SMX_MIXED_REFINED) return SMX_EINVAL;
+            const DevField& F = C->fld[kFieldOfHodge[h]];
+            double f = 0.0;
+            for (int a = 0; a < 3; ++a) f += 2.0 * (2 * (C->p[a] - 1) + 1) * (double)F.total;
+            *flops = f / 3.0;
+            *bytes = (12.0 + 16.0 / 3.0 + 8.0 / 3.0) * N;  // x0 FP32 or FP64 in, FP64 out, y once
+            return SMX_OK;
+        }
         case 18: {  // FP32 quadrature Hodge: the FP64 quadrature kernel's flops, FP32 metric
             const int st = smx_kernel_work(C, 3, field, flops, bytes);
             if (st) return st;
@@ -1628,7 +1754,7 @@ int smx_set_material_blocks(smx_ctx* C, int field, const double* values) {
         std::vector<double> ratio(nb);
         for (size_t k = 0; k < nb; ++k) ratio[k] = C->eps_vals[k] / values[k];
         CK(cudaMemcpyAsync(C->scratch, ratio.data(), nb * sizeof(double), cudaMemcpyHostToDevice, C->stream));
-        float2* g32 = C->precision == SMX_MIXED ? reinterpret_cast<float2*>(C->ws + C->o_G32[1]) : nullptr;
+        float2* g32 = C->precision != SMX_FP64 ? reinterpret_cast<float2*>(C->ws + C->o_G32[1]) : nullptr;
         CK(launch_rescale_metric(reinterpret_cast<double*>(C->ws + H.o_G), g32, C->hq[1], C->eps_epb, C->eps_nb,
                                  C->scratch, C->stream));
         // the same products on the host copy (one FP64 multiply each, so the copies stay bit-identical)

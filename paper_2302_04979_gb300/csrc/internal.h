@@ -158,6 +158,19 @@ cudaError_t launch_mode_digit_f32(const ModeDigitArgs& a, const double* in64, co
 cudaError_t launch_curl_f32(bool dual, const DevField& IN, const DevField& OUT, const float* in, double* out,
                             double alpha, const double* jhat, const double* amp, int amp_index, double s_host,
                             cudaStream_t s, double* zero = nullptr);
+// Banded 1D pairing factor applied along one axis (the FP64 residual of the
+// refined mixed step): out = A x along every line of the axis, or out = y - A x
+// when y is given.  x is FP64 (in64) or FP32 (in32); A in band rows.
+struct BandApplyArgs {
+    DevField field;
+    const double* band[3];  // per component: n x (2 kl + 1) band rows, row m holds A(m, m - kl .. m + kl)
+    int kl;                 // half-bandwidth (degree along the axis - 1)
+    int axis;
+};
+cudaError_t launch_band_apply(const BandApplyArgs& a, const double* in64, const float* in32, const double* y,
+                              double* out, cudaStream_t s);
+// out = x0 + c in FP64 (both FP32; the sum is exact in FP64 unless the exponents differ by more than 29)
+cudaError_t launch_refine_sum(const float* x0, const float* c, double* out, long long n, cudaStream_t s);
 cudaError_t launch_cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
 cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
 cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, double* y,

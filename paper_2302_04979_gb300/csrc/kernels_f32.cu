@@ -66,6 +66,61 @@ cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ refinement residual, FP64
+// One thread per entry: acc = sum_q A(m, m - kl + q) x(m - kl + q) along the
+// entry's line (the FP64 pipe, 2 kl + 1 FMAs), out = acc or y - acc.  Reads
+// along y and z are coalesced across threads (consecutive x); the input must
+// not alias the output.
+template <class TIN>
+__global__ void __launch_bounds__(256) band_apply_kernel(BandApplyArgs A, const TIN* __restrict__ in,
+                                                         const double* __restrict__ y, double* __restrict__ out) {
+    pdl_wait();
+    const long long idx = blockIdx.x * 256ll + threadIdx.x;
+    if (idx < A.field.total) {
+        int c = 0;
+        while (c < 2 && idx >= A.field.c[c + 1].off) ++c;
+        const DevComp C = A.field.c[c];
+        const long long loc = idx - C.off;
+        const int i = (int)(loc % C.n[0]);
+        const long long r = loc / C.n[0];
+        const int j = (int)(r % C.n[1]), k = (int)(r / C.n[1]);
+        const int m = A.axis == 0 ? i : (A.axis == 1 ? j : k);
+        const int n = C.n[A.axis];
+        const long long st = A.axis == 0 ? 1 : (A.axis == 1 ? (long long)C.n[0] : (long long)C.n[0] * C.n[1]);
+        const int W = 2 * A.kl + 1;
+        const double* brow = A.band[c] + (long long)m * W;
+        double acc = 0.0;
+        for (int q = 0; q < W; ++q) {
+            const int mm = m - A.kl + q;
+            if (mm >= 0 && mm < n) acc = fma(__ldg(brow + q), widen(in[idx + (long long)(mm - m) * st]), acc);
+        }
+        out[idx] = y ? y[idx] - acc : acc;
+    }
+    pdl_trigger();
+}
+
+cudaError_t launch_band_apply(const BandApplyArgs& a, const double* in64, const float* in32, const double* y,
+                              double* out, cudaStream_t s) {
+    const long long n = a.field.total;
+    if (n <= 0) return cudaGetLastError();
+    const dim3 grid((unsigned)((n + 255) / 256));
+    if (in64) return launch_k(band_apply_kernel<double>, grid, dim3(256), 0, s, a, in64, y, out);
+    return launch_k(band_apply_kernel<float>, grid, dim3(256), 0, s, a, in32, y, out);
+}
+
+__global__ void refine_sum_kernel(const float* __restrict__ x0, const float* __restrict__ c, double* __restrict__ out,
+                                  long long n) {
+    pdl_wait();
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = f2d_exact(x0[i]) + f2d_exact(c[i]);
+    pdl_trigger();
+}
+
+cudaError_t launch_refine_sum(const float* x0, const float* c, double* out, long long n, cudaStream_t s) {
+    if (n > 0) return launch_k(refine_sum_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, x0, c, out, n);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ Hodge: block Kronecker, FP32
 // Same algorithm as the FP64 block kernel (one CTA per tile and component,
 // three banded passes in shared memory, atomics to scatter) with split FP32

@@ -88,16 +88,19 @@ constexpr int kDgRows = 128;       // MMA M: operator rows (TMEM lanes)
 constexpr int kDgIssuer = 3;       // the warp (lane quarter 3: rows 96..127, never an output) issuing MMAs
 constexpr int kDgKcMax = (kModeMaxN + 15) / 16 * 2;  // k-chunks of 8 at the largest npad
 constexpr uint32_t kDgTmemCols = 512;
-constexpr int kDgHeader = 1024;    // 8 full + 8 drained mbarriers, TMEM address, line exponents (<= 128)
+constexpr int kDgHeader = 1536;    // 8 full + 8 drained mbarriers, TMEM address, line exponents (<= 128), row exponents (<= 80)
 constexpr int kDgSmemMax = 232448;  // opt-in shared memory per CTA
 
 static_assert(kModeMaxN <= 96, "operator rows must stay in lane quarters 0..2");
 
 __host__ __device__ inline int dg_op_bytes(int npad, int r8, int nd) { return nd * (npad / 16) * r8 * 32; }
 __host__ __device__ inline int dg_x_bytes(int npad, int nl, int nd) { return nd * (npad / 16) * nl * 32; }
+// after the last MMA the tile planes hold the final accumulators: r8 rows of nl + 1 64-bit words
+__host__ __device__ inline int dg_acc_bytes(int nl, int r8) { return r8 * (nl + 1) * 8; }
 // header, 256 bytes of slack to align the planes to the swizzle pattern, operator and tile planes
 __host__ __device__ inline int dg_smem_bytes(int nl, int npad, int r8, int nd) {
-    return kDgHeader + 256 + dg_op_bytes(npad, r8, nd) + dg_x_bytes(npad, nl, nd);
+    const int x = dg_x_bytes(npad, nl, nd), acc = dg_acc_bytes(nl, r8);
+    return kDgHeader + 256 + dg_op_bytes(npad, r8, nd) + (x > acc ? x : acc);
 }
 
 // Bit-pattern layout of the two input formats.
@@ -264,6 +267,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
     const uint32_t full0 = smem_u32(smem), drained0 = full0 + 64;
     uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 128);
     int* sExp = reinterpret_cast<int*>(smem + 256);
+    int* sRowE = reinterpret_cast<int*>(smem + 1024);
     unsigned char* sOp = smem + kDgHeader + ((256u - ((smem_u32(smem) + kDgHeader) & 255u)) & 255u);
     unsigned char* sX = sOp + dg_op_bytes(npad, r8, ND);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -283,6 +287,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
             mbar_init(drained0 + 8 * b, kGroups * nquarters);
         }
     if (tid < NL) sExp[tid] = 1;
+    if (tid < n) sRowE[tid] = A.rowexp[c][tid];  // the table, not the previous kernel's output
 
     // operator digits: the table is the shared layout, one contiguous copy
     const unsigned char* Bg = static_cast<const unsigned char*>(A.B[c]);
@@ -370,14 +375,21 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
     bool ok = true;
     TOUT* dst = out + C.off;
     double* dst64 = out64 ? out64 + C.off : nullptr;
-    TOUT* stage = reinterpret_cast<TOUT*>(sX);  // y/z sweeps: n x (NL + 1), after the last MMA
+    long long* sAcc = reinterpret_cast<long long*>(sX);  // n x (NL + 1) final accumulators, after the last MMA
 
     if (warp == kDgIssuer) {
         if (lane == 0) {
             // level l into buffer l % kBufs: every digit pair t + s = l, k-step by k-step;
             // the first MMA of a level overwrites the buffer
-            const uint32_t idesc = idesc_bf16_f32(kDgRows, NL);
-            const uint32_t a0 = smem_u32(sOp), b0 = smem_u32(sX);
+            // The issue loop is kept to a few integer instructions per MMA (one thread issues
+            // all of them; a descriptor rebuilt per MMA made the issue, not the tensor pipe,
+            // the limit): base descriptors once, then the 14-bit start-address field advanced
+            // by constant steps (every address stays below 2^18, so the field cannot carry).
+            constexpr uint32_t idesc = idesc_bf16_f32(kDgRows, NL);
+            const uint64_t dA0 = smem_desc_sw32(smem_u32(sOp), 256), dB0 = smem_desc_sw32(smem_u32(sX), 256);
+            const uint64_t stA = (uint64_t)(colA >> 4), stB = (uint64_t)(colX >> 4);
+            const uint64_t plA = (uint64_t)(opPlane >> 4), plB = (uint64_t)(xPlane >> 4);
+            const int nks = kc / 2;
             for (int lv = 0; lv < ND && ok; ++lv) {
                 const int buf = lv % kBufs;
                 if (lv >= kBufs) {
@@ -385,11 +397,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
                     tc_fence_after();
                     if (!ok) break;
                 }
+                const uint32_t d = tmem + (uint32_t)(buf * NL);
                 for (int t = 0; t <= lv; ++t) {
-                    const int s = lv - t;
-                    for (int ks = 0; ks < kc / 2; ++ks)
-                        mma_bf16(tmem + (uint32_t)(buf * NL), smem_desc_sw32(a0 + s * opPlane + ks * colA, 256),
-                                 smem_desc_sw32(b0 + t * xPlane + ks * colX, 256), idesc, (t | ks) ? 1u : 0u);
+                    uint64_t a = dA0 + (uint64_t)(lv - t) * plA, b = dB0 + (uint64_t)t * plB;
+                    mma_bf16(d, a, b, idesc, t ? 1u : 0u);  // the level's first MMA overwrites the buffer
+                    for (int ks = 1; ks < nks; ++ks) {
+                        a += stA;
+                        b += stB;
+                        mma_bf16(d, a, b, idesc, 1u);
+                    }
                 }
                 mma_commit(full0 + 8 * buf);
             }
@@ -398,14 +414,13 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         __syncwarp();
     } else if (reader) {
         const int i = 32 * quarter + lane;  // operator row = output entry along the line
-        const int Fi = i < n ? A.rowexp[c][i] : 0;
         const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(group * kCpw);
         unsigned long long acc[kCpw];  // Horner accumulators, two's complement (wraps only on unused rows)
 #pragma unroll
         for (int j = 0; j < kCpw; ++j) acc[j] = 0;
         for (int lv = 0; lv < ND; ++lv) {
             const int buf = lv % kBufs;
-            ok = __all_sync(0xffffffffu, mbar_wait_bounded(full0 + 8 * buf, (lv / kBufs) & 1));
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded_sleep(full0 + 8 * buf, (lv / kBufs) & 1, 128));
             if (!ok) break;
             tc_fence_after();
             uint32_t v[kCpw / 8][8];
@@ -430,33 +445,36 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         if (!ok) {
             if (lane == 0) atomicOr(A.status, 1u);
         } else if (i < n) {
-            const int eRow = 8 * ND + Fi - 1075 - kTopOp;  // 2^(8 ND) tau_i
+            // every MMA has completed, so the tile planes are free: the accumulators go to
+            // shared memory and all warps share the final rounding (the warps of the output
+            // rows' lane quarters sit on only two or three of the four SM sub-partitions)
 #pragma unroll
-            for (int j = 0; j < kCpw; ++j) {
-                const int col = group * kCpw + j, L = l0 + col;
-                const TOUT y = digit_out((long long)acc[j], eRow + digit_scale<TIN, ND>(sExp[col]), (TOUT*)nullptr);
-                if (axis == 0) {
-                    if (L < nlines) {
-                        dst[(long long)L * n + i] = y;
-                        if (dst64) dst64[(long long)L * n + i] = f2d_exact(y);
-                    }
-                } else {
-                    stage[i * (NL + 1) + col] = y;  // every MMA has completed: the digit planes are free
-                }
-            }
+            for (int j = 0; j < kCpw; ++j) sAcc[i * (NL + 1) + group * kCpw + j] = (long long)acc[j];
         }
     }
-    // the staged y/z tile: consecutive threads write consecutive lines
     ok = __syncthreads_and(ok) != 0;
     pdl_trigger();  // the next kernel may be scheduled; its pdl_wait still waits for this grid
-    if (ok && axis != 0) {
+    if (ok) {
+        // acc * 2^(8 ND) * sigma_L * tau_i rounded once; consecutive threads write consecutive
+        // addresses: entries of one line along x, consecutive lines along y and z
         const int nl = min(NL, nlines - l0);
-        for (int g = tid; g < n * NL; g += THREADS) {
-            const int ii = g / NL, col = g - ii * NL;
-            if (col >= nl) continue;
+        const int total = axis == 0 ? n * nl : n * NL;
+        for (int g = tid; g < total; g += THREADS) {
+            int ii, col;
+            if (axis == 0) {
+                col = g / n;
+                ii = g - col * n;
+            } else {
+                ii = g / NL;
+                col = g - ii * NL;
+                if (col >= nl) continue;
+            }
             const int L = l0 + col;
-            const long long o = (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L) + (long long)ii * stride;
-            const TOUT y = stage[ii * (NL + 1) + col];
+            const int e2 = 8 * ND + sRowE[ii] - 1075 - kTopOp + digit_scale<TIN, ND>(sExp[col]);
+            const TOUT y = digit_out(sAcc[ii * (NL + 1) + col], e2, (TOUT*)nullptr);
+            const long long o = axis == 0 ? (long long)L * n + ii
+                                          : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L) +
+                                                (long long)ii * stride;
             dst[o] = y;
             if (dst64) dst64[o] = f2d_exact(y);
         }

@@ -90,6 +90,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
     return true;
 }
 
+// The same wait for threads that only consume results: between polls the thread
+// sleeps for about `ns` nanoseconds, so that many waiting warps do not keep the
+// shared-memory pipe busy while the tensor core reads its operands from it.
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint32_t a, uint32_t parity, unsigned ns) {
+    if (mbar_try_wait(a, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(a, parity)) {
+        if (global_ns() - t0 > kWaitNs) return false;
+        __nanosleep(ns);
+    }
+    return true;
+}
+
 // 32 lanes x 8 consecutive 32-bit columns; the wait carries the registers so
 // that no use of them can be scheduled before it.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {

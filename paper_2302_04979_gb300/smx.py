@@ -104,12 +104,12 @@ _SIGS = {
                         ctypes.POINTER(ctypes.c_double)],
 }
 
-NCLASS = 27
+NCLASS = 28
 KERNEL_CLASSES = ("curl_primal", "curl_dual", "hodge_block", "hodge_quad", "solve_x", "solve_y", "solve_z",
                   "reduction", "mass_solve_x", "mass_solve_y", "mass_solve_z",
                   "curl_primal_f32", "curl_dual_f32", "hodge_block_f32", "line_f32_x", "line_f32_y", "line_f32_z",
                   "cast", "hodge_quad_f32", "mass_derivative", "receivers",
-                  "line_f64tc_x", "line_f64tc_y", "line_f64tc_z", "line_f32tc_x", "line_f32tc_y", "line_f32tc_z")
+                  "line_f64tc_x", "line_f64tc_y", "line_f64tc_z", "line_f32tc_x", "line_f32tc_y", "line_f32tc_z", "residual")
 
 
 def _lib():
@@ -172,7 +172,7 @@ def material(spec):
     return m, keep
 
 
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_REFINED = 0, 1, 2
 
 
 def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64"):
@@ -185,7 +185,7 @@ def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, pr
     P.geom_amplitude = float(amplitude)
     P.eps, k1 = material(eps)
     P.mu, k2 = material(mu)
-    P.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    P.precision = {"fp64": FP64, "mixed": MIXED, "mixed_refined": MIXED_REFINED}[precision]
     return P, k1 + k2
 
 

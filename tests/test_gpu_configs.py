@@ -3,11 +3,14 @@
 * cube p=2, 8^3, TE_111 initial data, 100 steps at 0.5 x CFL: every field
   compared after all 100 steps (1e-11), W conserved, error to the exact mode;
 * curved p=3, 32^3, Gaussian-bump permittivity, Gaussian-pulse current: every
-  field after 4 steps against the oracle, then 500 GPU steps checked through
-  the discrete Gauss laws (D^2 b = 0, continuity for D~^2 d);
+  field after all 500 driven steps against the oracle (FP64 1e-11, the refined
+  mixed form 1e-5), and the discrete Gauss laws (D^2 b = 0, continuity for
+  D~^2 d);
 * p=3, 64^3, 8^3-block permittivity (the benchmark workload) and p=4, 64^3:
-  every field after 2 steps against the oracle (the oracle needs seconds per
-  step at this size), then 1000 GPU steps with W conserved to round-off.
+  every field against the oracle after 50 and 25 steps (the oracle needs
+  seconds per step at this size), both mixed forms after 50 steps, then 1000
+  GPU steps with W conserved to round-off.
+The oracle trajectories are computed once per session and shared by the tests.
 Inputs come from the seeded generators and the oracle (projections, CFL);
 nothing expected is produced by the CUDA path.
 """
@@ -51,96 +54,135 @@ def test_cube_p2_te111_100_steps():
     assert err / nrm < 0.3                  # p=2 on 8^3: dispersion-dominated, loose by design
 
 
+# ---------------------------------------------------------------- oracle trajectories (computed once)
+_CACHE = {}
+
+
+def _curved_case(nsteps):
+    """Config 2: sine-bump map (0.05), p=3, 32^3, Gaussian-bump permittivity, Gaussian-pulse current
+    projected by the oracle, dt = 0.003 (about 0.5 x CFL), zero initial fields; the oracle's fields
+    after nsteps steps (computed once per session)."""
+    key = ("curved", nsteps)
+    if key not in _CACHE:
+        bumps = synth.GaussianBumps(2302)
+        S = mx.Scheme2(3, 32, geometry=hodge.SineBumpMap(0.05), eps=bumps)
+        jhat = S.project_2form("D", synth.pulse_profile(synth.pulse_centre(2302), 0.05), rtol=1e-10)
+        d, b, e = np.zeros(S.N_e), np.zeros(S.N_h), np.zeros(S.N_e)
+        dt = 0.003
+        amps = synth.source_amplitudes(dt, nsteps, f0=1.0, tau=0.25, t0=0.75)
+        ref = S.step(d, b, e, dt, nsteps, jhat=jhat, amps=amps)
+        _CACHE[key] = dict(S=S, bumps=bumps, jhat=jhat, d=d, b=b, e=e, dt=dt, amps=amps, ref=ref)
+    return _CACHE[key]
+
+
+CURVED_STEPS = 500
+
+
 @pytest.mark.slow
 def test_curved_p3_32cube_pulse():
+    """FP64 against the oracle after all 500 driven steps (1e-11), and the discrete Gauss laws
+    (D^2 b = 0; continuity for D~^2 d) on the GPU fields."""
     from paper_2302_04979_gb300 import smx
-    bumps = synth.GaussianBumps(2302)
-    S = mx.Scheme2(3, 32, geometry=hodge.SineBumpMap(0.05), eps=bumps)
-    ctx = smx.Context(3, 32, geometry="sine_bump", amplitude=0.05, eps=bumps).bind()
-    jhat = S.project_2form("D", synth.pulse_profile(synth.pulse_centre(2302), 0.05), rtol=1e-10)
-    d = np.zeros(S.N_e)
-    b = np.zeros(S.N_h)
-    e = np.zeros(S.N_e)
-    # 0.5 x CFL: the oracle's CFL of this map and material is 0.0126 at 16^3 and
-    # linear in h (Sec. 5.2), so about 0.0063 at 32^3
-    dt = 0.003
-    n_ref, n_gpu = 4, 500
-    amps = synth.source_amplitudes(dt, n_gpu, f0=1.0, tau=0.25, t0=0.75)
-    # start where the pulse is strong so the short comparison is not trivial
-    shift = 300
-    ref = S.step(d, b, e, dt, n_ref, jhat=jhat, amps=amps[shift:shift + n_ref])
-    got = _run_gpu(ctx, d, b, e, dt, n_ref, jhat=jhat, amps=amps[shift:shift + n_ref])
-    for g, w in zip(got, ref):
-        assert rel_l2(to_host(g), w) < 1e-11
-    got = _run_gpu(ctx, d, b, e, dt, n_gpu, jhat=jhat, amps=amps)
+    c = _curved_case(CURVED_STEPS)
+    S, dt, amps = c["S"], c["dt"], c["amps"]
+    ctx = smx.Context(3, 32, geometry="sine_bump", amplitude=0.05, eps=c["bumps"]).bind()
+    got = _run_gpu(ctx, c["d"], c["b"], c["e"], dt, CURVED_STEPS, jhat=c["jhat"], amps=amps)
+    errs = [rel_l2(to_host(g), w) for g, w in zip(got, c["ref"])]
+    print("\ncurved 32^3 FP64 vs oracle after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e" % (CURVED_STEPS, *errs))
+    assert max(errs) < 1e-11
     D2, Dt2 = forms3d.div_matrix("B", S.p, S.nel), forms3d.div_matrix("D", S.p, S.nel)
     dn, bn = to_host(got[0]), to_host(got[1])
     scale = np.abs(dn).max()
     assert scale > 0
     assert np.abs(D2 @ bn).max() <= 1e-12 * max(np.abs(bn).max(), 1.0)
-    expected = -dt * amps.sum() * (Dt2 @ jhat)
+    expected = -dt * amps.sum() * (Dt2 @ c["jhat"])
     assert np.abs(Dt2 @ dn - expected).max() <= 1e-11 * max(np.abs(expected).max(), scale)
 
 
-def test_curved_p3_32cube_pulse_mixed():
-    """The curved configuration in mixed precision: 4 steps against the FP64 oracle (1e-5), then
-    500 steps against the FP64 GPU path on the same pulse, with the discrete Gauss law of B kept.
-    Over the 500 driven steps the electric 1-form reaches a relative L2 difference of about 1.3e-5
-    (the other fields stay below 1e-5): FP32 data rounding in every stage accumulates over the
-    run, above the 1e-5 target for this one field; the bound asserted here is 2e-5."""
-    import torch
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["mixed_refined", "mixed"])
+def test_curved_p3_32cube_pulse_mixed(precision):
+    """Config 2 in both mixed forms against the FP64 oracle after all 500 driven steps, with the
+    drift of W (evaluated in FP64) stated.  The refined form (one refinement sweep of each
+    Kronecker solve with an FP64 residual, FP64 star outputs) meets the 1e-5 contract.  The plain
+    FP32 form (FP32 star outputs, no refinement: the faster variant) reaches about 1.3e-5 on the
+    electric 1-form here, above the contract: its bound is stated as 2e-5."""
     from paper_2302_04979_gb300 import smx
-    bumps = synth.GaussianBumps(2302)
-    S = mx.Scheme2(3, 32, geometry=hodge.SineBumpMap(0.05), eps=bumps)
-    ctx64 = smx.Context(3, 32, geometry="sine_bump", amplitude=0.05, eps=bumps).bind()
-    ctx = smx.Context(3, 32, geometry="sine_bump", amplitude=0.05, eps=bumps, precision="mixed").bind()
-    jhat = S.project_2form("D", synth.pulse_profile(synth.pulse_centre(2302), 0.05), rtol=1e-10)
-    d, b, e = np.zeros(S.N_e), np.zeros(S.N_h), np.zeros(S.N_e)
-    dt, n_ref, n_gpu, shift = 0.003, 4, 500, 300
-    amps = synth.source_amplitudes(dt, n_gpu, f0=1.0, tau=0.25, t0=0.75)
-    # a state with the pulse already radiating, from the FP64 GPU path
-    st = _run_gpu(ctx64, d, b, e, dt, shift, jhat=jhat, amps=amps[:shift])
-    d1, b1, e1 = (to_host(t) for t in st[:3])
-    ref = S.step(d1, b1, e1, dt, n_ref, jhat=jhat, amps=amps[shift:shift + n_ref])
-    got = _run_gpu(ctx, d1, b1, e1, dt, n_ref, jhat=jhat, amps=amps[shift:shift + n_ref])
-    errs = [rel_l2(to_host(g), w) for g, w in zip(got, ref)]
-    print("\ncurved 32^3 mixed, 4 steps vs oracle: rel L2 d %.2e b %.2e e %.2e h %.2e" % tuple(errs))
-    assert max(errs) < 1e-5
-    g64 = _run_gpu(ctx64, d, b, e, dt, n_gpu, jhat=jhat, amps=amps)
-    gmx = _run_gpu(ctx, d, b, e, dt, n_gpu, jhat=jhat, amps=amps)
-    errs = [rel_l2(to_host(x), to_host(y)) for x, y in zip(gmx, g64)]
-    W64 = ctx64.energy(g64[0], g64[1], g64[2], dt)[1]
-    Wmx = ctx64.energy(gmx[0], gmx[1], gmx[2], dt)[1]
-    print("curved 32^3 mixed vs FP64 after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W %.6e vs %.6e"
-          % (n_gpu, *errs, Wmx, W64))
-    assert max(errs) < 2e-5
+    c = _curved_case(CURVED_STEPS)
+    S, dt = c["S"], c["dt"]
+    ctx = smx.Context(3, 32, geometry="sine_bump", amplitude=0.05, eps=c["bumps"], precision=precision).bind()
+    got = _run_gpu(ctx, c["d"], c["b"], c["e"], dt, CURVED_STEPS, jhat=c["jhat"], amps=c["amps"])
+    errs = [rel_l2(to_host(g), w) for g, w in zip(got, c["ref"])]
+    W_ref = S.energy(*c["ref"][:3], dt)[1]
+    W_got = S.energy(to_host(got[0]), to_host(got[1]), to_host(got[2]), dt)[1]
+    print("\ncurved 32^3 %s vs oracle after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W %.9e vs %.9e (rel %.2e)"
+          % (precision, CURVED_STEPS, *errs, W_got, W_ref, abs(W_got - W_ref) / abs(W_ref)))
+    assert max(errs) < (1e-5 if precision == "mixed_refined" else 2e-5)
     D2 = forms3d.div_matrix("B", S.p, S.nel)
-    bn = to_host(gmx[1])
+    bn = to_host(got[1])
     assert np.abs(D2 @ bn).max() <= 1e-6 * max(np.abs(bn).max(), 1.0)
 
 
-def _big_case(p):
-    eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
-    return eps, mx.Scheme2(p, 64, eps=eps)
+def _big_case(p, nsteps):
+    """The benchmark workload (p=3) and config 3 (p=4): 64^3, permittivity on 8^3 seeded blocks in
+    [1, 9), random d, divergence-free random b; the oracle's fields after nsteps steps."""
+    key = ("big", p, nsteps)
+    if key not in _CACHE:
+        eps = ("blocks", synth.block_material(2302, (8, 8, 8), 1.0, 9.0))
+        S = mx.Scheme2(p, 64, eps=eps)
+        d = synth.uniform(2303, S.N_e, -1.0, 1.0)
+        b = S.D1 @ synth.uniform(2304, S.N_e, -1.0, 1.0)
+        e = S.e_from_d(d)
+        # about 0.55 x CFL: the oracle's CFL at 16^3 is 0.0145 (p=3) and 0.0086 (p=4), linear in h
+        dt = 2e-3 if p == 3 else 1.2e-3
+        ref = S.step(d, b, e, dt, nsteps)
+        _CACHE[key] = dict(S=S, eps=eps, d=d, b=b, e=e, dt=dt, ref=ref)
+    return _CACHE[key]
+
+
+BIG_STEPS = {3: 50, 4: 25}
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("p", [3, 4])
 def test_64cube_block_eps(p):
+    """Every field against the oracle after 50 (p=3, the benchmark workload) and 25 (p=4) steps
+    (1e-11), with the default line operators and with the banded recurrences; then 1000 GPU steps
+    with W conserved to round-off."""
     from paper_2302_04979_gb300 import smx
-    eps, S = _big_case(p)
-    ctx = smx.Context(p, 64, eps=eps).bind()
-    d = synth.uniform(2303, S.N_e, -1.0, 1.0)
-    b = S.D1 @ synth.uniform(2304, S.N_e, -1.0, 1.0)
-    e = S.e_from_d(d)
-    # about 0.55 x CFL: the oracle's CFL at 16^3 is 0.0145 (p=3) and 0.0086 (p=4), linear in h
-    dt = 2e-3 if p == 3 else 1.2e-3
-    ref = S.step(d, b, e, dt, 2)
-    got = _run_gpu(ctx, d, b, e, dt, 2)
-    for g, w in zip(got, ref):
-        assert rel_l2(to_host(g), w) < 1e-11
+    n = BIG_STEPS[p]
+    c = _big_case(p, n)
+    ctx = smx.Context(p, 64, eps=c["eps"]).bind()
+    for kernel in ("auto", "simt"):
+        ctx.set_mode_kernel(kernel)
+        got = _run_gpu(ctx, c["d"], c["b"], c["e"], c["dt"], n)
+        errs = [rel_l2(to_host(g), w) for g, w in zip(got, c["ref"])]
+        print("\n64^3 p=%d FP64 (%s) vs oracle after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e"
+              % (p, kernel, n, *errs))
+        assert max(errs) < 1e-11
+    ctx.set_mode_kernel("auto")
+    d, b, e, dt = c["d"], c["b"], c["e"], c["dt"]
     E0, W0 = ctx.energy(to_dev(d), to_dev(b), to_dev(e), dt)
     got = _run_gpu(ctx, d, b, e, dt, 1000)
     E1, W1 = ctx.energy(got[0], got[1], got[2], dt)
     assert abs(W1 - W0) <= 1e-12 * W0
     assert np.isfinite(E1) and E1 < 10 * E0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["mixed", "mixed_refined"])
+def test_64cube_mixed_against_oracle(precision):
+    """The benchmark workload in both mixed forms against the oracle after 50 steps (1e-5), W drift
+    (in FP64) stated."""
+    from paper_2302_04979_gb300 import smx
+    n = BIG_STEPS[3]
+    c = _big_case(3, n)
+    ctx = smx.Context(3, 64, eps=c["eps"], precision=precision).bind()
+    got = _run_gpu(ctx, c["d"], c["b"], c["e"], c["dt"], n)
+    errs = [rel_l2(to_host(g), w) for g, w in zip(got, c["ref"])]
+    S = c["S"]
+    W0 = S.energy(c["d"], c["b"], c["e"], c["dt"])[1]
+    W1 = S.energy(to_host(got[0]), to_host(got[1]), to_host(got[2]), c["dt"])[1]
+    print("\n64^3 p=3 %s vs oracle after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W drift %.2e"
+          % (precision, n, *errs, abs(W1 - W0) / W0))
+    assert max(errs) < 1e-5

@@ -3,7 +3,9 @@
 The contract for this form is a relative L2 error of at most 1e-5 per field
 against the FP64 oracle after the stated step count, with the drift of the
 conserved energy W stated.  The errors measured here are printed (pytest -s)
-and asserted against that bound.
+and asserted against that bound.  Both mixed forms are covered: "mixed" (FP32
+stars) and "mixed_refined" (each Kronecker solve refined once with an FP64
+residual, FP64 star outputs); the refined star must also be markedly closer.
 """
 import numpy as np
 import pytest
@@ -38,9 +40,12 @@ def _scheme(case):
     return mx.Scheme2(case["p"], case["nel"], geometry=geom, eps=case.get("eps", 1.0), mu=case.get("mu", 1.0))
 
 
-def _context(smx, case):
+def _context(smx, case, precision="mixed"):
     return smx.Context(case["p"], case["nel"], geometry=case.get("geometry", "identity"), eps=case.get("eps", 1.0),
-                       mu=case.get("mu", 1.0), precision="mixed").bind()
+                       mu=case.get("mu", 1.0), precision=precision).bind()
+
+
+PRECISIONS = ("mixed", "mixed_refined")
 
 
 def _setup(case):
@@ -59,16 +64,17 @@ def _setup(case):
 KERNELS = ("tensor", "simt")
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_mixed_against_oracle(name, kernel):
+def test_mixed_against_oracle(name, kernel, precision):
     import torch
     from paper_2302_04979_gb300 import smx
     case = CASES[name]
     S, d, b, e, dt = _setup(case)
     n = case["steps"]
     ref = S.step(d, b, e, dt, n)
-    ctx = _context(smx, case)
+    ctx = _context(smx, case, precision)
     ctx.set_mode_kernel(kernel)
     dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
     hd = torch.zeros(S.N_h, dtype=torch.float64, device="cuda")
@@ -77,27 +83,30 @@ def test_mixed_against_oracle(name, kernel):
     errs = [rel_l2(to_host(g), w) for g, w in zip((dd, bd, ed, hd), ref)]
     W0 = S.energy(d, b, e, dt)[1]
     W1 = S.energy(to_host(dd), to_host(bd), to_host(ed), dt)[1]
-    print("\n%s mixed (%s) after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W drift %.2e"
-          % (name, kernel, n, *errs, abs(W1 - W0) / W0))
+    print("\n%s %s (%s) after %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; W drift %.2e"
+          % (name, precision, kernel, n, *errs, abs(W1 - W0) / W0))
     assert max(errs) < 1e-5
     assert abs(W1 - W0) / W0 < 1e-5
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_mixed_hodge_star_against_oracle(name, kernel):
+def test_mixed_hodge_star_against_oracle(name, kernel, precision):
     """One mixed-precision Hodge star (K_1^{-1} M~ d and K~_1^{-1} M b) against the oracle's FP64 one.
 
     Every stage rounds its data to FP32 once (the CUDA-core operators carry FP64 accuracy in
     their (hi, lo) terms; the tensor-core digit products are exact on 31-bit fixed-point lines
-    and round once), so one star stays within a few FP32 roundings: 2e-6."""
+    and round once), so one star stays within a few FP32 roundings: 2e-6.  The refined star
+    removes the solve's rounding (FP64 residual, one FP32 correction, FP64 output); what is
+    left is the FP32 arithmetic of the mass apply: 1e-6 (5e-8 to 5e-7 measured)."""
     import torch
     from paper_2302_04979_gb300 import smx
     case = CASES[name]
     S = _scheme(case)
     d = synth.uniform(80, S.N_e, -1.0, 1.0)
     b = synth.uniform(81, S.N_h, -1.0, 1.0)
-    ctx = _context(smx, case)
+    ctx = _context(smx, case, precision)
     ctx.set_mode_kernel(kernel)
     e_dev = torch.empty(S.N_e, dtype=torch.float64, device="cuda")
     h_dev = torch.empty(S.N_h, dtype=torch.float64, device="cuda")
@@ -105,8 +114,9 @@ def test_mixed_hodge_star_against_oracle(name, kernel):
     ctx.hodge_star_mixed(smx.FIELD_B, to_dev(b), h_dev)
     ctx.device_status()
     ee, eh = rel_l2(to_host(e_dev), S.e_from_d(d)), rel_l2(to_host(h_dev), S.h_from_b(b))
-    print("\n%s mixed star (%s): rel L2 e %.2e h %.2e" % (name, kernel, ee, eh))
-    assert ee < 2e-6 and eh < 2e-6
+    print("\n%s %s star (%s): rel L2 e %.2e h %.2e" % (name, precision, kernel, ee, eh))
+    bound = 1e-6 if precision == "mixed_refined" else 2e-6
+    assert ee < bound and eh < bound
 
 
 def test_mixed_kernels_agree_at_64cube():
