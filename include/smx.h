@@ -51,6 +51,16 @@ extern "C" {
 /* ---- geometry map F : (0,1)^3 -> Omega (Sec. 2.3) ---- */
 #define SMX_GEOM_IDENTITY 0  /* F = identity: the unit-cube cavity of Sec. 5.1.1 */
 #define SMX_GEOM_SINE_BUMP 1 /* F_i = x_i + a sin(pi x) sin(pi y) sin(pi z), a = geom_amplitude */
+#define SMX_GEOM_CALLBACK 2  /* a general single-patch map given by the host callback geom_fn (Sec. 2.3) */
+
+/* Host callback of SMX_GEOM_CALLBACK: for i < n, the map F at the parametric
+ * point (xhat[3i], xhat[3i+1], xhat[3i+2]) in (0,1)^3 into x[3i + r] = F_r and
+ * its Jacobian into jac[9i + 3r + c] = dF_r / dxhat_c.  Called inside
+ * smx_create (at every quadrature point, a few calls of many points) and
+ * smx_project; det J_F must be positive and every value finite there
+ * (SMX_EGEOM otherwise).  A map that is not the identity always takes the
+ * quadrature Hodge (sum-factorised, metric w J^T J / det J stored per point). */
+typedef void (*smx_geometry_fn)(int64_t n, const double* xhat, double* x, double* jac, void* user);
 
 /* ---- material description (eps or mu) ---- */
 #define SMX_MAT_CONST 0      /* one value everywhere */
@@ -84,6 +94,8 @@ typedef struct {
     smx_material eps;      /* permittivity: weights M~^2_{1/eps} (Eq. discrete2_hodge_eps) */
     smx_material mu;       /* permeability: weights M^2_{1/mu} (Eq. discrete2_hodge_mu) */
     int precision;         /* SMX_FP64, SMX_MIXED or SMX_MIXED_REFINED: arithmetic of smx_step / smx_step_host */
+    smx_geometry_fn geom_fn; /* SMX_GEOM_CALLBACK: the map (must stay callable while smx_project may be called) */
+    void* geom_user;         /* passed to geom_fn */
 } smx_params;
 
 /* ---- precision of the leapfrog step ----

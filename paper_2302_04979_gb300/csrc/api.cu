@@ -84,6 +84,7 @@ struct smx_ctx {
     int p[3], nel[3];
     int geometry;
     double amp;
+    GeomMap gmap;  // the map F (built-in or host callback)
     DevField fld[4];
     long long N_e, N_h;
     BandLU fac[3][4];  // per axis: G, M, G^T, M^T
@@ -331,21 +332,23 @@ int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
     H.Qtot = (long long)H.Qn[0] * H.Qn[1] * H.Qn[2];
     const long long Q = H.Qtot;
     std::vector<double> X3(3 * Q), Jall(9 * Q), wdet(Q);
-    for (long long qi = 0; qi < Q; ++qi) {
-        const int ix = (int)(qi % H.Qn[0]);
-        const int iy = (int)((qi / H.Qn[0]) % H.Qn[1]);
-        const int iz = (int)(qi / ((long long)H.Qn[0] * H.Qn[1]));
-        const int ii[3] = {ix, iy, iz};
-        double xh[3], w = 1.0;
-        for (int a = 0; a < 3; ++a) {
-            const int e = ii[a] / H.q[a], k = ii[a] % H.q[a];
-            xh[a] = (e + gx[a][k]) / C->nel[a];
-            w *= gw[a][k] / C->nel[a];
+    {
+        std::vector<double> xh(3 * Q);
+        for (long long qi = 0; qi < Q; ++qi) {
+            const int ii[3] = {(int)(qi % H.Qn[0]), (int)((qi / H.Qn[0]) % H.Qn[1]),
+                               (int)(qi / ((long long)H.Qn[0] * H.Qn[1]))};
+            double w = 1.0;
+            for (int a = 0; a < 3; ++a) {
+                const int e = ii[a] / H.q[a], k = ii[a] % H.q[a];
+                xh[3 * qi + a] = (e + gx[a][k]) / C->nel[a];
+                w *= gw[a][k] / C->nel[a];
+            }
+            wdet[qi] = w;
         }
-        geometry_eval(C->geometry, C->amp, xh, &X3[3 * qi], &Jall[9 * qi]);
-        const double dj = det3(&Jall[9 * qi]);
-        if (!(dj > 0.0) || !std::isfinite(dj)) return SMX_EGEOM;
-        wdet[qi] = w / dj;
+        // F and J_F at every quadrature point (one callback call for a host map); det J_F > 0 checked
+        const int st = geometry_eval_points(C->gmap, Q, xh.data(), X3.data(), Jall.data());
+        if (st) return st;
+        for (long long qi = 0; qi < Q; ++qi) wdet[qi] /= det3(&Jall[9 * qi]);
     }
     std::vector<double> mat(Q);
     if (m.kind == SMX_MAT_POINTWISE) {
@@ -830,7 +833,9 @@ int smx_create(const smx_params* P, smx_ctx** out) {
         if (P->p[a] < 2 || P->p[a] > kPMax) return SMX_EINVAL;
         if (P->nel[a] < 1 || P->nel[a] > 800) return SMX_EINVAL;
     }
-    if (P->geometry != SMX_GEOM_IDENTITY && P->geometry != SMX_GEOM_SINE_BUMP) return SMX_EINVAL;
+    if (P->geometry != SMX_GEOM_IDENTITY && P->geometry != SMX_GEOM_SINE_BUMP && P->geometry != SMX_GEOM_CALLBACK)
+        return SMX_EINVAL;
+    if (P->geometry == SMX_GEOM_CALLBACK && !P->geom_fn) return SMX_EINVAL;
     if (!std::isfinite(P->geom_amplitude)) return SMX_EINVAL;
     int st = check_material(P->eps, P->nel);
     if (st) return st;
@@ -846,6 +851,10 @@ int smx_create(const smx_params* P, smx_ctx** out) {
         }
         C->geometry = P->geometry;
         C->amp = P->geom_amplitude;
+        C->gmap.kind = P->geometry;
+        C->gmap.amp = P->geom_amplitude;
+        C->gmap.fn = P->geometry == SMX_GEOM_CALLBACK ? P->geom_fn : nullptr;
+        C->gmap.user = P->geom_user;
         if (P->eps.kind == SMX_MAT_BLOCKS) {
             C->eps_blocks = true;
             for (int a = 0; a < 3; ++a) {
@@ -1387,7 +1396,7 @@ int smx_project(const smx_ctx* C, int field, smx_field_fn fn, void* user, double
     if (!C || !fn || !coeffs || (field != SMX_FIELD_B && field != SMX_FIELD_D)) return SMX_EINVAL;
     try {
         int iters = 0;
-        return l2_project_2form(C->p, C->nel, C->geometry, C->amp, field, fn, user, coeffs, 1e-14, 500, &iters);
+        return l2_project_2form(C->p, C->nel, C->gmap, field, fn, user, coeffs, 1e-14, 500, &iters);
     } catch (const std::bad_alloc&) {
         return SMX_ENOMEM;
     }

@@ -34,8 +34,7 @@ struct Comp {
 };
 
 struct Space {
-    int p[3], nel[3], geom;
-    double amp;
+    int p[3], nel[3];
     Comp c[3];
     long long total;
     Axis1D ax[3];
@@ -43,7 +42,7 @@ struct Space {
     std::vector<double> bval[3][4];
 };
 
-void build_space(Space& S, const int p[3], const int nel[3], int geom, double amp, int field) {
+void build_space(Space& S, const int p[3], const int nel[3], int field) {
     for (int a = 0; a < 3; ++a) {
         S.p[a] = p[a];
         S.nel[a] = nel[a];
@@ -60,8 +59,6 @@ void build_space(Space& S, const int p[3], const int nel[3], int geom, double am
                 }
         }
     }
-    S.geom = geom;
-    S.amp = amp;
     long long off = 0;
     for (int c = 0; c < 3; ++c) {
         Comp& C = S.c[c];
@@ -146,7 +143,9 @@ void integrate_element(const Space& S, const int e[3], const double* const bas[3
 // component's local coefficients are interpolated to the element's q^3 points
 // by three 1D contractions, multiplied by w J^T J / det J there, and
 // integrated back by the transposed contractions.
-void mass_apply(const Space& S, const std::vector<double>& x, std::vector<double>& y) {
+// Gm: per quadrature point (slab order of for_slab_points, slabs along z in turn) the six
+// entries 00 01 02 11 12 22 of w J^T J / det J.
+void mass_apply(const Space& S, const std::vector<double>& Gm, const std::vector<double>& x, std::vector<double>& y) {
     std::fill(y.begin(), y.end(), 0.0);
     const int qx = S.ax[0].q, qy = S.ax[1].q, qz = S.ax[2].q, nq = qx * qy * qz;
     constexpr int R = kRMax;  // largest local count per axis (p + 1)
@@ -193,24 +192,18 @@ void mass_apply(const Space& S, const std::vector<double>& x, std::vector<double
                             }
                 }
                 // the metric at every point of the element
+                const long long slab = (long long)S.nel[0] * qx * S.nel[1] * qy * qz;
                 for (int kz = 0; kz < qz; ++kz)
                     for (int ky = 0; ky < qy; ++ky)
                         for (int kx = 0; kx < qx; ++kx) {
-                            const double xh[3] = {(ex + S.ax[0].x[kx]) / S.nel[0], (ey + S.ax[1].x[ky]) / S.nel[1],
-                                                  (ez + S.ax[2].x[kz]) / S.nel[2]};
-                            const double w = S.ax[0].w[kx] / S.nel[0] * S.ax[1].w[ky] / S.nel[1] * S.ax[2].w[kz] /
-                                             S.nel[2];
-                            double X[3], J[9];
-                            geometry_eval(S.geom, S.amp, xh, X, J);
-                            const double sc = w / det3(J);
+                            const long long pt = ez * slab + (((long long)kz * S.nel[1] + ey) * qy + ky) *
+                                                                 ((long long)S.nel[0] * qx) + ex * qx + kx;
+                            const double* g = &Gm[6 * pt];
                             const size_t qi = (size_t)(kz * qy + ky) * qx + kx;
                             const double u[3] = {U[qi], U[nq + qi], U[2 * (size_t)nq + qi]};
-                            for (int i = 0; i < 3; ++i) {
-                                double acc = 0.0;
-                                for (int j = 0; j < 3; ++j)
-                                    acc += (J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j]) * u[j];
-                                U[(size_t)i * nq + qi] = sc * acc;  // u was copied: overwrite in place
-                            }
+                            U[qi] = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];  // u was copied: overwrite in place
+                            U[nq + qi] = g[1] * u[0] + g[3] * u[1] + g[4] * u[2];
+                            U[2 * (size_t)nq + qi] = g[2] * u[0] + g[4] * u[1] + g[5] * u[2];
                         }
                 integrate_element(S, e, bas, U.data(), y, t1.data(), t2.data());
             }
@@ -277,23 +270,40 @@ double dot(const std::vector<double>& a, const std::vector<double>& b) {
 
 }  // namespace
 
-int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int field, project_fn fn, void* user,
+int l2_project_2form(const int p[3], const int nel[3], const GeomMap& geom, int field, project_fn fn, void* user,
                      double* out, double rtol, int maxit, int* iters) {
     Space S;
-    build_space(S, p, nel, geom, amp, field);
+    build_space(S, p, nel, field);
     const long long N = S.total;
-    // right-hand side, one callback per slab of elements along z
-    std::vector<double> r(N, 0.0), X3, V3;
+    // right-hand side, one callback (and one geometry evaluation) per slab of elements along z;
+    // the metric w J^T J / det J of every point is kept for the mass applies
+    const long long slab_pts = (long long)S.nel[0] * S.ax[0].q * S.nel[1] * S.ax[1].q * S.ax[2].q;
+    std::vector<double> Gm(6 * slab_pts * S.nel[2]);
+    std::vector<double> r(N, 0.0), X3, V3, XH, J3;
     std::vector<double> U(3 * (size_t)S.ax[0].q * S.ax[1].q * S.ax[2].q), t1((size_t)kRMax * kRMax * 16),
         t2((size_t)kRMax * 16 * 16);
     for (int ez = 0; ez < S.nel[2]; ++ez) {
-        X3.clear();
-        for_slab_points(S, ez, [&](const double* xh, double, const int*, const int*) {
-            double X[3], J[9];
-            geometry_eval(S.geom, S.amp, xh, X, J);
-            X3.insert(X3.end(), X, X + 3);
-        });
-        const long long n = (long long)X3.size() / 3;
+        XH.clear();
+        for_slab_points(S, ez, [&](const double* xh, double, const int*, const int*) { XH.insert(XH.end(), xh, xh + 3); });
+        const long long n = (long long)XH.size() / 3;
+        X3.assign(3 * n, 0.0);
+        J3.assign(9 * n, 0.0);
+        const int gst = geometry_eval_points(geom, n, XH.data(), X3.data(), J3.data());
+        if (gst) return gst;
+        {
+            long long pt = 0;
+            for_slab_points(S, ez, [&](const double*, double w, const int*, const int*) {
+                const double* J = &J3[9 * pt];
+                const double sc = w / det3(J);
+                double* g = &Gm[6 * (ez * slab_pts + pt)];
+                const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+                for (int k = 0; k < 6; ++k) {
+                    const int i = ij[k][0], j = ij[k][1];
+                    g[k] = sc * (J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j]);
+                }
+                ++pt;
+            });
+        }
         V3.assign(3 * n, 0.0);
         fn(n, X3.data(), V3.data(), user);
         for (long long i = 0; i < 3 * n; ++i)
@@ -306,14 +316,11 @@ int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int
                 for (int kz = 0; kz < qz; ++kz)
                     for (int ky = 0; ky < qy; ++ky)
                         for (int kx = 0; kx < qx; ++kx) {
-                            const double xh[3] = {(ex + S.ax[0].x[kx]) / S.nel[0], (ey + S.ax[1].x[ky]) / S.nel[1],
-                                                  (ez + S.ax[2].x[kz]) / S.nel[2]};
                             const double w = S.ax[0].w[kx] / S.nel[0] * S.ax[1].w[ky] / S.nel[1] * S.ax[2].w[kz] /
                                              S.nel[2];
-                            double X[3], J[9];
-                            geometry_eval(S.geom, S.amp, xh, X, J);
                             const long long pt =
                                 (((long long)kz * S.nel[1] + ey) * qy + ky) * ((long long)S.nel[0] * qx) + ex * qx + kx;
+                            const double* J = &J3[9 * pt];
                             const double* V = &V3[3 * pt];
                             const size_t qi = (size_t)(kz * qy + ky) * qx + kx;
                             for (int c = 0; c < 3; ++c)  // w (J^T V)_c
@@ -329,7 +336,7 @@ int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int
     // preconditioned conjugate gradients from x = P^{-1} r
     std::vector<double> x = r, res(N), z(N), d(N), Ad(N);
     kron_solve(S, K, x);
-    mass_apply(S, x, Ad);
+    mass_apply(S, Gm, x, Ad);
     for (long long i = 0; i < N; ++i) res[i] = r[i] - Ad[i];
     const double rnorm0 = std::sqrt(dot(r, r));
     int it = 0;
@@ -339,7 +346,7 @@ int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int
         d = z;
         double rz = dot(res, z);
         for (it = 1; it <= maxit; ++it) {
-            mass_apply(S, d, Ad);
+            mass_apply(S, Gm, d, Ad);
             const double alpha = rz / dot(d, Ad);
             for (long long i = 0; i < N; ++i) {
                 x[i] += alpha * d[i];

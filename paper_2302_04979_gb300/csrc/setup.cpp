@@ -227,6 +227,23 @@ double det3(const double J[9]) {
     return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
 }
 
+int geometry_eval_points(const GeomMap& g, int64_t n, const double* xh, double* X, double* J) {
+    if (g.kind == SMX_GEOM_CALLBACK) {
+        for (int64_t i = 0; i < 3 * n; ++i) X[i] = std::nan("");
+        for (int64_t i = 0; i < 9 * n; ++i) J[i] = std::nan("");
+        g.fn(n, xh, X, J, g.user);
+    } else {
+        for (int64_t i = 0; i < n; ++i) geometry_eval(g.kind, g.amp, xh + 3 * i, X + 3 * i, J + 9 * i);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(X[3 * i + k])) return SMX_EGEOM;
+        const double dj = det3(J + 9 * i);
+        if (!std::isfinite(dj) || !(dj > 0.0)) return SMX_EGEOM;
+    }
+    return SMX_OK;
+}
+
 // Round an FP32 value to BF16, nearest even (IEEE rounding on the 16 dropped bits).
 static uint16_t bf16_nearest(float f) {
     uint32_t u;

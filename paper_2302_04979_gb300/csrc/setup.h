@@ -53,6 +53,21 @@ std::vector<double> band_lu_dense(const BandLU& f);
 void geometry_eval(int geom, double a, const double xh[3], double X[3], double J[9]);
 double det3(const double J[9]);
 
+// A geometry map: one of the built-in maps (kind SMX_GEOM_IDENTITY, or
+// SMX_GEOM_SINE_BUMP with amplitude amp) or a host callback (SMX_GEOM_CALLBACK)
+// that fills x[3 i + r] = F_r and jac[9 i + 3 r + c] = dF_r / dxhat_c at the n
+// parametric points xh[3 i + c].
+typedef void (*geometry_fn)(int64_t n, const double* xh, double* x, double* jac, void* user);
+struct GeomMap {
+    int kind = 0;
+    double amp = 0.0;
+    geometry_fn fn = nullptr;
+    void* user = nullptr;
+};
+// F and J_F at n points (one callback call for a callback map).  Returns SMX_OK, or
+// SMX_EGEOM if a value is not finite or det J_F <= 0 at some point.
+int geometry_eval_points(const GeomMap& g, int64_t n, const double* xh, double* X, double* J);
+
 // L2 projection of a physical 2-form onto X~^2 (field SMX_FIELD_D) or X^2_{h,0}
 // (SMX_FIELD_B) (project.cpp): fn(n, xyz, out) fills out[3 i + c] with the
 // vector proxy at the physical points xyz[3 i ..]; out (host, the field's
@@ -60,7 +75,7 @@ double det3(const double J[9]);
 // Returns SMX_OK, SMX_ENONFINITE (fn gave a non-finite value) or
 // SMX_ESINGULAR (no convergence in maxit iterations).
 typedef void (*project_fn)(int64_t n, const double* xyz, double* out, void* user);
-int l2_project_2form(const int p[3], const int nel[3], int geom, double amp, int field, project_fn fn, void* user,
+int l2_project_2form(const int p[3], const int nel[3], const GeomMap& geom, int field, project_fn fn, void* user,
                      double* out, double rtol, int maxit, int* iters);
 
 // Element mass matrix of one kind on element e: (d+1) x (d+1), row-major,

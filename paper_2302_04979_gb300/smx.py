@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsmx.so")
 OK, EINVAL, EGEOM, EMAT, ECUDA, ENONFINITE, ESTATE, ENOMEM, ESINGULAR, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 ETIMEOUT = -10
 MODE_TENSOR, MODE_SIMT, MODE_AUTO = 0, 1, 2
-GEOM_IDENTITY, GEOM_SINE_BUMP = 0, 1
+GEOM_IDENTITY, GEOM_SINE_BUMP, GEOM_CALLBACK = 0, 1, 2
 MAT_CONST, MAT_BLOCKS, MAT_POINTWISE = 0, 1, 2
 FIELD_E, FIELD_B, FIELD_H, FIELD_D = 0, 1, 2, 3
 
@@ -30,6 +30,8 @@ MATERIAL_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.POINTER(ctypes.c_dou
 
 
 FIELD_FN = MATERIAL_FN  # smx_field_fn: the same C signature, 3 values per point
+GEOMETRY_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
 class Material(ctypes.Structure):
@@ -41,7 +43,7 @@ class Material(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int * 3), ("nel", ctypes.c_int * 3), ("geometry", ctypes.c_int),
                 ("geom_amplitude", ctypes.c_double), ("eps", Material), ("mu", Material),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("geom_fn", GEOMETRY_FN), ("geom_user", ctypes.c_void_p)]
 
 
 class SmxError(RuntimeError):
@@ -175,18 +177,42 @@ def material(spec):
 FP64, MIXED, MIXED_REFINED = 0, 1, 2
 
 
+def geometry_callback(mapping):
+    """smx_geometry_fn for a map object: mapping(X, Y, Z) -> (x, y, z) and mapping.jacobian(X, Y, Z)
+    -> J[r, c] = dF_r / dxhat_c (arrays over the points), as the seeded input maps provide."""
+    def cb(n, xh, x, jac, user):
+        pts = np.ctypeslib.as_array(xh, shape=(n, 3))
+        X = np.ctypeslib.as_array(x, shape=(n, 3))
+        J = np.ctypeslib.as_array(jac, shape=(n, 3, 3))
+        try:
+            F = mapping(pts[:, 0], pts[:, 1], pts[:, 2])
+            X[:] = np.stack([np.asarray(F[r], dtype=np.float64) * np.ones(n) for r in range(3)], axis=1)
+            D = np.asarray(mapping.jacobian(pts[:, 0], pts[:, 1], pts[:, 2]), dtype=np.float64)
+            J[:] = np.moveaxis(D * np.ones((3, 3, n)), 2, 0)
+        except Exception:  # reported as SMX_EGEOM by the library
+            X[:] = np.nan
+    return GEOMETRY_FN(cb)
+
+
 def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64"):
+    """geometry: "identity", "sine_bump" (amplitude) or a map object (see geometry_callback)."""
     P = Params()
     p = np.broadcast_to(np.asarray(p, dtype=int), (3,))
     nel = np.broadcast_to(np.asarray(nel, dtype=int), (3,))
     for a in range(3):
         P.p[a], P.nel[a] = int(p[a]), int(nel[a])
-    P.geometry = {"identity": GEOM_IDENTITY, "sine_bump": GEOM_SINE_BUMP}[geometry]
+    keep = []
+    if isinstance(geometry, str):
+        P.geometry = {"identity": GEOM_IDENTITY, "sine_bump": GEOM_SINE_BUMP}[geometry]
+    else:
+        P.geometry = GEOM_CALLBACK
+        P.geom_fn = geometry_callback(geometry)
+        keep.append(P.geom_fn)
     P.geom_amplitude = float(amplitude)
     P.eps, k1 = material(eps)
     P.mu, k2 = material(mu)
     P.precision = {"fp64": FP64, "mixed": MIXED, "mixed_refined": MIXED_REFINED}[precision]
-    return P, k1 + k2
+    return P, keep + k1 + k2
 
 
 class Context:
@@ -197,6 +223,8 @@ class Context:
         P, keep = make_params(p, nel, geometry, amplitude, eps, mu, precision)
         h = ctypes.c_void_p()
         _check(lib.smx_create(ctypes.byref(P), ctypes.byref(h)), "smx_create")
+        # a geometry callback is called again by smx_project: keep it alive with the context
+        self._geometry_fn = keep[0] if not isinstance(geometry, str) else None
         del keep
         self.h = h
         ne, nh = ctypes.c_int64(), ctypes.c_int64()

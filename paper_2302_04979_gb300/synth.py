@@ -95,3 +95,37 @@ def bump_coefficients(seed, comp_shapes, comp=2, width=0.05):
         r2 = (x - x0[0]) ** 2 + (y - x0[1]) ** 2 + (z - x0[2]) ** 2
         parts.append(np.exp(-r2 / (2.0 * width ** 2)).reshape(-1))
     return np.concatenate(parts)
+
+
+class SineBumpMap:
+    """The curved configuration's map F_i(x) = x_i + a sin(pi x) sin(pi y) sin(pi z) (maps the unit
+    cube onto itself) and its Jacobian J[r, c] = dF_r/dx_c, as an input for a host-callback map."""
+
+    def __init__(self, amplitude=0.05):
+        self.a = float(amplitude)
+
+    def __call__(self, x, y, z):
+        s = np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        return x + self.a * s, y + self.a * s, z + self.a * s
+
+    def jacobian(self, x, y, z):
+        x, y, z = np.broadcast_arrays(np.asarray(x, dtype=np.float64), y, z)
+        g = [np.pi * np.cos(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z),
+             np.pi * np.sin(np.pi * x) * np.cos(np.pi * y) * np.sin(np.pi * z),
+             np.pi * np.sin(np.pi * x) * np.sin(np.pi * y) * np.cos(np.pi * z)]
+        return np.array([[(1.0 if r == c else 0.0) + self.a * g[c] for c in range(3)] for r in range(3)])
+
+
+class ShearMap:
+    """A smooth map of the unit cube onto a sheared, bent, squeezed hexahedral domain (not the cube):
+    F = (x + 0.2 y z, y + 0.1 sin(pi x), 0.8 z + 0.1 x y), det J >= 0.73 on [0, 1]^3."""
+
+    def __call__(self, x, y, z):
+        return x + 0.2 * y * z, y + 0.1 * np.sin(np.pi * x), 0.8 * z + 0.1 * x * y
+
+    def jacobian(self, x, y, z):
+        x, y, z = np.broadcast_arrays(np.asarray(x, dtype=np.float64), y, z)
+        one, zero = np.ones_like(x), np.zeros_like(x)
+        return np.array([[one, 0.2 * z, 0.2 * y],
+                         [0.1 * np.pi * np.cos(np.pi * x), one, zero],
+                         [0.1 * y, 0.1 * x, 0.8 * one]])
