@@ -173,12 +173,12 @@ __device__ __forceinline__ uint32_t top_digit_f32(unsigned long long u) {
 }
 
 // acc * 2^e2 rounded to the nearest double (ties to even), by integer
-// instructions while the result is a normal number.
-__device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
-    if (acc == 0) return 0.0;
-    const unsigned long long sgn = acc < 0 ? (1ull << 63) : 0ull;
+// instructions while the result is a normal number.  The significand m keeps its
+// leading bit (2^52 <= m <= 2^53), so adding it to (biased exponent - 1) << 52
+// lets a rounding carry (m = 2^53) step the exponent by itself.
+__device__ __noinline__ double scaled_to_double_slow(long long acc, int e2) {
     const unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
-    int pb = 63 - __clzll((long long)a);  // leading bit
+    int pb = 63 - __clzll((long long)a);
     unsigned long long m;
     if (pb <= 52) {
         m = a << (52 - pb);
@@ -194,44 +194,49 @@ __device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
             }
         }
     }
-    const int be = pb + e2 + 1023;  // biased exponent of the result
-    if (be >= 1 && be <= 2046)
-        return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
     // outside the normal range: exact m times 2^k in two power-of-two factors
     const int k = pb - 52 + e2;
     const int k1 = max(-1022, min(1023, k / 2)), k2 = max(-1022, min(1023, k - k1));
     const double f1 = __longlong_as_double((long long)(k1 + 1023) << 52);
     const double f2 = __longlong_as_double((long long)(k2 + 1023) << 52);
     const double v = (double)(long long)m * f1 * f2;
-    return sgn ? -v : v;
+    return acc < 0 ? -v : v;
 }
 
+__device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
+    if (acc == 0) return 0.0;
+    const unsigned long long a = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+    const int lz = __clzll((long long)a);
+    unsigned long long m;
+    if (lz >= 11) {
+        m = a << (lz - 11);
+    } else {
+        const int sh = 11 - lz;  // round half to even: add half - 1, plus 1 when the kept part is odd
+        m = (a + ((1ull << (sh - 1)) - 1) + ((a >> sh) & 1ull)) >> sh;
+    }
+    const int be = 63 - lz + e2 + 1023;  // biased exponent without a rounding carry
+    if (be < 1 || be + (int)(m >> 53) > 2046) return scaled_to_double_slow(acc, e2);
+    const unsigned long long bits = ((unsigned long long)(be - 1) << 52) + m;
+    return __longlong_as_double((long long)(bits | ((unsigned long long)acc & (1ull << 63))));
+}
 
-// acc * 2^e2 rounded to the nearest float (ties to even), by integer
-// instructions while the result is a normal number (else through FP64).
+// acc * 2^e2 rounded to the nearest float (ties to even), the same way (through the
+// double routine outside the normal range).
 __device__ __forceinline__ float scaled_to_float(long long acc, int e2) {
     if (acc == 0) return 0.0f;
-    const uint32_t sgn = acc < 0 ? 0x80000000u : 0u;
-    const unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
-    int pb = 63 - __clzll((long long)a);
+    const unsigned long long a = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+    const int lz = __clzll((long long)a);
     unsigned long long m;
-    if (pb <= 23) {
-        m = a << (23 - pb);
+    if (lz >= 40) {
+        m = a << (lz - 40);
     } else {
-        const int sh = pb - 23;
-        m = a >> sh;
-        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (m & 1ull))) {
-            m += 1;
-            if (m >> 24) {
-                m >>= 1;
-                pb += 1;
-            }
-        }
+        const int sh = 40 - lz;
+        m = (a + ((1ull << (sh - 1)) - 1) + ((a >> sh) & 1ull)) >> sh;
     }
-    const int be = pb + e2 + 127;
-    if (be >= 1 && be <= 254) return __uint_as_float(sgn | ((uint32_t)be << 23) | ((uint32_t)m & 0x7FFFFFu));
-    return (float)scaled_to_double(acc, e2);
+    const int be = 63 - lz + e2 + 127;
+    if (be < 1 || be + (int)(m >> 24) > 254) return (float)scaled_to_double(acc, e2);
+    const uint32_t bits = ((uint32_t)(be - 1) << 23) + (uint32_t)m;
+    return __uint_as_float(bits | (acc < 0 ? 0x80000000u : 0u));
 }
 
 // Output of a tile entry: FP64, or FP32 with an optional exact FP64 copy.
@@ -459,24 +464,32 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         // addresses: entries of one line along x, consecutive lines along y and z
         const int nl = min(NL, nlines - l0);
         const int total = axis == 0 ? n * nl : n * NL;
-        for (int g = tid; g < total; g += THREADS) {
-            int ii, col;
-            if (axis == 0) {
-                col = g / n;
-                ii = g - col * n;
-            } else {
-                ii = g / NL;
-                col = g - ii * NL;
-                if (col >= nl) continue;
+        // four independent values per iteration: each rounding is a long chain of dependent
+        // integer instructions, and interleaving four chains hides their latency
+        constexpr int kU = 4;
+        for (int g0 = tid; g0 < total; g0 += kU * THREADS) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int g = g0 + u * THREADS;
+                int ii, col;
+                if (axis == 0) {
+                    col = g / n;
+                    ii = g - col * n;
+                } else {
+                    ii = g / NL;
+                    col = g - ii * NL;
+                }
+                if (g < total && col < nl) {
+                    const int L = l0 + col;
+                    const int e2 = 8 * ND + sRowE[ii] - 1075 - kTopOp + digit_scale<TIN, ND>(sExp[col]);
+                    const TOUT y = digit_out(sAcc[ii * (NL + 1) + col], e2, (TOUT*)nullptr);
+                    const long long o = axis == 0 ? (long long)L * n + ii
+                                                  : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L) +
+                                                        (long long)ii * stride;
+                    dst[o] = y;
+                    if (dst64) dst64[o] = f2d_exact(y);
+                }
             }
-            const int L = l0 + col;
-            const int e2 = 8 * ND + sRowE[ii] - 1075 - kTopOp + digit_scale<TIN, ND>(sExp[col]);
-            const TOUT y = digit_out(sAcc[ii * (NL + 1) + col], e2, (TOUT*)nullptr);
-            const long long o = axis == 0 ? (long long)L * n + ii
-                                          : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L) +
-                                                (long long)ii * stride;
-            dst[o] = y;
-            if (dst64) dst64[o] = f2d_exact(y);
         }
     }
     tc_fence_before();

@@ -12,11 +12,15 @@ rational arithmetic and check the claims the kernels rely on:
   entries, so an FP32 accumulator holds it exactly;
 * the result, rounded once, is within a few units of 2^-53 of
   max|x| sum|B| + max|B| sum|x| (seven digits), or of 2^-24 (four digits,
-  FP32 output), also for lines whose entries span many orders of magnitude.
+  FP32 output), also for lines whose entries span many orders of magnitude;
+* the kernels' integer rounding of the final accumulator to FP64 or FP32 is
+  exact round-to-nearest-even.
 
 The GPU parity tests (tests/test_gpu_digit.py, tests/test_gpu_mixed.py)
 check the kernels themselves against the oracle.
 """
+import math
+import random
 import struct
 from fractions import Fraction
 
@@ -135,3 +139,73 @@ def test_worst_case_level_sums_fit_fp32():
     assert worst < 2 ** 24
     # the top digit reaches 128 only for |X| close to 2^55; the bound above already assumes it
     assert digits(2 ** 55 - 1, 7)[0] == 128
+
+
+def _clz64(a):
+    return 64 - a.bit_length()
+
+
+def _kernel_round(acc, e2, mant):
+    """The digit kernels' integer rounding of acc * 2^e2 to a normal FP64 (mant = 52) or FP32
+    (mant = 23) number, restated: leading bit to position mant by a left shift, or a right shift
+    that adds half - 1 plus the kept part's lowest bit (half to even); the significand keeps its
+    leading bit, so adding it to (biased exponent - 1) << mant carries a rounding overflow into
+    the exponent.  None where the kernels take their slow path (outside the normal range)."""
+    if acc == 0:
+        return 0.0
+    bias, emax = (1023, 2046) if mant == 52 else (127, 254)
+    a = -acc if acc < 0 else acc
+    lz = _clz64(a)
+    top = 63 - mant
+    if lz >= top:
+        m = a << (lz - top)
+    else:
+        sh = top - lz
+        m = (a + ((1 << (sh - 1)) - 1) + ((a >> sh) & 1)) >> sh
+    be = 63 - lz + e2 + bias
+    if be < 1 or be + (m >> (mant + 1)) > emax:
+        return None
+    bits = ((be - 1) << mant) + m
+    if mant == 52:
+        return struct.unpack("<d", struct.pack("<Q", bits | ((1 << 63) if acc < 0 else 0)))[0]
+    return float(struct.unpack("<f", struct.pack("<I", bits | ((1 << 31) if acc < 0 else 0)))[0])
+
+
+def _exact_round(acc, e2, mant):
+    """acc * 2^e2 rounded to mant + 1 significant bits, ties to even, with exact integers."""
+    a = abs(acc)
+    pb = a.bit_length() - 1
+    if pb > mant:
+        sh = pb - mant
+        q, r, half = a >> sh, a & ((1 << sh) - 1), 1 << (sh - 1)
+        if r > half or (r == half and q & 1):
+            q += 1
+        v = math.ldexp(q, sh + e2)
+    else:
+        v = math.ldexp(a, e2)
+    return -v if acc < 0 else v
+
+
+@pytest.mark.parametrize("mant", [52, 23])
+def test_integer_rounding_of_the_accumulators(mant):
+    """The final rounding of the digit kernels (FP64 and FP32 outputs) equals exact
+    round-to-nearest-even of acc * 2^e2 on random accumulators below 2^62, on exact ties and on
+    carries into the next power of two."""
+    rng = random.Random(7 + mant)
+    cases = []
+    for _ in range(20000):
+        cases.append(rng.getrandbits(rng.randint(1, 62)) * rng.choice([1, -1]))
+    for k in range(1, 12):  # exact ties at every dropped-bit count
+        for _ in range(200):
+            cases.append((((rng.getrandbits(50) | 1) << k) | (1 << (k - 1))) * rng.choice([1, -1]))
+    for n in range(mant + 1, 62):  # all ones: rounding carries into the next power of two
+        cases.append((1 << n) - 1)
+    checked = 0
+    for acc in cases:
+        e2 = rng.randint(-900, 900) if mant == 52 else rng.randint(-120, 60)
+        got = _kernel_round(acc, e2, mant)
+        if got is None:
+            continue
+        assert got == _exact_round(acc, e2, mant), (acc, e2)
+        checked += 1
+    assert checked > 15000
