@@ -88,7 +88,8 @@ constexpr int kDgRows = 128;       // MMA M: operator rows (TMEM lanes)
 constexpr int kDgIssuer = 3;       // the warp (lane quarter 3: rows 96..127, never an output) issuing MMAs
 constexpr int kDgKcMax = (kModeMaxN + 15) / 16 * 2;  // k-chunks of 8 at the largest npad
 constexpr uint32_t kDgTmemCols = 512;
-constexpr int kDgHeader = 1536;    // 8 full + 8 drained mbarriers, TMEM address, line exponents (<= 128), row exponents (<= 80)
+constexpr int kDgHeader = 2560;    // 8 full + 8 drained mbarriers, TMEM address, line exponents (<= 128),
+                                   // row exponents (<= 80), line base offsets (<= 128)
 constexpr int kDgSmemMax = 232448;  // opt-in shared memory per CTA
 
 static_assert(kModeMaxN <= 96, "operator rows must stay in lane quarters 0..2");
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
     uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 128);
     int* sExp = reinterpret_cast<int*>(smem + 256);
     int* sRowE = reinterpret_cast<int*>(smem + 1024);
+    long long* sBase = reinterpret_cast<long long*>(smem + 1536);  // offset of each line's first entry
     unsigned char* sOp = smem + kDgHeader + ((256u - ((smem_u32(smem) + kDgHeader) & 255u)) & 255u);
     unsigned char* sX = sOp + dg_op_bytes(npad, r8, ND);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -293,6 +295,17 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         }
     if (tid < NL) sExp[tid] = 1;
     if (tid < n) sRowE[tid] = A.rowexp[c][tid];  // the table, not the previous kernel's output
+    const int nx = C.n[0], nxy = C.n[0] * C.n[1];
+    const int stride = axis == 0 ? 1 : (axis == 1 ? nx : nxy);
+    // each line's base offset once (the only run-time integer divisions of the kernel: on GB300
+    // they go through the conversion pipe, so none is left in the per-entry loops)
+    if (tid < NL) {
+        const int L = l0 + tid;
+        sBase[tid] = axis == 0 ? (long long)L * n : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L);
+    }
+    // g / kc for the x sweep by a multiply: exact for g < 2^32 / kc^2 (here g < NL kc <= 1280)
+    const unsigned kcMagic = 0xFFFFFFFFu / (unsigned)kc + 1u;
+    __syncthreads();
 
     // operator digits: the table is the shared layout, one contiguous copy
     const unsigned char* Bg = static_cast<const unsigned char*>(A.B[c]);
@@ -300,8 +313,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
     pdl_wait();  // the input lines are the previous kernel's output
 
     // data tile as bit patterns: items (line r, k-chunk q) of 8 values
-    const int nx = C.n[0], nxy = C.n[0] * C.n[1];
-    const int stride = axis == 0 ? 1 : (axis == 1 ? nx : nxy);
     const TIN* src = in + C.off;
     const int nitems = NL * kc;
     U val[kItems][8];
@@ -310,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         const int g = tid + it * THREADS;
         int r, q;
         if (axis == 0) {  // k-chunk fastest: a line's values are contiguous
-            r = g / kc;
+            r = (int)__umulhi((unsigned)g, kcMagic);
             q = g - r * kc;
         } else {  // line fastest: consecutive lines are consecutive addresses
             q = g / NL;
@@ -318,8 +329,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         }
         const int L = l0 + r;
         const bool live = g < nitems && L < nlines;
-        const long long base =
-            axis == 0 ? (long long)L * n : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L);
+        const long long base = live ? sBase[r] : 0;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const int k = 8 * q + t;
@@ -338,19 +348,28 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         atomicMax(sExp + r, emax);
     }
     __syncthreads();
+    // every item's line exponent before any digit-plane store (a load may not pass a store
+    // that might alias it, which would serialise the items)
+    int Ev[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int g = tid + it * THREADS;
+        const int r = axis == 0 ? (int)__umulhi((unsigned)g, kcMagic) : g % NL;
+        Ev[it] = g < nitems ? sExp[r] : 1;
+    }
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const int g = tid + it * THREADS;
         if (g >= nitems) break;
         int r, q;
         if (axis == 0) {
-            r = g / kc;
+            r = (int)__umulhi((unsigned)g, kcMagic);
             q = g - r * kc;
         } else {
             q = g / NL;
             r = g - q * NL;
         }
-        const int E = sExp[r];
+        const int E = Ev[it];
         uint32_t w[ND][4];
 #pragma unroll
         for (int t = 0; t < 8; t += 2) {
@@ -463,32 +482,60 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
         // acc * 2^(8 ND) * sigma_L * tau_i rounded once; consecutive threads write consecutive
         // addresses: entries of one line along x, consecutive lines along y and z
         const int nl = min(NL, nlines - l0);
-        const int total = axis == 0 ? n * nl : n * NL;
-        // four independent values per iteration: each rounding is a long chain of dependent
-        // integer instructions, and interleaving four chains hides their latency
-        constexpr int kU = 4;
-        for (int g0 = tid; g0 < total; g0 += kU * THREADS) {
+        // every shared-memory load of a batch before any global store: each rounding is a chain of
+        // dependent integer instructions, and a load may not pass a store that might alias it
+        if (axis == 0) {
+            // one warp per line, lanes along the line's entries (contiguous in memory)
+            constexpr int kR = (kModeMaxN + 31) / 32;
+            for (int col = warp; col < nl; col += THREADS / 32) {
+                const long long base = sBase[col];
+                const int es = digit_scale<TIN, ND>(sExp[col]);
+                long long av[kR];
+                int e2v[kR];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int g = g0 + u * THREADS;
-                int ii, col;
-                if (axis == 0) {
-                    col = g / n;
-                    ii = g - col * n;
-                } else {
-                    ii = g / NL;
-                    col = g - ii * NL;
+                for (int j = 0; j < kR; ++j) {
+                    const int ii = lane + 32 * j;
+                    const int iis = ii < n ? ii : 0;
+                    av[j] = sAcc[iis * (NL + 1) + col];
+                    e2v[j] = 8 * ND + sRowE[iis] - 1075 - kTopOp + es;
                 }
-                if (g < total && col < nl) {
-                    const int L = l0 + col;
-                    const int e2 = 8 * ND + sRowE[ii] - 1075 - kTopOp + digit_scale<TIN, ND>(sExp[col]);
-                    const TOUT y = digit_out(sAcc[ii * (NL + 1) + col], e2, (TOUT*)nullptr);
-                    const long long o = axis == 0 ? (long long)L * n + ii
-                                                  : (axis == 1 ? (long long)(L % nx) + (long long)(L / nx) * nxy : L) +
-                                                        (long long)ii * stride;
-                    dst[o] = y;
-                    if (dst64) dst64[o] = f2d_exact(y);
+#pragma unroll
+                for (int j = 0; j < kR; ++j) {
+                    const int ii = lane + 32 * j;
+                    const TOUT y = digit_out(av[j], e2v[j], (TOUT*)nullptr);
+                    if (ii < n) {
+                        dst[base + ii] = y;
+                        if (dst64) dst64[base + ii] = f2d_exact(y);
+                    }
                 }
+            }
+        } else {
+            // consecutive threads: consecutive lines (consecutive addresses)
+            constexpr int kU = 4;
+            const int total = n * NL;
+            for (int g0 = tid; g0 < total; g0 += kU * THREADS) {
+                long long av[kU], ov[kU];
+                int e2v[kU];
+                bool live[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int g = g0 + u * THREADS;
+                    const int ii = g / NL, col = g - ii * NL;
+                    live[u] = g < total && col < nl;
+                    const int iis = live[u] ? ii : 0, cols = live[u] ? col : 0;
+                    av[u] = sAcc[iis * (NL + 1) + cols];
+                    e2v[u] = 8 * ND + sRowE[iis] - 1075 - kTopOp + digit_scale<TIN, ND>(sExp[cols]);
+                    ov[u] = sBase[cols] + (long long)iis * stride;
+                }
+                TOUT yv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) yv[u] = digit_out(av[u], e2v[u], (TOUT*)nullptr);
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (live[u]) {
+                        dst[ov[u]] = yv[u];
+                        if (dst64) dst64[ov[u]] = f2d_exact(yv[u]);
+                    }
             }
         }
     }
@@ -502,10 +549,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
 
 int mode_digit_npad(int n) { return (n + 15) / 16 * 16; }
 
-// Lines per tile of an FP64 sweep.  The MMA time is proportional to N (about 2
-// cycles per column of an M = 128, K = 16 instruction on GB300), so the tile only
-// decides how the lines spread over the SMs: 128-line tiles while they still
-// fill all 152 SMs with one wave, else 96 (one wave of 135 CTAs at p = 3, 64^3).
+// Lines per tile of an FP64 sweep.  An M = 128, K = 16 MMA with both operands in
+// shared memory takes about 32 + N/4 cycles on GB300 (the operator's 4 KB and the
+// tile's N x 32 bytes at 128 bytes per cycle) and N/2 at full rate, so a CTA's
+// MMA time grows with its lines while the other phases (load, digit cut,
+// rounding) are a fixed latency per CTA: 128-line tiles while they still fill
+// all 152 SMs with one wave, else 96 (one wave of 135 CTAs at p = 3, 64^3).
 static int digit_tile_lines(const ModeDigitArgs& a, long long maxlines) {
     const long long tiles128 = 3 * ((maxlines + 127) / 128);
     bool fits128 = true;
