@@ -24,6 +24,8 @@ hodge     geometry map, material, matrix-free Hodge mass apply M^2, M~^2
           (Sec. 3.4, 2-form pullback of Sec. 2.3)
 maxwell   scheme 2 leapfrog step, energy, CFL by power iteration,
           L2 projection and error norms (Sec. 3.4, Sec. 4.2, Sec. 5)
+scheme1   scheme 1: 1-form mass matrices M^1_eps, M~^1_mu and the leapfrog
+          with mass-matrix Hodge stars, energy, CFL (Sec. 3.3, Sec. 5.2)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against closed forms, identities the paper states,
