@@ -540,6 +540,34 @@ def batched_config(smx, dev, stream, nsteps):
                     % (sum(8 * 2 * (c.N_e + c.N_h) for c in ctxs) / 1e6)}
 
 
+def scheme1_comparison(smx, dev, stream, eps, steps, dt2):
+    """Scheme 1 (mass-matrix Hodge stars, Sec. 3.3) on the same workload: ms per step (eager, the CG
+    reads its residual on the host every few iterations), CG iterations, and its CFL limit beside
+    scheme 2's (Sec. 5.2), so the per-step and whole-run costs of the two schemes compare."""
+    import torch
+    ctx = smx.Context(P, NEL, eps=eps, mu=1.0, scheme1=True).bind(dev)
+    ctx.set_stream(stream)
+    st = make_state(ctx, smx, dev, SEED + 9)
+    e1 = torch.empty_like(st[2])
+    ctx.scheme1_star(smx.FIELD_D, st[0], e1, tol=1e-12)
+    st = (st[0], st[1], e1, st[3])
+    dt1 = ctx.cfl_scheme1(iters=60, tol=1e-4, cg_tol=1e-10)
+    dt = 0.5 * dt1
+    iters = ctx.step_scheme1(*st, dt, 1, tol=1e-12)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    iters = max(iters, ctx.step_scheme1(*st, dt, steps, tol=1e-12))
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / steps
+    dof = ctx.N_e + ctx.N_h
+    return {"value": dof / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "max_cg_iterations": iters,
+            "cg_tol": 1e-12, "dt_max": dt1, "dt_max_scheme2": dt2,
+            "note": "scheme 1 of the paper (Sec. 3.3): Hodge stars by preconditioned CG on the 1-form masses; "
+                    "same workload, FP64"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2302_04979_gb300 import smx, synth
@@ -616,9 +644,12 @@ def run_ours(args, rank, world, local):
 
     # ---- the other configurations and the batched one (rank 0 of a single-GPU run only)
     configs = batched = None
+    s1 = None
     if world == 1 and not args.no_extra:
         configs = other_configs(smx, dev, stream, flush, max(20, min(args.steps, 200)))
         batched = batched_config(smx, dev, stream, 300)
+        s1 = scheme1_comparison(smx, dev, stream, eps, 5, 2.0 * dt)
+        s1["step_time_ratio_vs_scheme2"] = s1["ms_per_step"] / (total_ms / args.steps)
     clocks = sampler.stop()
 
     # ---- end to end through the host-buffer C call (copies inside the timed region)
@@ -676,6 +707,8 @@ def run_ours(args, rank, world, local):
             out["configs"] = configs
         if batched is not None:
             out["batched"] = batched
+        if s1 is not None:
+            out["scheme1"] = s1
     return out
 
 

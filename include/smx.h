@@ -96,6 +96,7 @@ typedef struct {
     int precision;         /* SMX_FP64, SMX_MIXED or SMX_MIXED_REFINED: arithmetic of smx_step / smx_step_host */
     smx_geometry_fn geom_fn; /* SMX_GEOM_CALLBACK: the map (must stay callable while smx_project may be called) */
     void* geom_user;         /* passed to geom_fn */
+    int scheme1;           /* nonzero: also build the tables of scheme 1 (smx_step_scheme1; p <= 5) */
 } smx_params;
 
 /* ---- precision of the leapfrog step ----
@@ -150,6 +151,39 @@ int smx_bind_workspace(smx_ctx* ctx, void* device_ptr, size_t bytes);
 /* Stream for all later device work (a cudaStream_t passed as void*; NULL =
  * legacy default stream). */
 int smx_set_stream(smx_ctx* ctx, void* stream);
+
+/* ==== Scheme 1 (Sec. 3.3): Hodge stars by mass-matrix solves ====
+ * The comparison scheme of the paper: the same kick-drift-kick leapfrog on (d, b), with
+ *   e = (M^1_eps)^{-1} K~_2 d  (Eq. discrete1_hodge_eps),  h = (M~^1_mu)^{-1} K_2 b  (Eq. discrete1_hodge_mu),
+ * M^1_eps the mass of X^1_{h,0} weighted by eps (1-form pullback u = J^{-T} u^, Sec. 2.3), M~^1_mu
+ * that of X~^1 weighted by mu, K~_2 = K_1^T and K_2 = K~_1^T (Eq. pairing_transpose).  Each mass
+ * solve is a conjugate-gradient iteration on the device (matrix-free mass apply: block-Kronecker
+ * on the identity map, sum-factorised quadrature otherwise) preconditioned with the unit-material
+ * Kronecker mass (three banded line sweeps; exact up to the material constant on the identity map
+ * with constant material), stopped at ||y - M x|| <= tol ||y||; the host reads the residual every
+ * four iterations, so these calls synchronise the stream.  The context must be created with
+ * scheme1 = 1 (else SMX_ESTATE).  Vectors as for smx_step; e and h are written. */
+
+/* One scheme-1 Hodge star: field SMX_FIELD_D gives out = e from x = d, SMX_FIELD_B gives out = h
+ * from x = b.  *iters (optional): CG iterations used.  Errors: SMX_EINVAL, SMX_ESTATE,
+ * SMX_ESINGULAR (no convergence in maxit iterations), SMX_ENONFINITE, SMX_ECUDA. */
+int smx_scheme1_star(smx_ctx* ctx, int field, const double* x, double* out, double tol, int maxit, int* iters);
+
+/* nsteps kick-drift-kick steps of scheme 1 (the order of smx_step); *max_iters (optional): the
+ * largest CG iteration count of any solve.  Errors as smx_scheme1_star and smx_step. */
+int smx_step_scheme1(smx_ctx* ctx, double* d, double* b, double* e, double* h, const double* jhat,
+                     const double* amp, double dt, int nsteps, double tol, int maxit, int* max_iters);
+
+/* E_h = 1/2 (e^T K~_2 d + h^T K_2 b) of scheme 1 (Sec. 3.3; equal to 1/2 (e^T M^1 e + h^T M~^1 h)
+ * when e, h are the stars of d, b).  Synchronises.  out[0] receives it. */
+int smx_energy_scheme1(smx_ctx* ctx, const double* d, const double* b, const double* e, const double* h,
+                       double* out);
+
+/* CFL limit of scheme 1 (Sec. 5.2): 2 / sqrt(lambda_max) of D~^1 S_H D^1 S_E by power iteration (as
+ * smx_cfl; v, w of N_e, t of N_h, device), with the mass solves to cg_tol in at most cg_maxit
+ * iterations. */
+int smx_cfl_scheme1(smx_ctx* ctx, int iters, double tol, double* v, double* w, double* t, double cg_tol,
+                    int cg_maxit, double* dt_max);
 
 /* CUDA graphs for smx_step (default on): the first call with a given set of
  * (d, b, e, h, jhat, amp) pointers, dt and nsteps is captured into a graph,

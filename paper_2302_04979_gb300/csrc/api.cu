@@ -152,6 +152,20 @@ struct smx_ctx {
     // FP64 residual, a second FP64 vector, and the residual passes [field][axis]
     std::vector<double> band_rows[3][4];
     size_t o_band[3][4] = {};
+    // scheme 1 (mass-matrix Hodge stars): 1-form masses [0] M~^1_mu (field H), [1] M^1_eps (field E),
+    // the unit-material Kronecker masses of every kind per axis as the PCG preconditioner (banded LU
+    // with half-bandwidth p), three PCG vectors and the PCG scalars, and the argument blocks
+    bool s1 = false;
+    HodgeHost hodge1[2];
+    BandLU mfac[3][4];
+    size_t o_mfac[3][4][3] = {};
+    size_t o_s1v[3] = {}, o_cg = 0;
+    double* s1v[3] = {nullptr, nullptr, nullptr};
+    double* cg = nullptr;
+    HodgeBlockArgs hb1[2];
+    HodgeQuadArgs hq1[2];
+    SolveArgs pre1[2][3];
+    BandApplyArgs kt[2][3];  // [0] K_2 = K~_1^T (B -> H layout), [1] K~_2 = K_1^T (D -> E layout)
     size_t o_t64 = 0;
     double* t64 = nullptr;
     BandApplyArgs band[2][3];
@@ -215,9 +229,9 @@ std::vector<int> tile_bounds(int nel, int nblocks) {
     return b;
 }
 
-int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
-    HodgeHost& H = C->hodge[h];
-    const int field = kFieldOfHodge[h];
+// Block-Kronecker tables of the mass of `field` with weight 1/material (invert, the 2-form
+// masses of scheme 2) or the material itself (the 1-form masses of scheme 1).
+int build_hodge_block_t(smx_ctx* C, HodgeHost& H, int field, const smx_material& m, bool invert) {
     std::vector<int> bounds[3];
     for (int a = 0; a < 3; ++a) {
         const int nb = (m.kind == SMX_MAT_BLOCKS) ? m.blocks[a] : 1;
@@ -276,9 +290,13 @@ int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
                     v = m.block_values[blk];
                     H.tile_block.push_back(blk);
                 }
-                H.gamma[((size_t)tz * H.ntile[1] + ty) * H.ntile[0] + tx] = 1.0 / v;
+                H.gamma[((size_t)tz * H.ntile[1] + ty) * H.ntile[0] + tx] = invert ? 1.0 / v : v;
             }
     return SMX_OK;
+}
+
+int build_hodge_block(smx_ctx* C, int h, const smx_material& m) {
+    return build_hodge_block_t(C, C->hodge[h], kFieldOfHodge[h], m, true);
 }
 
 // Global univariate masses of every space kind as band rows (half-bandwidth =
@@ -310,8 +328,10 @@ void build_separable(smx_ctx* C, int h, double gamma) {
     }
 }
 
-int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
-    HodgeHost& H = C->hodge[h];
+// Quadrature tables: basis values and, per point, the metric of a 2-form mass weighted by
+// 1/material, w J^T J / (det J material) (one_form = false), or of a 1-form mass weighted by the
+// material, w material det J (J^T J)^{-1} (one_form = true: u = J^{-T} u^, Sec. 2.3).
+int build_hodge_quad_t(smx_ctx* C, HodgeHost& H, const smx_material& m, bool one_form) {
     std::vector<double> gx[3], gw[3];
     for (int a = 0; a < 3; ++a) {
         const int p = C->p[a], nel = C->nel[a];
@@ -371,11 +391,29 @@ int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
     H.G.assign(6 * Q, 0.0);
     for (long long qi = 0; qi < Q; ++qi) {
         if (!finite_pos(mat[qi])) return SMX_EMAT;
-        const double s = wdet[qi] / mat[qi];
         const double* J = &Jall[9 * qi];
         double JtJ[3][3];
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) JtJ[i][j] = J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j];
+        double s = wdet[qi] / mat[qi];
+        if (one_form) {
+            // (J^T J)^{-1} by cofactors; w det J material = (w / det J) det J^2 material
+            const double dj = det3(J);
+            double A[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) A[i][j] = JtJ[i][j];
+            const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1], c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+            const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0], c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+            const double c12 = A[0][2] * A[1][0] - A[0][0] * A[1][2], c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+            const double detA = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+            JtJ[0][0] = c00 / detA;
+            JtJ[0][1] = JtJ[1][0] = c01 / detA;
+            JtJ[0][2] = JtJ[2][0] = c02 / detA;
+            JtJ[1][1] = c11 / detA;
+            JtJ[1][2] = JtJ[2][1] = c12 / detA;
+            JtJ[2][2] = c22 / detA;
+            s = wdet[qi] * dj * dj * mat[qi];
+        }
         H.G[0 * Q + qi] = s * JtJ[0][0];
         H.G[1 * Q + qi] = s * JtJ[0][1];
         H.G[2 * Q + qi] = s * JtJ[0][2];
@@ -385,6 +423,8 @@ int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) {
     }
     return SMX_OK;
 }
+
+int build_hodge_quad(smx_ctx* C, int h, const smx_material& m) { return build_hodge_quad_t(C, C->hodge[h], m, false); }
 
 // Dense A^{-1} (row-major) from a banded LU, column by column.
 std::vector<double> dense_inverse(const BandLU& f) {
@@ -473,6 +513,14 @@ void layout(smx_ctx* C) {
         C->o_h32 = C->o_e32 + f32(C->N_e);
         C->o_y32 = C->o_h32 + f32(C->N_h);
         C->total_bytes = C->o_y32 + f32((long long)nmax);
+    }
+    if (C->s1) {  // PCG vectors and scalars of scheme 1
+        for (int k = 0; k < 3; ++k) {
+            C->o_s1v[k] = C->total_bytes;
+            C->total_bytes += (nmax * sizeof(double) + 255) & ~size_t(255);
+        }
+        C->o_cg = C->total_bytes;
+        C->total_bytes += 256;
     }
     if (C->precision == SMX_MIXED_REFINED) {  // a second FP64 vector for the residual passes
         C->o_t64 = C->total_bytes;
@@ -757,6 +805,92 @@ int step_refined(smx_ctx* C, double* d, double* b, double* e, double* h, const d
     return SMX_OK;
 }
 
+// ---- scheme 1 (Sec. 3.3): Hodge stars by mass-matrix solves, for comparison with scheme 2
+// y = K^T x along the three axes: k = 0 K_2 = K~_1^T (x in the B layout, y in H), k = 1
+// K~_2 = K_1^T (x in D, y in E); t1, t2 are scratch vectors (all four distinct).
+int s1_pair_t(smx_ctx* C, int k, const double* x, double* y, double* t1, double* t2) {
+    int st = run(C, 27, 1, [&] { return launch_band_apply(C->kt[k][0], x, nullptr, nullptr, t1, C->stream); });
+    if (st) return st;
+    st = run(C, 27, 1, [&] { return launch_band_apply(C->kt[k][1], t1, nullptr, nullptr, t2, C->stream); });
+    if (st) return st;
+    return run(C, 27, 1, [&] { return launch_band_apply(C->kt[k][2], t2, nullptr, nullptr, y, C->stream); });
+}
+
+// y = M x for the 1-form mass k (0: M~^1_mu, 1: M^1_eps), y overwritten
+int s1_mass(smx_ctx* C, int k, const double* x, double* y) {
+    const long long n = C->fld[k == 0 ? SMX_FIELD_H : SMX_FIELD_E].total;
+    int st = run(C, 20, 1, [&] { return launch_zero(y, n, C->stream); });
+    if (st) return st;
+    if (C->hodge1[k].mode == 0) return run(C, 2, 1, [&] { return launch_hodge_block(C->hb1[k], x, y, C->stream); });
+    return run(C, 3, 1, [&] { return launch_hodge_quad(C->hq1[k], x, y, C->stream); });
+}
+
+// x = P^{-1} y: the unit-material Kronecker mass solved by three banded sweeps (in place when x == y)
+int s1_precond(smx_ctx* C, int k, const double* y, double* x) {
+    int st = run(C, 4, 1, [&] { return launch_solve_axis(C->pre1[k][0], C->p[0], y, x, C->stream); });
+    if (st) return st;
+    st = run(C, 5, 1, [&] { return launch_solve_axis(C->pre1[k][1], C->p[1], x, x, C->stream); });
+    if (st) return st;
+    return run(C, 6, 1, [&] { return launch_solve_axis(C->pre1[k][2], C->p[2], x, x, C->stream); });
+}
+
+// x = M^{-1} y by conjugate gradients preconditioned with the unit-material Kronecker mass
+// (for constant material on the identity map the mass is that preconditioner times the
+// constant: one iteration), to ||y - M x|| <= tol ||y||.  The residual is read back after the
+// first iteration and then every 4 (the only host synchronisations); *iters receives the
+// iterations used.  y must not be a PCG vector.
+int s1_pcg(smx_ctx* C, int k, const double* y, double* x, double tol, int maxit, int* iters) {
+    const long long n = C->fld[k == 0 ? SMX_FIELD_H : SMX_FIELD_E].total;
+    double *r = C->s1v[0], *z = C->s1v[1], *pv = C->s1v[2], *Ap = C->scratch2, *cg = C->cg;
+    int st;
+    auto dot = [&](const double* a, const double* b, int slot) {
+        return run(C, 7, 2, [&] { return launch_dot(a, b, n, C->partial, cg + slot, C->stream); });
+    };
+    auto converged = [&](bool& done) {
+        double h[kCgCount];
+        CK(cudaMemcpyAsync(h, cg, sizeof h, cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+        if (!std::isfinite(h[kCgRr]) || !std::isfinite(h[kCgYy])) return SMX_ENONFINITE;
+        done = h[kCgRr] <= tol * tol * h[kCgYy];
+        return SMX_OK;
+    };
+    if ((st = s1_precond(C, k, y, x))) return st;
+    if ((st = s1_mass(C, k, x, r))) return st;
+    if ((st = run(C, 20, 1, [&] { return launch_sub_from(y, r, n, C->stream); }))) return st;
+    if ((st = dot(y, y, kCgYy)) || (st = dot(r, r, kCgRr))) return st;
+    bool done = false;
+    if ((st = converged(done))) return st;
+    int it = 0;
+    if (!done) {
+        if ((st = s1_precond(C, k, r, z))) return st;
+        if ((st = dot(r, z, kCgRz))) return st;
+        if ((st = run(C, 20, 1, [&] { return launch_copy(z, pv, n, C->stream); }))) return st;
+        while (it < maxit) {
+            ++it;
+            if ((st = s1_mass(C, k, pv, Ap))) return st;
+            if ((st = dot(pv, Ap, kCgPAp))) return st;
+            if ((st = run(C, 20, 1, [&] { return launch_cg_xr(x, r, pv, Ap, cg, n, C->stream); }))) return st;
+            if (it == 1 || it % 4 == 0 || it == maxit) {
+                if ((st = dot(r, r, kCgRr))) return st;
+                if ((st = converged(done))) return st;
+                if (done) break;
+            }
+            if ((st = s1_precond(C, k, r, z))) return st;
+            if ((st = dot(r, z, kCgRzNew))) return st;
+            if ((st = run(C, 20, 2, [&] { return launch_cg_p(pv, z, cg, n, C->stream); }))) return st;
+        }
+    }
+    if (iters) *iters = it;
+    return done ? SMX_OK : SMX_ESINGULAR;
+}
+
+// One Hodge star of scheme 1: h = (M~^1_mu)^{-1} K_2 b (k = 0) or e = (M^1_eps)^{-1} K~_2 d (k = 1)
+int s1_star(smx_ctx* C, int k, const double* x, double* out, double tol, int maxit, int* iters) {
+    int st = s1_pair_t(C, k, x, C->scratch, C->s1v[0], C->s1v[1]);
+    if (st) return st;
+    return s1_pcg(C, k, C->scratch, out, tol, maxit, iters);
+}
+
 // One discrete Hodge star of scheme 2 (Eq. discrete2_hodge_mu for h = 0,
 // Eq. discrete2_hodge_eps for h = 1): three fused mass+solve line passes when
 // the field's mass is a single Kronecker product, else mass apply into the
@@ -918,6 +1052,48 @@ int smx_create(const smx_params* P, smx_ctx** out) {
             }
             if (block && mats[h]->kind == SMX_MAT_CONST) build_separable(C, h, 1.0 / mats[h]->value);
         }
+        if (P->scheme1) {
+            // scheme 1: 1-form masses weighted by the material itself (Eq. discrete1_hodge_mu / _eps),
+            // block-Kronecker on the identity map, quadrature with the 1-form metric otherwise
+            for (int a = 0; a < 3; ++a)
+                if (C->p[a] > 5) {
+                    delete C;
+                    return SMX_EINVAL;
+                }
+            C->s1 = true;
+            const smx_material* mats1[2] = {&P->mu, &P->eps};
+            const int flds1[2] = {SMX_FIELD_H, SMX_FIELD_E};
+            for (int k = 0; k < 2; ++k) {
+                const bool block = C->geometry == SMX_GEOM_IDENTITY && mats1[k]->kind != SMX_MAT_POINTWISE;
+                C->hodge1[k].mode = block ? 0 : 1;
+                st = block ? build_hodge_block_t(C, C->hodge1[k], flds1[k], *mats1[k], false)
+                           : build_hodge_quad_t(C, C->hodge1[k], *mats1[k], true);
+                if (st) {
+                    delete C;
+                    return st;
+                }
+            }
+            // the preconditioner: unit-material Kronecker 1D masses of every kind, banded LU with
+            // half-bandwidth p on both sides (the widest kind; narrower kinds carry zeros)
+            for (int a = 0; a < 3; ++a)
+                for (int kind = 0; kind < 4; ++kind) {
+                    const int pa = C->p[a], nel = C->nel[a], d = kind_degree(kind, pa), off = kind_offset(kind);
+                    const int dim = kind_dim(kind, pa, nel);
+                    std::vector<double> M((size_t)dim * dim, 0.0);
+                    for (int e = 0; e < nel; ++e) {
+                        const std::vector<double> Me = element_mass(kind, pa, nel, e);
+                        for (int r = 0; r <= d; ++r)
+                            for (int q = 0; q <= d; ++q) {
+                                const int i = e + r + off, j = e + q + off;
+                                if (i >= 0 && i < dim && j >= 0 && j < dim) M[(size_t)i * dim + j] += Me[r * (d + 1) + q];
+                            }
+                    }
+                    if (!band_lu(M, dim, pa, pa, C->mfac[a][kind])) {
+                        delete C;
+                        return SMX_ESINGULAR;
+                    }
+                }
+        }
         if (P->precision != SMX_FP64 && P->precision != SMX_MIXED && P->precision != SMX_MIXED_REFINED) {
             delete C;
             return SMX_EINVAL;
@@ -953,9 +1129,33 @@ int smx_create(const smx_params* P, smx_ctx** out) {
                 H.G.shrink_to_fit();
             }
         }
-        if (C->precision == SMX_MIXED_REFINED)
+        if (C->precision == SMX_MIXED_REFINED || C->s1)
             for (int a = 0; a < 3; ++a)
                 for (int w = 0; w < 4; ++w) C->o_band[a][w] = C->blob.add(C->band_rows[a][w]);
+        if (C->s1) {
+            for (int k = 0; k < 2; ++k) {
+                HodgeHost& H = C->hodge1[k];
+                if (H.mode == 0) {
+                    for (int a = 0; a < 3; ++a) {
+                        H.o_tf0[a] = C->blob.add(H.tf0[a]);
+                        H.o_tlen[a] = C->blob.add(H.tlen[a]);
+                        H.o_tmat[a] = C->blob.add(H.tmat[a]);
+                    }
+                    H.o_gamma = C->blob.add(H.gamma);
+                } else {
+                    for (int a = 0; a < 3; ++a) H.o_bval[a] = C->blob.add(H.bval[a]);
+                    H.o_G = C->blob.add(H.G);
+                    H.G.clear();
+                    H.G.shrink_to_fit();
+                }
+            }
+            for (int a = 0; a < 3; ++a)
+                for (int kind = 0; kind < 4; ++kind) {
+                    C->o_mfac[a][kind][0] = C->blob.add(C->mfac[a][kind].L);
+                    C->o_mfac[a][kind][1] = C->blob.add(C->mfac[a][kind].U);
+                    C->o_mfac[a][kind][2] = C->blob.add(C->mfac[a][kind].dinv);
+                }
+        }
         if (C->precision != SMX_FP64) {
             // FP32 (hi, lo) copies of every operator table of the mixed step
             for (int a = 0; a < 3; ++a)
@@ -1200,6 +1400,69 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
                     Mg.npad[c] = mode_digit_npad(C->fld[fld].c[c].n[a]);
                 }
             }
+    if (C->s1) {
+        for (int k = 0; k < 3; ++k) C->s1v[k] = reinterpret_cast<double*>(ws + C->o_s1v[k]);
+        C->cg = reinterpret_cast<double*>(ws + C->o_cg);
+        const int flds1[2] = {SMX_FIELD_H, SMX_FIELD_E};
+        for (int k = 0; k < 2; ++k) {
+            const HodgeHost& H = C->hodge1[k];
+            const int fld = flds1[k];
+            if (H.mode == 0) {
+                HodgeBlockArgs& A = C->hb1[k];
+                A.field = C->fld[fld];
+                for (int a = 0; a < 3; ++a) {
+                    A.ntile[a] = H.ntile[a];
+                    A.tf0[a] = reinterpret_cast<const int*>(ws + H.o_tf0[a]);
+                    A.tlen[a] = reinterpret_cast<const int*>(ws + H.o_tlen[a]);
+                    A.tmat[a] = reinterpret_cast<const double*>(ws + H.o_tmat[a]);
+                }
+                for (int c = 0; c < 3; ++c)
+                    for (int a = 0; a < 3; ++a) {
+                        A.kinds[c][a] = kFieldKinds[fld][c][a];
+                        A.deg[c][a] = kind_degree(A.kinds[c][a], C->p[a]);
+                    }
+                A.gamma = reinterpret_cast<const double*>(ws + H.o_gamma);
+                A.max_nloc = H.max_nloc;
+            } else {
+                HodgeQuadArgs& Q = C->hq1[k];
+                Q.field = C->fld[fld];
+                for (int a = 0; a < 3; ++a) {
+                    Q.nel[a] = C->nel[a];
+                    Q.q[a] = H.q[a];
+                    Q.Qn[a] = H.Qn[a];
+                    Q.bval[a] = reinterpret_cast<const double*>(ws + H.o_bval[a]);
+                }
+                for (int c = 0; c < 3; ++c)
+                    for (int a = 0; a < 3; ++a) {
+                        Q.kinds[c][a] = kFieldKinds[fld][c][a];
+                        Q.deg[c][a] = kind_degree(Q.kinds[c][a], C->p[a]);
+                        Q.koff[c][a] = kind_offset(Q.kinds[c][a]);
+                    }
+                Q.G = reinterpret_cast<const double*>(ws + H.o_G);
+                Q.Qtot = H.Qtot;
+            }
+            for (int a = 0; a < 3; ++a) {
+                SolveArgs& S = C->pre1[k][a];
+                S.field = C->fld[fld];
+                S.axis = a;
+                for (int c = 0; c < 3; ++c) {
+                    const int kind = kFieldKinds[fld][c][a];
+                    S.f[c].L = reinterpret_cast<const double*>(ws + C->o_mfac[a][kind][0]);
+                    S.f[c].U = reinterpret_cast<const double*>(ws + C->o_mfac[a][kind][1]);
+                    S.f[c].dinv = reinterpret_cast<const double*>(ws + C->o_mfac[a][kind][2]);
+                    S.f[c].n = C->mfac[a][kind].n;
+                }
+                // K_2 = K~_1^T along the axis: the transposes of K~_1's factors (which = 1); K~_2 = K_1^T
+                BandApplyArgs& Ba = C->kt[k][a];
+                Ba.field = C->fld[fld];
+                Ba.axis = a;
+                Ba.kl = C->p[a] - 1;
+                const int which = k == 0 ? 1 : 0;
+                for (int c = 0; c < 3; ++c)
+                    Ba.band[c] = reinterpret_cast<const double*>(ws + C->o_band[a][factor_index(which, c, a) ^ 2]);
+            }
+        }
+    }
     if (C->precision == SMX_MIXED_REFINED) {
         C->t64 = reinterpret_cast<double*>(ws + C->o_t64);
         for (int h = 0; h < 2; ++h) {
@@ -1373,6 +1636,98 @@ int smx_step(smx_ctx* C, double* d, double* b, double* e, double* h, const doubl
     }
     CK(cudaGraphLaunch(G.exec, C->stream));
     C->launches += G.kernels;
+    return SMX_OK;
+}
+
+int smx_scheme1_star(smx_ctx* C, int field, const double* x, double* out, double tol, int maxit, int* iters) {
+    NEED_WS(C);
+    if (!C->s1) return SMX_ESTATE;
+    if (!x || !out || x == out || !(tol > 0.0) || maxit < 0) return SMX_EINVAL;
+    if (field != SMX_FIELD_B && field != SMX_FIELD_D) return SMX_EINVAL;
+    return s1_star(C, field == SMX_FIELD_B ? 0 : 1, x, out, tol, maxit, iters);
+}
+
+int smx_step_scheme1(smx_ctx* C, double* d, double* b, double* e, double* h, const double* jhat, const double* amp,
+                     double dt, int nsteps, double tol, int maxit, int* max_iters) {
+    NEED_WS(C);
+    if (!C->s1) return SMX_ESTATE;
+    if (!d || !b || !e || !h || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt) || !(tol > 0.0) || maxit < 0)
+        return SMX_EINVAL;
+    if (jhat && !amp) return SMX_EINVAL;
+    int worst = 0, it = 0, st;
+    if ((st = curl_primal_impl(C, e, b, -0.5 * dt))) return st;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((st = s1_star(C, 0, b, h, tol, maxit, &it))) return st;  // h = (M~^1_mu)^{-1} K_2 b
+        worst = std::max(worst, it);
+        if ((st = curl_dual_impl(C, h, d, dt, jhat, amp, n, 0.0))) return st;
+        if ((st = s1_star(C, 1, d, e, tol, maxit, &it))) return st;  // e = (M^1_eps)^{-1} K~_2 d
+        worst = std::max(worst, it);
+        if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt))) return st;
+    }
+    if (max_iters) *max_iters = worst;
+    return SMX_OK;
+}
+
+int smx_energy_scheme1(smx_ctx* C, const double* d, const double* b, const double* e, const double* h,
+                       double* out) {
+    NEED_WS(C);
+    if (!C->s1) return SMX_ESTATE;
+    if (!d || !b || !e || !h || !out) return SMX_EINVAL;
+    // E_h = 1/2 (e^T K~_2 d + h^T K_2 b) (Sec. 3.3, energy with pairing matrices)
+    int st = s1_pair_t(C, 1, d, C->scratch, C->s1v[0], C->s1v[1]);
+    if (st) return st;
+    if ((st = dot_impl(C, e, C->scratch, C->N_e, 0))) return st;
+    if ((st = s1_pair_t(C, 0, b, C->scratch, C->s1v[0], C->s1v[1]))) return st;
+    if ((st = dot_impl(C, h, C->scratch, C->N_h, 1))) return st;
+    double host[2];
+    CK(cudaMemcpyAsync(host, C->dots, sizeof host, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    out[0] = 0.5 * (host[0] + host[1]);
+    return std::isfinite(out[0]) ? SMX_OK : SMX_ENONFINITE;
+}
+
+int smx_cfl_scheme1(smx_ctx* C, int iters, double tol, double* v, double* w, double* t, double cg_tol, int cg_maxit,
+                    double* dt_max) {
+    NEED_WS(C);
+    if (!C->s1) return SMX_ESTATE;
+    if (!v || !w || !t || !dt_max || iters < 1 || !(tol >= 0.0) || !(cg_tol > 0.0)) return SMX_EINVAL;
+    // lambda_max of T = D~^1 S_H D^1 S_E by power iteration in the inner product of K_1 S_E
+    // (T is self-adjoint there); S_E, S_H the scheme-1 Hodge stars.  w holds S_E v, t holds
+    // D^1 S_E v, then S_H of it, then T v in w.
+    std::vector<double> v0(C->N_e);
+    uint64_t state = 0x5eed5eedULL;
+    for (auto& x : v0) x = (double)(splitmix64(state) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    CK(cudaMemcpyAsync(v, v0.data(), v0.size() * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+    double lam = 0.0, lam_old = 0.0;
+    int it_cg = 0, st;
+    // A x = K_1 S_E x = (K~_2)^T S_E x; the inner product needs only x^T K_1 S_E x = (K~_2 x)^T S_E x
+    for (int it = 0; it < iters; ++it) {
+        if ((st = s1_star(C, 1, v, w, cg_tol, cg_maxit, &it_cg))) return st;           // w = S_E v
+        CK(cudaMemsetAsync(t, 0, C->N_h * sizeof(double), C->stream));
+        if ((st = curl_primal_impl(C, w, t, 1.0))) return st;                           // t = D^1 S_E v
+        if ((st = s1_pair_t(C, 1, v, C->scratch2, C->s1v[0], C->s1v[1]))) return st;   // K~_2 v
+        if ((st = dot_impl(C, w, C->scratch2, C->N_e, 0))) return st;                   // den = v.A v
+        if ((st = s1_star(C, 0, t, C->state, cg_tol, cg_maxit, &it_cg))) return st;   // S_H D^1 S_E v
+        CK(cudaMemsetAsync(w, 0, C->N_e * sizeof(double), C->stream));
+        if ((st = curl_dual_impl(C, C->state, w, 1.0, nullptr, nullptr, 0, 0.0))) return st;  // w = T v
+        if ((st = s1_star(C, 1, w, t, cg_tol, cg_maxit, &it_cg))) return st;           // t = S_E T v (N_e <= len t)
+        if ((st = s1_pair_t(C, 1, v, C->scratch2, C->s1v[0], C->s1v[1]))) return st;
+        if ((st = dot_impl(C, t, C->scratch2, C->N_e, 1))) return st;                   // num = v.A T v
+        if ((st = s1_pair_t(C, 1, w, C->scratch2, C->s1v[0], C->s1v[1]))) return st;
+        if ((st = dot_impl(C, t, C->scratch2, C->N_e, 2))) return st;                   // |T v|_A^2
+        double host[3];
+        CK(cudaMemcpyAsync(host, C->dots, 3 * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+        if (!std::isfinite(host[0]) || !std::isfinite(host[1]) || !(host[2] > 0.0) || !(host[0] > 0.0))
+            return SMX_ENONFINITE;
+        lam = host[1] / host[0];
+        const double sc = 1.0 / std::sqrt(host[2]);
+        if ((st = run(C, 7, 1, [&] { return launch_scale_copy(w, v, sc, C->N_e, C->stream); }))) return st;
+        if (it > 0 && std::fabs(lam - lam_old) <= tol * std::fabs(lam)) break;
+        lam_old = lam;
+    }
+    if (!(lam > 0.0)) return SMX_ENONFINITE;
+    *dt_max = 2.0 / std::sqrt(lam);
     return SMX_OK;
 }
 

@@ -258,4 +258,17 @@ cudaError_t launch_dot(const double* x, const double* y, long long n, double* pa
 cudaError_t launch_scale_copy(const double* x, double* y, double a, long long n, cudaStream_t s);
 cudaError_t launch_zero(double* y, long long n, cudaStream_t s);  // y = 0 as a kernel of the launch chain
 
+// ---- preconditioned conjugate gradients of scheme 1 (kernels.cu); scalars live on the device:
+// scal[0] = r.z, scal[1] = p.Ap, scal[2] = r.r, scal[3] = new r.z, scal[4] = y.y
+enum CgScalar { kCgRz = 0, kCgPAp = 1, kCgRr = 2, kCgRzNew = 3, kCgYy = 4, kCgCount = 5 };
+// x += alpha p, r -= alpha Ap with alpha = r.z / p.Ap (0 when p.Ap = 0)
+cudaError_t launch_cg_xr(double* x, double* r, const double* p, const double* Ap, const double* scal, long long n,
+                         cudaStream_t s);
+// p = z + beta p with beta = new r.z / r.z (0 when r.z = 0); then r.z = new r.z (one thread, after the grid:
+// a second tiny kernel)
+cudaError_t launch_cg_p(double* p, const double* z, double* scal, long long n, cudaStream_t s);
+// r = y - r (in place: r holds M x on entry)
+cudaError_t launch_sub_from(const double* y, double* r, long long n, cudaStream_t s);
+cudaError_t launch_copy(const double* x, double* y, long long n, cudaStream_t s);
+
 }  // namespace smx

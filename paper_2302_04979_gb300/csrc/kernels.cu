@@ -663,6 +663,60 @@ cudaError_t launch_zero(double* y, long long n, cudaStream_t s) {
     return launch_k(zero_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, y, n);
 }
 
+// ------------------------------------------------------------------ conjugate gradients (scheme 1)
+__global__ void cg_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                             const double* __restrict__ Ap, const double* __restrict__ scal, long long n) {
+    const double pap = scal[kCgPAp];
+    const double alpha = pap > 0.0 ? scal[kCgRz] / pap : 0.0;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) {
+        x[i] = fma(alpha, p[i], x[i]);
+        r[i] = fma(-alpha, Ap[i], r[i]);
+    }
+}
+
+__global__ void cg_p_kernel(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal,
+                            long long n) {
+    const double rz = scal[kCgRz];
+    const double beta = rz > 0.0 ? scal[kCgRzNew] / rz : 0.0;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void cg_shift_kernel(double* scal) { scal[kCgRz] = scal[kCgRzNew]; }
+
+__global__ void sub_from_kernel(const double* __restrict__ y, double* __restrict__ r, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) r[i] = y[i] - r[i];
+}
+
+__global__ void copy_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i];
+}
+
+cudaError_t launch_cg_xr(double* x, double* r, const double* p, const double* Ap, const double* scal, long long n,
+                         cudaStream_t s) {
+    if (n > 0) cg_xr_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, r, p, Ap, scal, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p(double* p, const double* z, double* scal, long long n, cudaStream_t s) {
+    if (n > 0) cg_p_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, z, scal, n);
+    cg_shift_kernel<<<1, 1, 0, s>>>(scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_from(const double* y, double* r, long long n, cudaStream_t s) {
+    if (n > 0) sub_from_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, r, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const double* x, double* y, long long n, cudaStream_t s) {
+    if (n > 0) copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ batched cavities
 // One persistent (cooperative) launch runs a whole leapfrog step of many
 // independent cavities: ten phases separated by grid barriers,

@@ -43,7 +43,8 @@ class Material(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int * 3), ("nel", ctypes.c_int * 3), ("geometry", ctypes.c_int),
                 ("geom_amplitude", ctypes.c_double), ("eps", Material), ("mu", Material),
-                ("precision", ctypes.c_int), ("geom_fn", GEOMETRY_FN), ("geom_user", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("geom_fn", GEOMETRY_FN), ("geom_user", ctypes.c_void_p),
+                ("scheme1", ctypes.c_int)]
 
 
 class SmxError(RuntimeError):
@@ -91,6 +92,13 @@ _SIGS = {
     "smx_hodge_star": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_hodge_star_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "smx_step": [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int],
+    "smx_scheme1_star": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                         ctypes.POINTER(ctypes.c_int)],
+    "smx_step_scheme1": [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "smx_energy_scheme1": [ctypes.c_void_p] * 5 + [ctypes.POINTER(ctypes.c_double)],
+    "smx_cfl_scheme1": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
     "smx_energy": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                    ctypes.POINTER(ctypes.c_double)],
     "smx_cfl": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -194,7 +202,7 @@ def geometry_callback(mapping):
     return GEOMETRY_FN(cb)
 
 
-def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64"):
+def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64", scheme1=False):
     """geometry: "identity", "sine_bump" (amplitude) or a map object (see geometry_callback)."""
     P = Params()
     p = np.broadcast_to(np.asarray(p, dtype=int), (3,))
@@ -212,15 +220,17 @@ def make_params(p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, pr
     P.eps, k1 = material(eps)
     P.mu, k2 = material(mu)
     P.precision = {"fp64": FP64, "mixed": MIXED, "mixed_refined": MIXED_REFINED}[precision]
+    P.scheme1 = 1 if scheme1 else 0
     return P, keep + k1 + k2
 
 
 class Context:
     """Owns an smx_ctx; the device workspace is a torch tensor bound by ``bind``."""
 
-    def __init__(self, p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64"):
+    def __init__(self, p, nel, geometry="identity", amplitude=0.05, eps=1.0, mu=1.0, precision="fp64",
+                 scheme1=False):
         lib = _lib()
-        P, keep = make_params(p, nel, geometry, amplitude, eps, mu, precision)
+        P, keep = make_params(p, nel, geometry, amplitude, eps, mu, precision, scheme1)
         h = ctypes.c_void_p()
         _check(lib.smx_create(ctypes.byref(P), ctypes.byref(h)), "smx_create")
         # a geometry callback is called again by smx_project: keep it alive with the context
@@ -369,6 +379,36 @@ class Context:
     def step(self, d, b, e, h, dt, nsteps, jhat=None, amp=None):
         _check(_lib().smx_step(self.h, _ptr(d), _ptr(b), _ptr(e), _ptr(h), _ptr(jhat), _ptr(amp), float(dt),
                                int(nsteps)), "smx_step")
+
+    # ---- scheme 1 (mass-matrix Hodge stars), context created with scheme1=True
+    def scheme1_star(self, field, x, out, tol=1e-13, maxit=200):
+        it = ctypes.c_int()
+        _check(_lib().smx_scheme1_star(self.h, field, _ptr(x), _ptr(out), float(tol), int(maxit), ctypes.byref(it)),
+               "smx_scheme1_star")
+        return it.value
+
+    def step_scheme1(self, d, b, e, h, dt, nsteps, jhat=None, amp=None, tol=1e-13, maxit=200):
+        it = ctypes.c_int()
+        _check(_lib().smx_step_scheme1(self.h, _ptr(d), _ptr(b), _ptr(e), _ptr(h), _ptr(jhat), _ptr(amp), float(dt),
+                                       int(nsteps), float(tol), int(maxit), ctypes.byref(it)), "smx_step_scheme1")
+        return it.value
+
+    def energy_scheme1(self, d, b, e, h):
+        out = ctypes.c_double()
+        _check(_lib().smx_energy_scheme1(self.h, _ptr(d), _ptr(b), _ptr(e), _ptr(h), ctypes.byref(out)),
+               "smx_energy_scheme1")
+        return out.value
+
+    def cfl_scheme1(self, iters=300, tol=1e-10, cg_tol=1e-12, cg_maxit=200):
+        import torch
+        dev = self.workspace.device
+        v = torch.empty(self.N_e, dtype=torch.float64, device=dev)
+        w = torch.empty_like(v)
+        t = torch.empty(self.N_h, dtype=torch.float64, device=dev)
+        out = ctypes.c_double()
+        _check(_lib().smx_cfl_scheme1(self.h, int(iters), float(tol), _ptr(v), _ptr(w), _ptr(t), float(cg_tol),
+                                      int(cg_maxit), ctypes.byref(out)), "smx_cfl_scheme1")
+        return out.value
 
     def step_host(self, d, b, e, h, dt, nsteps, jhat=None, amp=None):
         """Leapfrog on host (CPU, ideally pinned) float64 tensors; copies in and out inside the call."""
