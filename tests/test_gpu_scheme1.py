@@ -69,8 +69,12 @@ def test_scheme1_steps_match_oracle(name):
     errs = [rel_l2(to_host(g), w) for g, w in zip(st, want)]
     print("\n%s scheme 1, %d steps: rel L2 d %.2e b %.2e e %.2e h %.2e; max CG iterations %d" % (name, n, *errs, iters))
     assert max(errs) < 1e-10
-    # energy with the pairing matrices (Sec. 3.3) against the oracle's mass-matrix form
-    Eg = ctx.energy_scheme1(*st)
+    # energy with the pairing matrices (Sec. 3.3) against the oracle's mass-matrix form, at the
+    # synchronised time (the step returns h at the half step: take the star of the final b)
+    from paper_2302_04979_gb300 import smx
+    hb = torch.empty_like(st[3])
+    ctx.scheme1_star(smx.FIELD_B, st[1], hb, tol=1e-13)
+    Eg = ctx.energy_scheme1(st[0], st[1], st[2], hb)
     Eo = S.energy(want[0], want[1])[0]
     assert abs(Eg - Eo) < 1e-10 * abs(Eo)
 
