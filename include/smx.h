@@ -408,8 +408,11 @@ int smx_hodge_star_mixed(smx_ctx* ctx, int field, const double* x, double* out);
  *   b' = b_n - a D^1 S_E d_n,  d_{n+1} = d_n + dt (D~^1 S_H b' - s_n jhat),
  *   b_{n+1} = b' - a D^1 S_E d_{n+1}.
  * Its transpose uses D~^1 = (D^1)^T, the pairing sweeps with the transposed
- * 1D factors (K_1^{-T}, K~_1^{-T}) and the symmetric masses.  FP64 contexts
- * only (SMX_ESTATE otherwise). */
+ * 1D factors (K_1^{-T}, K~_1^{-T}) and the symmetric masses.  FP64 contexts, and
+ * SMX_MIXED_REFINED contexts, whose reverse step takes the arithmetic of their
+ * forward step: each K^{-T} by FP32 sweeps with the transposed factors plus one
+ * refinement with an FP64 residual, each mass apply by the FP32 kernels with FP64
+ * sums (SMX_ESTATE for SMX_MIXED). */
 
 /* Receiver points for a misfit: R maps e (N_e) to the three parametric
  * components of the discrete electric 1-form (basis of X^1_{h,0}, Sec. 2.3)

@@ -19,12 +19,17 @@ from . import smx
 
 
 class LeapfrogProblem:
-    """One FP64 context with block permittivity and receivers, plus the fixed parts of the run."""
+    """One context with block permittivity and receivers, plus the fixed parts of the run.
+
+    precision "fp64" (default) or "mixed_refined": the forward steps and the reverse steps both in
+    that arithmetic (the refined mixed form's reverse step uses its FP32 operators with one FP64
+    residual refinement of each transposed Kronecker solve)."""
 
     def __init__(self, p, nel, eps_blocks, receivers_xhat, d0, b0, jhat, dt, nsteps, geometry="identity",
-                 amplitude=0.05, mu=1.0, device="cuda"):
+                 amplitude=0.05, mu=1.0, device="cuda", precision="fp64"):
         eps_blocks = np.asarray(eps_blocks, dtype=np.float64)
-        self.ctx = smx.Context(p, nel, geometry=geometry, amplitude=amplitude, eps=("blocks", eps_blocks), mu=mu)
+        self.ctx = smx.Context(p, nel, geometry=geometry, amplitude=amplitude, eps=("blocks", eps_blocks), mu=mu,
+                               precision=precision)
         self.ctx.receivers_set(receivers_xhat)
         self.ctx.bind(device)
         self.eps_shape = eps_blocks.shape

@@ -169,6 +169,10 @@ struct smx_ctx {
     size_t o_t64 = 0;
     double* t64 = nullptr;
     BandApplyArgs band[2][3];
+    // refined reverse step: FP32 sweeps and FP64 residual passes with the transposed 1D factors,
+    // [which][axis] with which = 0 for K_1^T (D layout), 1 for K~_1^T (B layout)
+    LineF32Args ln32T[2][3];
+    BandApplyArgs bandT[2][3];
 };
 
 namespace {
@@ -803,6 +807,52 @@ int step_refined(smx_ctx* C, double* d, double* b, double* e, double* h, const d
         if ((st = curl_primal_impl(C, e, b, (n + 1 == nsteps) ? -0.5 * dt : -dt, zero))) return st;
     }
     return SMX_OK;
+}
+
+// ---- refined mixed reverse step: the transposed stars S^T = M K^{-T} in the arithmetic of the
+// refined forward step.  x = K^{-T} y (which = 0: K_1^T, 1: K~_1^T; y, x FP64, distinct): x0 by
+// FP32 banded sweeps with the transposed factors, r = y - K^T x0 by FP64 banded passes, one FP32
+// correction, x = x0 + c.  Uses e32 / h32, y32, t64 and the state vectors as scratch.
+int solveT_refined(smx_ctx* C, int which, const double* y, double* x) {
+    const int h = which == 0 ? 1 : 0;
+    const long long n = C->fld[which == 0 ? SMX_FIELD_D : SMX_FIELD_B].total;
+    float* x0 = which == 0 ? C->e32 : C->h32;
+    double* t2 = C->state;
+    int st;
+    auto sweeps = [&](const double* in64, float* out) {
+        for (int a = 0; a < 3; ++a) {
+            const int r = run(C, 14 + a, 1, [&] {
+                return launch_line_f32(C->ln32T[which][a], C->p[a] - 1, false, a == 0 ? in64 : nullptr,
+                                       a == 0 ? nullptr : out, out, C->stream);
+            });
+            if (r) return r;
+        }
+        return SMX_OK;
+    };
+    (void)h;
+    if ((st = sweeps(y, x0))) return st;
+    if ((st = run(C, 27, 1, [&] { return launch_band_apply(C->bandT[which][0], nullptr, x0, nullptr, C->t64, C->stream); })))
+        return st;
+    if ((st = run(C, 27, 1, [&] { return launch_band_apply(C->bandT[which][1], C->t64, nullptr, nullptr, t2, C->stream); })))
+        return st;
+    if ((st = run(C, 27, 1, [&] { return launch_band_apply(C->bandT[which][2], t2, nullptr, y, C->t64, C->stream); })))
+        return st;
+    if ((st = sweeps(C->t64, C->y32))) return st;
+    return run(C, 17, 1, [&] { return launch_refine_sum(x0, C->y32, x, n, C->stream); });
+}
+
+// out += M x (h = 0: M^2_{1/mu}, 1: M~^2_{1/eps}) with the mixed step's FP32 mass kernels (element
+// contributions summed in FP64) for a refined context, else the FP64 mass kernels.
+int mass_acc_any(smx_ctx* C, int h, const double* x, double* out) {
+    if (C->precision != SMX_MIXED_REFINED) return hodge_apply_acc_impl(C, h, x, out);
+    int st = mass_f32(C, h, x, false);  // into the scratch vector
+    if (st) return st;
+    const long long n = C->fld[kFieldOfHodge[h]].total;
+    return run(C, 20, 1, [&] { return launch_axpy(C->scratch, out, 1.0, n, C->stream); });
+}
+
+int solveT_any(smx_ctx* C, int which, const double* y, double* x) {
+    return C->precision == SMX_MIXED_REFINED ? solveT_refined(C, which, y, x) : solveT_impl(C, which, y, x);
 }
 
 // ---- scheme 1 (Sec. 3.3): Hodge stars by mass-matrix solves, for comparison with scheme 2
@@ -1464,6 +1514,25 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
         }
     }
     if (C->precision == SMX_MIXED_REFINED) {
+        for (int which = 0; which < 2; ++which) {
+            const int fld = which == 0 ? SMX_FIELD_D : SMX_FIELD_B;
+            for (int a = 0; a < 3; ++a) {
+                LineF32Args& Lt = C->ln32T[which][a];
+                BandApplyArgs& Bt = C->bandT[which][a];
+                Lt.field = Bt.field = C->fld[fld];
+                Lt.axis = Bt.axis = a;
+                Bt.kl = C->p[a] - 1;
+                for (int c = 0; c < 3; ++c) {
+                    const int w = factor_index(which, c, a) ^ 2;  // the transposed factor
+                    Lt.L[c] = reinterpret_cast<const float2*>(ws + C->o_fac32[a][w][0]);
+                    Lt.U[c] = reinterpret_cast<const float2*>(ws + C->o_fac32[a][w][1]);
+                    Lt.dinv[c] = reinterpret_cast<const float2*>(ws + C->o_fac32[a][w][2]);
+                    Lt.mass[c] = nullptr;
+                    Lt.deg[c] = 0;
+                    Bt.band[c] = reinterpret_cast<const double*>(ws + C->o_band[a][w]);
+                }
+            }
+        }
         C->t64 = reinterpret_cast<double*>(ws + C->o_t64);
         for (int h = 0; h < 2; ++h) {
             const int fld = kFieldOfHodge[h], which = h == 0 ? 1 : 0;  // M^2 pairs with K~_1, M~^2 with K_1
@@ -2136,7 +2205,7 @@ int smx_step_adjoint(smx_ctx* C, const double* d_n, const double* d_np1, double*
                      const double* ebar, const double* jhat, double dt, double* amp_bar, double* eps_bar) {
     NEED_WS(C);
     if (!d_n || !d_np1 || !dbar || !bbar || !(dt > 0.0) || !std::isfinite(dt)) return SMX_EINVAL;
-    if (C->precision != SMX_FP64) return SMX_ESTATE;
+    if (C->precision == SMX_MIXED) return SMX_ESTATE;  // FP64 or the refined mixed form
     if (eps_bar && !C->eps_blocks) return SMX_EINVAL;
     const double a = 0.5 * dt;
     double* A1 = C->scratch;
@@ -2146,9 +2215,9 @@ int smx_step_adjoint(smx_ctx* C, const double* d_n, const double* d_np1, double*
     // w = dbar + S_E^T (-a D^1^T bbar), with D^1^T = D~^1; eps pair (z1, d_{n+1})
     CK(cudaMemsetAsync(A1, 0, be, C->stream));
     if ((st = curl_dual_impl(C, bbar, A1, -a, nullptr, nullptr, 0, 0.0))) return st;
-    if ((st = solveT_impl(C, 0, A1, A2))) return st;
+    if ((st = solveT_any(C, 0, A1, A2))) return st;
     if (eps_bar && (st = pair_impl(C, A2, d_np1, eps_bar))) return st;
-    if ((st = hodge_apply_acc_impl(C, 1, A2, dbar))) return st;
+    if ((st = mass_acc_any(C, 1, A2, dbar))) return st;
     // source amplitude: sbar_n = -dt jhat^T w
     if (jhat && amp_bar) {
         if ((st = run(C, 7, 2, [&] { return launch_dot(jhat, dbar, C->N_e, C->partial, amp_bar, C->stream); })))
@@ -2158,27 +2227,27 @@ int smx_step_adjoint(smx_ctx* C, const double* d_n, const double* d_np1, double*
     // bbar' = bbar + dt S_H^T D~^1^T w, with D~^1^T = D^1
     CK(cudaMemsetAsync(A1, 0, bh, C->stream));
     if ((st = curl_primal_impl(C, dbar, A1, dt))) return st;
-    if ((st = solveT_impl(C, 1, A1, A2))) return st;
-    if ((st = hodge_apply_acc_impl(C, 0, A2, bbar))) return st;
+    if ((st = solveT_any(C, 1, A1, A2))) return st;
+    if ((st = mass_acc_any(C, 0, A2, bbar))) return st;
     // dbar_n = w + S_E^T (-a D~^1 bbar' + ebar); eps pair (z3, d_n)
     CK(cudaMemsetAsync(A1, 0, be, C->stream));
     if ((st = curl_dual_impl(C, bbar, A1, -a, nullptr, nullptr, 0, 0.0))) return st;
     if (ebar && (st = run(C, 20, 1, [&] { return launch_axpy(ebar, A1, 1.0, C->N_e, C->stream); }))) return st;
-    if ((st = solveT_impl(C, 0, A1, A2))) return st;
+    if ((st = solveT_any(C, 0, A1, A2))) return st;
     if (eps_bar && (st = pair_impl(C, A2, d_n, eps_bar))) return st;
-    return hodge_apply_acc_impl(C, 1, A2, dbar);
+    return mass_acc_any(C, 1, A2, dbar);
 }
 
 int smx_adjoint_terminal(smx_ctx* C, const double* d_N, const double* ebar, double* dbar, double* eps_bar) {
     NEED_WS(C);
     if (!d_N || !ebar || !dbar) return SMX_EINVAL;
-    if (C->precision != SMX_FP64) return SMX_ESTATE;
+    if (C->precision == SMX_MIXED) return SMX_ESTATE;  // FP64 or the refined mixed form
     if (eps_bar && !C->eps_blocks) return SMX_EINVAL;
     int st;
-    if ((st = solveT_impl(C, 0, ebar, C->scratch2))) return st;
+    if ((st = solveT_any(C, 0, ebar, C->scratch2))) return st;
     if (eps_bar && (st = pair_impl(C, C->scratch2, d_N, eps_bar))) return st;
     CK(cudaMemsetAsync(dbar, 0, (size_t)C->N_e * sizeof(double), C->stream));
-    return hodge_apply_acc_impl(C, 1, C->scratch2, dbar);
+    return mass_acc_any(C, 1, C->scratch2, dbar);
 }
 
 // ---- batched cavities

@@ -28,11 +28,11 @@ def _small(geometry):
                 amps=amps, obs=obs, P=P)
 
 
-def _gpu_grad(case, checkpoint_every=None):
+def _gpu_grad(case, checkpoint_every=None, precision="fp64"):
     import torch
     from paper_2302_04979_gb300 import adjoint as gadj
     prob = gadj.LeapfrogProblem(case["p"], case["nel"], case["eps"], case["xr"], case["d0"], case["b0"], case["jhat"],
-                                case["dt"], case["nsteps"], geometry=case["geometry"])
+                                case["dt"], case["nsteps"], geometry=case["geometry"], precision=precision)
     if checkpoint_every:
         prob.k = checkpoint_every
     eps_t = torch.tensor(case["eps"], dtype=torch.float64, requires_grad=True)
@@ -54,6 +54,32 @@ def test_gradient_matches_oracle(geometry):
     assert abs(loss - loss_ref) <= 1e-11 * loss_ref
     assert rel_l2(geps, geps_ref) < 1e-10
     assert rel_l2(gamp, gamp_ref) < 1e-10
+
+
+@pytest.mark.parametrize("geometry", ["identity", "sine_bump"])
+def test_refined_mixed_gradient_matches_oracle(geometry):
+    """The refined mixed form's forward and reverse steps (FP32 operators, one FP64-residual
+    refinement of every Kronecker solve and of every transposed one) against the oracle's FP64
+    gradient: the remaining difference is the FP32 arithmetic of the mass applies."""
+    case = _small(geometry)
+    loss_ref, geps_ref, gamp_ref = case["P"].gradient(case["eps"], case["amps"], case["obs"])
+    loss, geps, gamp, _ = _gpu_grad(case, precision="mixed_refined")
+    print("\n%s refined mixed: loss rel %.2e; rel L2 grad eps %.2e, amps %.2e"
+          % (geometry, abs(loss - loss_ref) / loss_ref, rel_l2(geps, geps_ref), rel_l2(gamp, gamp_ref)))
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    assert rel_l2(geps, geps_ref) < 1e-5
+    assert rel_l2(gamp, gamp_ref) < 1e-5
+
+
+def test_plain_mixed_has_no_reverse_step():
+    import torch
+    from paper_2302_04979_gb300 import smx
+    ctx = smx.Context(2, 3, eps=("blocks", np.ones((1, 1, 1))), precision="mixed").bind()
+    v = torch.zeros(ctx.N_e, dtype=torch.float64, device="cuda")
+    w = torch.zeros(ctx.N_h, dtype=torch.float64, device="cuda")
+    with pytest.raises(smx.SmxError) as err:
+        ctx.step_adjoint(v, v, v.clone(), w, 0.01)
+    assert err.value.status == smx.ESTATE
 
 
 def test_checkpoint_spacing_does_not_change_the_gradient():
@@ -98,6 +124,7 @@ def test_adjoint_configuration_finite_differences():
         return float(gadj.misfit(prob.forward(torch.as_tensor(a).cuda()), obs, dt))
 
     worst = 0.0
+    fds = []
     for k in range(8):
         ve = synth.normal(2400 + k, eps.size).reshape(eps.shape)
         va = synth.normal(2500 + k, nsteps)
@@ -106,7 +133,26 @@ def test_adjoint_configuration_finite_differences():
         an = float(np.sum(geps * ve) + gamp @ va)
         worst = max(worst, abs(fd - an) / abs(an))
         print("direction %d: FD %.10e adjoint %.10e rel %.2e" % (k, fd, an, abs(fd - an) / abs(an)))
+        fds.append(fd)
     assert worst < 1e-6
+    # the refined mixed form's gradient (forward and reverse in its arithmetic) against the same
+    # FP64 central differences
+    probm = gadj.LeapfrogProblem(p, nel, eps, xr, d0, b0, jhat, dt, nsteps, geometry="sine_bump",
+                                 precision="mixed_refined")
+    eps_m = torch.tensor(eps, dtype=torch.float64, requires_grad=True)
+    amps_m = amps_dev.clone().requires_grad_(True)
+    lossm = gadj.misfit(gadj.LeapfrogTraces.apply(eps_m, amps_m, probm), obs, dt)
+    lossm.backward()
+    gm_eps, gm_amp = eps_m.grad.numpy(), amps_m.grad.cpu().numpy()
+    worst_m = 0.0
+    for k in range(8):
+        ve = synth.normal(2400 + k, eps.size).reshape(eps.shape)
+        va = synth.normal(2500 + k, nsteps)
+        an = float(np.sum(gm_eps * ve) + gm_amp @ va)
+        worst_m = max(worst_m, abs(fds[k] - an) / abs(fds[k]))
+        print("direction %d: refined mixed adjoint %.10e rel to FP64 FD %.2e" % (k, an, abs(fds[k] - an) / abs(fds[k])))
+    print("loss FP64 %.12e, refined mixed %.12e" % (float(loss), float(lossm)))
+    assert worst_m < 1e-4
 
 
 @pytest.mark.parametrize("geometry", ["identity", "sine_bump"])
