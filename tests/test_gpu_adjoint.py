@@ -152,7 +152,7 @@ def test_adjoint_configuration_finite_differences():
         worst_m = max(worst_m, abs(fds[k] - an) / abs(fds[k]))
         print("direction %d: refined mixed adjoint %.10e rel to FP64 FD %.2e" % (k, an, abs(fds[k] - an) / abs(fds[k])))
     print("loss FP64 %.12e, refined mixed %.12e" % (float(loss), float(lossm)))
-    assert worst_m < 1e-4
+    assert worst_m < 1e-5   # measured 0.4e-6 .. 3.3e-6
 
 
 @pytest.mark.parametrize("geometry", ["identity", "sine_bump"])
