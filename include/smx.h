@@ -450,18 +450,21 @@ int smx_step_adjoint(smx_ctx* ctx, const double* d_n, const double* d_np1, doubl
 int smx_adjoint_terminal(smx_ctx* ctx, const double* d_N, const double* ebar, double* dbar, double* eps_bar);
 
 /* ==== Batched cavities: one persistent launch per leapfrog step ====
- * Many independent cavities (each its own bound FP64 context: identity map,
- * constant mu, block or constant eps; any p and nel) stepped together: one
- * cooperative launch per step runs the ten phases of the kick-drift-kick
- * step (the same device code as smx_step) over a flat work list of
- * (cavity, unit) items, with grid barriers between phases.  Each barrier wait
- * is bounded (one second); see smx_batch_status. */
+ * Many independent cavities (each its own bound FP64 context: any p and nel,
+ * any map and material) stepped together: one cooperative launch per step runs
+ * the eleven phases of the kick-drift-kick step (the same device code as
+ * smx_step: fused mass + solve passes for a star with constant material on the
+ * identity map, else a block-Kronecker or quadrature mass apply followed by the
+ * pairing sweeps) over a flat work list of (cavity, unit) items, with grid
+ * barriers between phases.  On a non-default stream the launches of one
+ * smx_batch_step call are captured into a CUDA graph and replayed while nsteps
+ * is unchanged (the step index lives in a device counter).  Each barrier wait is
+ * bounded (one second); see smx_batch_status. */
 typedef struct smx_batch smx_batch;
 
 /* Build a batch over n bound contexts (host arrays; the contexts must outlive
  * the batch and share one stream, that of ctxs[0]).  Host memory only.
- * Errors: SMX_EINVAL (a context is unbound, mixed precision, curved, or has
- * non-constant mu or quadrature-mode eps), SMX_ENOMEM. */
+ * Errors: SMX_EINVAL (a context is unbound or not SMX_FP64), SMX_ENOMEM. */
 int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out);
 int smx_batch_destroy(smx_batch* batch);
 
@@ -477,8 +480,13 @@ int smx_batch_bind_workspace(smx_batch* batch, void* device_ptr, size_t bytes);
 int smx_batch_set_state(smx_batch* batch, int i, double* d, double* b, double* e, double* h, const double* jhat,
                         const double* amp, double dt);
 
-/* nsteps leapfrog steps of every cavity: nsteps launches on the stream. */
+/* nsteps leapfrog steps of every cavity: nsteps launches on the stream (one graph launch when
+ * captured). */
 int smx_batch_step(smx_batch* batch, int nsteps);
+
+/* CUDA-graph capture of smx_batch_step (default on; used on a non-default stream).  enable = 0
+ * launches eagerly. */
+int smx_batch_set_graphs(smx_batch* batch, int enable);
 
 /* Synchronise; SMX_ETIMEOUT if a grid barrier gave up since the last call
  * (the results of that launch are not valid), else SMX_OK.  Once a barrier

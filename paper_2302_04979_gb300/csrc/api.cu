@@ -2255,15 +2255,27 @@ struct smx_batch {
     std::vector<smx_ctx*> ctx;
     std::vector<BatchCavity> cav;
     std::vector<int2> items[kBatchPhases];
-    size_t o_cav = 0, o_items[kBatchPhases] = {}, o_bar = 0, o_status = 0, total = 0;
+    size_t o_cav = 0, o_items[kBatchPhases] = {}, o_bar = 0, o_status = 0, o_stepctr = 0, total = 0;
     unsigned char* ws = nullptr;
     cudaStream_t stream = nullptr;
     int maxn = 0, maxkl = 0, max_nloc = 0;
+    size_t max_quad = 0;  // shared memory (doubles) of the largest quadrature element
     int line_warps = 0, grid = 0;
     size_t smem = 0;
-    long long steps = 0;  // amplitude index of the next step
+    long long steps = 0;  // amplitude index of the next step (host mirror of the device counter)
     bool state_set = false;
     unsigned long long wait_ns = 1000000000ull;  // grid-barrier wait limit
+    // captured CUDA graph of the last smx_batch_step call's nsteps launches
+    int use_graphs = 1;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    ~smx_batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
+    void drop_graph() {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
 };
 
 namespace {
@@ -2300,9 +2312,8 @@ int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out) {
     try {
         for (int i = 0; i < n; ++i) {
             smx_ctx* C = ctxs[i];
-            // identity map, FP64, constant mu (separable star of B), block or constant eps, bound
-            if (!C || !C->ws || C->precision != SMX_FP64 || C->geometry != SMX_GEOM_IDENTITY ||
-                !C->hodge[0].separable || C->hodge[1].mode != 0) {
+            // FP64, bound; any map and material
+            if (!C || !C->ws || C->precision != SMX_FP64) {
                 delete B;
                 return SMX_EINVAL;
             }
@@ -2315,30 +2326,50 @@ int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out) {
             for (int a = 0; a < 3; ++a) {
                 K.msH[a] = C->ms[0][a];
                 K.msD[a] = C->ms[1][a];
+                K.solveH[a] = C->solve[1][a];
                 K.solveE[a] = C->solve[0][a];
                 K.kl[a] = C->p[a] - 1;
                 B->maxkl = std::max(B->maxkl, C->p[a] - 1);
                 for (int c = 0; c < 3; ++c)
                     for (int f = 0; f < 4; ++f) B->maxn = std::max(B->maxn, C->fld[f].c[c].n[a]);
             }
+            K.hbB = C->hb[0];
             K.hbD = C->hb[1];
+            K.hqB = C->hq[0];
+            K.hqD = C->hq[1];
+            K.sepB = C->hodge[0].separable ? 1 : 0;
             K.sepD = C->hodge[1].separable ? 1 : 0;
+            K.modeB = C->hodge[0].mode;
+            K.modeD = C->hodge[1].mode;
             K.y = C->scratch;
-            B->max_nloc = std::max(B->max_nloc, C->hodge[1].max_nloc);
-            B->cav.push_back(K);
-            batch_curl_items(B->items[0], i, K.fB);
-            for (int a = 0; a < 3; ++a) batch_line_items(B->items[1 + a], i, K.fH, a);
-            batch_curl_items(B->items[4], i, K.fD);
-            if (!K.sepD) {
-                const long long nz = (K.fE.total + kBatchThreads * 8 - 1) / (kBatchThreads * 8);
-                for (long long z = 0; z < nz; ++z) B->items[4].push_back(make_int2(i, batch_zero_unit((int)z)));
-                const HodgeHost& H = C->hodge[1];
-                const int nt = H.ntile[0] * H.ntile[1] * H.ntile[2];
-                for (int c = 0; c < 3; ++c)
-                    for (int t = 0; t < nt; ++t) B->items[5].push_back(make_int2(i, batch_comp_unit(c, t)));
+            for (int h = 0; h < 2; ++h) {
+                const HodgeHost& H = C->hodge[h];
+                if (H.mode == 0) B->max_nloc = std::max(B->max_nloc, H.max_nloc);
+                else B->max_quad = std::max(B->max_quad, hodge_quad_smem_doubles(H.q[0], H.q[1], H.q[2]));
             }
-            for (int a = 0; a < 3; ++a) batch_line_items(B->items[6 + a], i, K.fD, a);
-            B->items[9] = B->items[0];
+            B->cav.push_back(K);
+            // the mass apply of a star that is not fused: zero y in the curl phase before it, then
+            // one unit per (component, tile) or per element
+            auto mass_items = [&](int h, int zero_phase, int mass_phase, long long ntot) {
+                const HodgeHost& H = C->hodge[h];
+                const long long nz = (ntot + kBatchThreads * 8 - 1) / (kBatchThreads * 8);
+                for (long long z = 0; z < nz; ++z) B->items[zero_phase].push_back(make_int2(i, batch_zero_unit((int)z)));
+                if (H.mode == 0) {
+                    const int nt = H.ntile[0] * H.ntile[1] * H.ntile[2];
+                    for (int c = 0; c < 3; ++c)
+                        for (int t = 0; t < nt; ++t) B->items[mass_phase].push_back(make_int2(i, batch_comp_unit(c, t)));
+                } else {
+                    const int ne = C->nel[0] * C->nel[1] * C->nel[2];
+                    for (int e = 0; e < ne; ++e) B->items[mass_phase].push_back(make_int2(i, e));
+                }
+            };
+            batch_curl_items(B->items[0], i, K.fB);
+            batch_curl_items(B->items[10], i, K.fB);
+            if (!K.sepB) mass_items(0, 0, 1, K.fB.total);
+            for (int a = 0; a < 3; ++a) batch_line_items(B->items[2 + a], i, K.fH, a);
+            batch_curl_items(B->items[5], i, K.fD);
+            if (!K.sepD) mass_items(1, 5, 6, K.fD.total);
+            for (int a = 0; a < 3; ++a) batch_line_items(B->items[7 + a], i, K.fD, a);
         }
         // workspace: cavity table, item lists, barrier and status words
         size_t off = 0;
@@ -2351,6 +2382,7 @@ int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out) {
         for (int ph = 0; ph < kBatchPhases; ++ph) B->o_items[ph] = take(std::max<size_t>(1, B->items[ph].size()) * sizeof(int2));
         B->o_bar = take(2 * sizeof(unsigned));
         B->o_status = take(sizeof(unsigned));
+        B->o_stepctr = take(sizeof(unsigned));
         B->total = off;
     } catch (const std::bad_alloc&) {
         delete B;
@@ -2373,7 +2405,7 @@ int smx_batch_workspace_bytes(const smx_batch* B, size_t* bytes) {
 
 static int batch_configure(smx_batch* B, int line_warps) {
     const size_t warp = batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
-    const size_t hodge = (size_t)3 * kLMax * (kLMax + 1) + 2 * (size_t)B->max_nloc + 8;
+    const size_t hodge = std::max((size_t)3 * kLMax * (kLMax + 1) + 2 * (size_t)B->max_nloc + 8, B->max_quad);
     const size_t smem = std::max(warp * line_warps, hodge) * sizeof(double);
     if (smem > 226 * 1024) return SMX_EINVAL;
     const int per_sm = batch_blocks_per_sm(smem);
@@ -2381,6 +2413,7 @@ static int batch_configure(smx_batch* B, int line_warps) {
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (per_sm < 1) return SMX_EINVAL;
+    if (B->line_warps != line_warps || B->smem != smem || B->grid != per_sm * sms) B->drop_graph();
     B->line_warps = line_warps;
     B->smem = smem;
     B->grid = per_sm * sms;
@@ -2427,6 +2460,9 @@ static int batch_launch(smx_batch* B, int nsteps) {
             if (!K.d) return SMX_ESTATE;
         CK(cudaMemcpyAsync(B->ws + B->o_cav, B->cav.data(), B->cav.size() * sizeof(BatchCavity),
                            cudaMemcpyHostToDevice, B->stream));
+        const unsigned ctr = (unsigned)B->steps;  // the device step counter follows the host's
+        CK(cudaMemcpyAsync(B->ws + B->o_stepctr, &ctr, sizeof ctr, cudaMemcpyHostToDevice, B->stream));
+        CK(cudaStreamSynchronize(B->stream));   // ctr is a stack variable
         B->state_set = true;
     }
     BatchArgs A{};
@@ -2437,13 +2473,47 @@ static int batch_launch(smx_batch* B, int nsteps) {
     }
     A.bar = reinterpret_cast<unsigned*>(B->ws + B->o_bar);
     A.status = reinterpret_cast<unsigned*>(B->ws + B->o_status);
+    A.stepctr = reinterpret_cast<unsigned*>(B->ws + B->o_stepctr);
     A.line_warps = B->line_warps;
     A.warp_smem = (int)batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
     A.wait_ns = B->wait_ns;
-    for (int n = 0; n < nsteps; ++n) {
-        A.step = (int)B->steps++;
-        CK(launch_batch_step(A, B->grid, B->smem, B->stream));
+    // the nsteps launches as one captured CUDA graph (replayed while nsteps and the shape are
+    // unchanged; the step index comes from the device counter), eagerly on the legacy stream
+    if (B->use_graphs && B->stream != nullptr && nsteps > 0) {
+        if (!B->graph || B->graph_steps != nsteps) {
+            B->drop_graph();
+            CK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t el = cudaSuccess;
+            for (int n = 0; n < nsteps && el == cudaSuccess; ++n) el = launch_batch_step(A, B->grid, B->smem, B->stream);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(B->stream, &g);
+            if (el != cudaSuccess || ec != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return SMX_ECUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&B->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                B->graph = nullptr;
+                return SMX_ECUDA;
+            }
+            B->graph_steps = nsteps;
+        }
+        CK(cudaGraphLaunch(B->graph, B->stream));
+        B->steps += nsteps;
+        return SMX_OK;
     }
+    for (int n = 0; n < nsteps; ++n) {
+        CK(launch_batch_step(A, B->grid, B->smem, B->stream));
+        ++B->steps;
+    }
+    return SMX_OK;
+}
+
+int smx_batch_set_graphs(smx_batch* B, int enable) {
+    if (!B) return SMX_EINVAL;
+    B->use_graphs = enable ? 1 : 0;
+    if (!enable) B->drop_graph();
     return SMX_OK;
 }
 
@@ -2466,6 +2536,7 @@ int smx_batch_status(smx_batch* B) {
 
 int smx_batch_set_wait_limit(smx_batch* B, double seconds) {
     if (!B || !(seconds >= 0.0) || seconds > 60.0) return SMX_EINVAL;
+    B->drop_graph();  // the limit is a launch parameter of the captured launches
     B->wait_ns = (unsigned long long)(seconds * 1e9);
     return SMX_OK;
 }

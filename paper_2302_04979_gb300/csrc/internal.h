@@ -205,23 +205,27 @@ cudaError_t launch_hodge_block_pair(const HodgeBlockArgs& a, const PairArgs& p, 
                                     double* out, cudaStream_t s);
 
 // ---- batched cavities: one persistent launch per leapfrog step (kernels.cu)
-// Identity map, constant mu (separable Hodge star of B) and block (or
-// constant) eps; FP64.  Per cavity: its field layouts, the argument blocks of
-// its own context, its state and scratch.
+// FP64 cavities of any map and material: each Hodge star is either the fused mass + solve passes
+// (identity map, constant material: sep) or a mass apply (block-Kronecker tiles on the identity
+// map, quadrature elements otherwise) into the cavity's scratch vector y followed by the pairing
+// sweeps.  Per cavity: its field layouts, the argument blocks of its own context, state, scratch.
 struct BatchCavity {
     DevField fE, fB, fH, fD;
-    MassSolveArgs msH[3];     // Hodge star of B: fused mass + K~_1 solve per axis
-    MassSolveArgs msD[3];     // Hodge star of D when eps is constant (sepD)
-    HodgeBlockArgs hbD;       // block Hodge of D otherwise
-    SolveArgs solveE[3];      // K_1 sweeps
+    MassSolveArgs msH[3];     // star of B, sepB: fused mass + K~_1 solve per axis
+    MassSolveArgs msD[3];     // star of D, sepD
+    SolveArgs solveH[3];      // K~_1 sweeps (star of B otherwise)
+    SolveArgs solveE[3];      // K_1 sweeps (star of D otherwise)
+    HodgeBlockArgs hbB, hbD;  // block-Kronecker mass applies (mode 0)
+    HodgeQuadArgs hqB, hqD;   // quadrature mass applies (mode 1)
     double *d, *b, *e, *h, *y;
     const double* jhat;       // or null
     const double* amp;        // device, one value per step (with jhat)
     double dt;
     int kl[3];                // p - 1 per axis
-    int sepD;
+    int sepB, sepD;           // fused star
+    int modeB, modeD;         // mass apply otherwise: 0 block tiles, 1 quadrature elements
 };
-constexpr int kBatchPhases = 10;
+constexpr int kBatchPhases = 11;
 constexpr int kBatchThreads = 256;
 struct BatchArgs {
     const BatchCavity* cav;
@@ -231,13 +235,15 @@ struct BatchArgs {
     unsigned* status;       // bit 1: a grid barrier gave up
     int line_warps;         // warps of a CTA that take line items
     int warp_smem;          // doubles of shared memory per line warp
-    int step;               // index into amp
+    int step;               // index into amp (when stepctr is null)
+    unsigned* stepctr;      // device step counter: read at entry, advanced by CTA 0 at the end (graph replays)
     unsigned long long wait_ns;  // limit of each grid-barrier wait (default one second)
 };
 // unit encodings
 __host__ __device__ inline int batch_curl_unit(int c, int pb, int zc) { return (c << 28) | (zc << 14) | pb; }
 __host__ __device__ inline int batch_zero_unit(int z) { return (1 << 30) | z; }
 __host__ __device__ inline int batch_comp_unit(int c, int k) { return (c << 24) | k; }
+size_t hodge_quad_smem_doubles(int qx, int qy, int qz);
 cudaError_t launch_batch_step(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 int batch_blocks_per_sm(size_t smem);
 size_t batch_line_warp_doubles(int maxn, int kl);  // staging of one line warp

@@ -134,11 +134,9 @@ cudaError_t launch_hodge_block(const HodgeBlockArgs& a, const double* x, double*
 // integrate back against the same basis, scatter-add.  One CTA per element.
 constexpr int kQuadThreads = 128;
 
-__global__ void __launch_bounds__(kQuadThreads) hodge_quad_kernel(HodgeQuadArgs A, const double* __restrict__ x,
-                                                                  double* __restrict__ y) {
-    extern __shared__ double sm[];
-    pdl_wait();
-    const int e = blockIdx.x;
+// The work of one element by the whole CTA (any block size); sm: hodge_quad_smem_doubles(q).
+__device__ __forceinline__ void hodge_quad_element(const HodgeQuadArgs& A, int e, const double* __restrict__ x,
+                                                   double* __restrict__ y, double* sm) {
     const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
     const int el[3] = {ex, ey, ez};
     const int qx = A.q[0], qy = A.q[1], qz = A.q[2];
@@ -249,6 +247,18 @@ __global__ void __launch_bounds__(kQuadThreads) hodge_quad_kernel(HodgeQuadArgs 
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kQuadThreads) hodge_quad_kernel(HodgeQuadArgs A, const double* __restrict__ x,
+                                                                  double* __restrict__ y) {
+    extern __shared__ double sm[];
+    pdl_wait();
+    hodge_quad_element(A, blockIdx.x, x, y, sm);
+}
+
+size_t hodge_quad_smem_doubles(int qx, int qy, int qz) {
+    const size_t Qe = (size_t)qx * qy * qz;
+    return 3 * Qe + 2 * Qe * kRMax + (size_t)kRMax * kRMax * kRMax + 3 * 8 * kRMax;
 }
 
 cudaError_t launch_hodge_quad(const HodgeQuadArgs& a, const double* x, double* y, cudaStream_t s) {
@@ -719,16 +729,19 @@ cudaError_t launch_copy(const double* x, double* y, long long n, cudaStream_t s)
 
 // ------------------------------------------------------------------ batched cavities
 // One persistent (cooperative) launch runs a whole leapfrog step of many
-// independent cavities: ten phases separated by grid barriers,
-//   0 b -= dt/2 D^1 e            4 d += dt (D~^1 h - s jhat); y = 0
-//   1-3 h = A^{-1} M b per axis  5 y = M~ d (block Hodge)
-//   6-8 e = K_1^{-1} y per axis (or the fused mass + solve passes when eps
-//       is constant)               9 b -= dt/2 D^1 e
-// Each phase walks a flat list of (cavity, unit) items: whole-CTA units
-// (curl chunks, Hodge tiles, zeroing) or line units (kSolveLines lines, one
-// warp, each line warp with its own shared-memory staging).  The work of a
-// unit is the device function of the single-cavity kernel, so a batched step
-// computes exactly what the separate launches compute.
+// independent cavities: eleven phases separated by grid barriers,
+//   0 b -= dt/2 D^1 e; y = 0 (cavities whose star of B applies a mass)
+//   1 y = M b (block tiles or quadrature elements)        2-4 h = star of B per axis
+//   5 d += dt (D~^1 h - s jhat); y = 0 (star of D applies a mass)
+//   6 y = M~ d                                            7-9 e = star of D per axis
+//   10 b -= dt/2 D^1 e
+// A star is either the fused mass + solve passes (identity map, constant
+// material) or the pairing sweeps of y.  Each phase walks a flat list of
+// (cavity, unit) items: whole-CTA units (curl chunks, Hodge tiles or elements,
+// zeroing) or line units (kSolveLines lines, one warp, each line warp with its
+// own shared-memory staging).  The work of a unit is the device function of the
+// single-cavity kernel, so a batched step computes what the separate launches
+// compute.
 
 __device__ __forceinline__ unsigned long long batch_ns() {
     unsigned long long t;
@@ -822,6 +835,19 @@ __device__ __forceinline__ void batch_solve(const SolveArgs& A, int kl, int c, i
     }
 }
 
+__device__ __noinline__ void batch_hodge_element(const HodgeQuadArgs& A, int e, const double* x, double* y, double* sm) {
+    hodge_quad_element(A, e, x, y, sm);
+}
+
+// zero a chunk of y (unit z: kBatchThreads * 8 entries)
+__device__ __forceinline__ void batch_zero(const BatchCavity& K, int unit, long long n) {
+    const long long z0 = (long long)(unit & 0xFFFFFF) * (kBatchThreads * 8);
+    for (int q = 0; q < 8; ++q) {
+        const long long i = z0 + q * kBatchThreads + threadIdx.x;
+        if (i < n) K.y[i] = 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs B) {
     extern __shared__ double smb[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -829,28 +855,32 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs 
     // a barrier of an earlier launch gave up (its phases are incomplete and the
     // barrier words are stale until smx_batch_status resets them): do nothing
     if (*(volatile unsigned*)B.status & 2u) return;
+    // the step index (amplitude of the source): from the device counter when replayed from a graph
+    const int step = B.stepctr ? (int)*(volatile unsigned*)B.stepctr : B.step;
     for (int ph = 0; ph < kBatchPhases; ++ph) {
         const int2* items = B.items[ph];
         const int n = B.nitems[ph];
-        const bool line_phase = (ph >= 1 && ph <= 3) || (ph >= 6 && ph <= 8);
+        const bool line_phase = (ph >= 2 && ph <= 4) || (ph >= 7 && ph <= 9);
         if (!line_phase) {
             for (int it = blockIdx.x; it < n; it += nblocks) {
                 const int2 w = items[it];
                 const BatchCavity& K = B.cav[w.x];
-                if (ph == 0 || ph == 9) {
-                    batch_curl<false>(K, w.y, K.e, K.b, -0.5 * K.dt, nullptr, nullptr, 0);
-                } else if (ph == 4) {
-                    if (w.y & (1 << 30)) {  // zero a chunk of y
-                        const long long z0 = (long long)(w.y & 0xFFFFFF) * (kBatchThreads * 8);
-                        for (int q = 0; q < 8; ++q) {
-                            const long long i = z0 + q * kBatchThreads + threadIdx.x;
-                            if (i < K.fE.total) K.y[i] = 0.0;
-                        }
-                    } else {
-                        batch_curl<true>(K, w.y, K.h, K.d, K.dt, K.jhat, K.amp, B.step);
-                    }
-                } else {  // ph == 5: block Hodge of D into y
-                    batch_hodge_tile(K.hbD, w.y >> 24, w.y & 0xFFFFFF, K.d, K.y, smb);
+                if (ph == 0 || ph == 10) {
+                    if (w.y & (1 << 30))
+                        batch_zero(K, w.y, K.fB.total);
+                    else
+                        batch_curl<false>(K, w.y, K.e, K.b, -0.5 * K.dt, nullptr, nullptr, 0);
+                } else if (ph == 5) {
+                    if (w.y & (1 << 30))
+                        batch_zero(K, w.y, K.fD.total);
+                    else
+                        batch_curl<true>(K, w.y, K.h, K.d, K.dt, K.jhat, K.amp, step);
+                } else {  // ph == 1 or 6: mass apply into y
+                    const bool bside = ph == 1;
+                    if ((bside ? K.modeB : K.modeD) == 0)
+                        batch_hodge_tile(bside ? K.hbB : K.hbD, w.y >> 24, w.y & 0xFFFFFF, bside ? K.b : K.d, K.y, smb);
+                    else
+                        batch_hodge_element(bside ? K.hqB : K.hqD, w.y, bside ? K.b : K.d, K.y, smb);
                     __syncthreads();  // the next unit reuses the shared memory
                 }
             }
@@ -861,11 +891,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs 
                 const int2 w = items[it];
                 const BatchCavity& K = B.cav[w.x];
                 const int c = w.y >> 24, lb = w.y & 0xFFFFFF;
-                if (ph <= 3) {
-                    const int a = ph - 1;
-                    batch_mass_solve(K.msH[a], K.kl[a], c, lb, a == 0 ? K.b : K.h, K.h, sm, lane);
+                if (ph <= 4) {
+                    const int a = ph - 2;
+                    if (K.sepB)
+                        batch_mass_solve(K.msH[a], K.kl[a], c, lb, a == 0 ? K.b : K.h, K.h, sm, lane);
+                    else
+                        batch_solve(K.solveH[a], K.kl[a], c, lb, a == 0 ? K.y : K.h, K.h, sm, lane);
                 } else {
-                    const int a = ph - 6;
+                    const int a = ph - 7;
                     if (K.sepD)
                         batch_mass_solve(K.msD[a], K.kl[a], c, lb, a == 0 ? K.d : K.e, K.e, sm, lane);
                     else
@@ -876,6 +909,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_step_kernel(BatchArgs 
         }
         if (ph + 1 < kBatchPhases && !batch_barrier(B.bar, B.status, nblocks, B.wait_ns)) return;
     }
+    // every CTA read the step counter before the first barrier: advance it for the next replay
+    if (B.stepctr && blockIdx.x == 0 && threadIdx.x == 0) *B.stepctr += 1u;
 }
 
 size_t batch_line_warp_doubles(int maxn, int kl) {
@@ -899,9 +934,18 @@ int batch_blocks_per_sm(size_t smem) {
 }
 
 cudaError_t launch_batch_step(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
-    BatchArgs args = a;
-    void* params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void*)batch_step_kernel, dim3(grid), dim3(kBatchThreads), params, smem, s);
+    // a cooperative launch through the extensible launch API, which a stream capture records
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel, a);
 }
 
 }  // namespace smx

@@ -83,6 +83,7 @@ _SIGS = {
     "smx_batch_step": [ctypes.c_void_p, ctypes.c_int],
     "smx_batch_status": [ctypes.c_void_p],
     "smx_batch_set_wait_limit": [ctypes.c_void_p, ctypes.c_double],
+    "smx_batch_set_graphs": [ctypes.c_void_p, ctypes.c_int],
     "smx_batch_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "smx_curl_primal": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
     "smx_curl_dual": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -458,7 +459,8 @@ class Context:
 
 
 class Batch:
-    """Independent cavities (bound FP64 contexts) stepped by one persistent launch per step."""
+    """Independent cavities (bound FP64 contexts, any map and material) stepped by one persistent
+    launch per step, replayed as a CUDA graph on a non-default stream."""
 
     def __init__(self, contexts, device="cuda"):
         import torch
@@ -488,6 +490,9 @@ class Batch:
 
     def status(self):
         _check(_lib().smx_batch_status(self.h), "smx_batch_status")
+
+    def set_graphs(self, on):
+        _check(_lib().smx_batch_set_graphs(self.h, 1 if on else 0), "smx_batch_set_graphs")
 
     def set_wait_limit(self, seconds):
         """Limit of each grid-barrier wait (seconds; 0 makes every pending wait give up at once)."""
