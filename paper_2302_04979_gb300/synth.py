@@ -129,3 +129,25 @@ class ShearMap:
         return np.array([[one, 0.2 * z, 0.2 * y],
                          [0.1 * np.pi * np.cos(np.pi * x), one, zero],
                          [0.1 * y, 0.1 * x, 0.8 * one]])
+
+
+class QuarterCoaxMap:
+    """The quarter coaxial cable {1 < x^2 + y^2 < 2, x, y > 0, 0 < z < 1}: radius r = 1 + (sqrt 2 - 1) x^
+    and angle theta = (pi/2) y^ (the exact annular geometry that a degree-2 NURBS patch also
+    represents), F = (r cos theta, r sin theta, z^), det J = (pi/2)(sqrt 2 - 1) r > 0."""
+
+    dr = np.sqrt(2.0) - 1.0
+
+    def __call__(self, x, y, z):
+        r = 1.0 + self.dr * np.asarray(x, dtype=np.float64)
+        t = 0.5 * np.pi * np.asarray(y, dtype=np.float64)
+        return r * np.cos(t), r * np.sin(t), np.asarray(z, dtype=np.float64) + 0.0 * r
+
+    def jacobian(self, x, y, z):
+        x, y, z = np.broadcast_arrays(np.asarray(x, dtype=np.float64), y, z)
+        r = 1.0 + self.dr * x
+        t = 0.5 * np.pi * y
+        zero, one = np.zeros_like(x), np.ones_like(x)
+        return np.array([[self.dr * np.cos(t), -0.5 * np.pi * r * np.sin(t), zero],
+                         [self.dr * np.sin(t), 0.5 * np.pi * r * np.cos(t), zero],
+                         [zero, zero, one]])

@@ -11,7 +11,7 @@ from oracle import maxwell as mx
 from paper_2302_04979_gb300 import smx, synth
 from tests.gpu_util import rel_l2
 
-MAPS = {"sine_bump": synth.SineBumpMap(0.05), "shear": synth.ShearMap()}
+MAPS = {"sine_bump": synth.SineBumpMap(0.05), "shear": synth.ShearMap(), "coax": synth.QuarterCoaxMap()}
 
 
 @pytest.mark.parametrize("name", sorted(MAPS))
