@@ -1,7 +1,7 @@
 """A general geometry map given by a host callback (SMX_GEOM_CALLBACK, Sec. 2.3) on the GPU: the
 Hodge stars and leapfrog steps through the callback map against the oracle with the same map
 (1e-11), the callback sine bump against the built-in one, and the refined mixed form on the
-sheared domain (1e-5), and scheme 1 on the quarter coaxial cable (the second domain of Sec. 5.1)."""
+sheared domain (1e-5), and scheme 1 on the quarter coaxial cable (Sec. 5.1.2)."""
 import numpy as np
 import pytest
 
