@@ -658,7 +658,9 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
             if ((st = mass_f32(C, h, x, prezeroed))) return st;
             x64 = C->scratch;
         }
-        const bool tc = C->mode_kernel == SMX_MODE_TENSOR;  // AUTO: the CUDA-core kernel (no accumulation bias)
+        // AUTO: the four-digit tensor-core kernel (more accurate than the FP32 CUDA-core
+        // product, and faster on GB300: 0.132 against 0.144 ms per step at p = 3, 64^3)
+        const bool tc = C->mode_kernel != SMX_MODE_SIMT;
         auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
             return run(C, (tc ? 24 : 14) + a, 1, [&] {
                 return tc ? launch_mode_digit_f32(C->mdg[h][a], i64, i32, out, o64, C->stream)
@@ -724,7 +726,7 @@ int step_mixed(smx_ctx* C, double* d, double* b, double* e, double* h, const dou
 int solve_f32_impl(smx_ctx* C, int h, const double* y, float* out) {
     int st;
     if (C->use_mode) {
-        const bool tc = C->mode_kernel == SMX_MODE_TENSOR;
+        const bool tc = C->mode_kernel != SMX_MODE_SIMT;  // AUTO: the four-digit tensor-core kernel
         for (int a = 0; a < 3; ++a) {
             st = run(C, (tc ? 24 : 14) + a, 1, [&] {
                 const double* i64 = a == 0 ? y : nullptr;
@@ -950,15 +952,16 @@ int hodge_star_impl(smx_ctx* C, int h, const double* x, double* out, bool prezer
     // SMX_MODE_AUTO takes, per star, the kernel measured faster on GB300.  The
     // banded recurrences cost about n (2(2d+1) + 4 KL + 1) dependent FP64 steps
     // per line (fused mass + solve) or n (4 KL + 1) (pairing sweep); the digit
-    // kernel costs about 15 us of fixed latency plus time proportional to the
+    // kernel costs about 12 us of fixed latency plus time proportional to the
     // lines.  Measured: the digit passes win for a separable star once lines
-    // reach about 48 entries, and for the pairing sweeps too from p = 4 (KL = 3).
+    // reach about 48 entries, and for the pairing sweeps too from p = 4 (KL = 3)
+    // or from 64 entries (p = 3, 64^3: 19-21 us against 22-25 us per pass).
     int maxlen = 0, maxkl = 0;
     for (int a = 0; a < 3; ++a) {
         maxlen = std::max(maxlen, kind_dim(P0, C->p[a], C->nel[a]) + 1);
         maxkl = std::max(maxkl, C->p[a] - 1);
     }
-    const bool auto_digit = maxlen >= 48 && (C->hodge[h].separable || maxkl >= 3);
+    const bool auto_digit = maxlen >= 48 && (C->hodge[h].separable || maxkl >= 3 || maxlen >= 64);
     const bool digit = C->use_digit && C->precision == SMX_FP64 &&
                        (C->mode_kernel == SMX_MODE_TENSOR || (C->mode_kernel == SMX_MODE_AUTO && auto_digit));
     if (digit) {
@@ -1829,7 +1832,7 @@ int smx_project(const smx_ctx* C, int field, smx_field_fn fn, void* user, double
 int smx_mode_kernel(const smx_ctx* C, int* which) {
     if (!C || !which) return SMX_EINVAL;
     *which = C->use_digit ? C->mode_kernel : SMX_MODE_SIMT;
-    if (*which == SMX_MODE_AUTO && C->use_mode) *which = SMX_MODE_SIMT;  // mixed: AUTO is the CUDA-core kernel
+    if (*which == SMX_MODE_AUTO && C->use_mode) *which = SMX_MODE_TENSOR;  // mixed: AUTO is the tensor-core kernel
     return SMX_OK;
 }
 

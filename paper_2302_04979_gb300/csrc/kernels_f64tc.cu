@@ -402,40 +402,34 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
     long long* sAcc = reinterpret_cast<long long*>(sX);  // n x (NL + 1) final accumulators, after the last MMA
 
     if (warp == kDgIssuer) {
-        if (lane == 0) {
-            // level l into buffer l % kBufs: every digit pair t + s = l, k-step by k-step;
-            // the first MMA of a level overwrites the buffer
-            // The issue loop is kept to a few integer instructions per MMA (one thread issues
-            // all of them; a descriptor rebuilt per MMA made the issue, not the tensor pipe,
-            // the limit): base descriptors once, then the 14-bit start-address field advanced
-            // by constant steps (every address stays below 2^18, so the field cannot carry).
-            constexpr uint32_t idesc = idesc_bf16_f32(kDgRows, NL);
-            const uint64_t dA0 = smem_desc_sw32(smem_u32(sOp), 256), dB0 = smem_desc_sw32(smem_u32(sX), 256);
-            const uint64_t stA = (uint64_t)(colA >> 4), stB = (uint64_t)(colX >> 4);
-            const uint64_t plA = (uint64_t)(opPlane >> 4), plB = (uint64_t)(xPlane >> 4);
-            const int nks = kc / 2;
-            for (int lv = 0; lv < ND && ok; ++lv) {
-                const int buf = lv % kBufs;
-                if (lv >= kBufs) {
-                    ok = mbar_wait_bounded(drained0 + 8 * buf, ((lv - kBufs) / kBufs) & 1);
-                    tc_fence_after();
-                    if (!ok) break;
-                }
-                const uint32_t d = tmem + (uint32_t)(buf * NL);
-                for (int t = 0; t <= lv; ++t) {
-                    uint64_t a = dA0 + (uint64_t)(lv - t) * plA, b = dB0 + (uint64_t)t * plB;
-                    mma_bf16(d, a, b, idesc, t ? 1u : 0u);  // the level's first MMA overwrites the buffer
-                    for (int ks = 1; ks < nks; ++ks) {
-                        a += stA;
-                        b += stB;
-                        mma_bf16(d, a, b, idesc, 1u);
-                    }
-                }
-                mma_commit(full0 + 8 * buf);
+        // the whole warp runs the issue loop with warp-uniform values; one elected lane issues
+        // each MMA and commit (level l into buffer l % kBufs, every digit pair t + s = l,
+        // k-step by k-step; the first MMA of a level overwrites the buffer)
+        constexpr uint32_t idesc = idesc_bf16_f32(kDgRows, NL);
+        const uint64_t dA0 = smem_desc_sw32(smem_u32(sOp), 256), dB0 = smem_desc_sw32(smem_u32(sX), 256);
+        const uint64_t stA = (uint64_t)(colA >> 4), stB = (uint64_t)(colX >> 4);
+        const uint64_t plA = (uint64_t)(opPlane >> 4), plB = (uint64_t)(xPlane >> 4);
+        const int nks = kc / 2;
+        for (int lv = 0; lv < ND && ok; ++lv) {
+            const int buf = lv % kBufs;
+            if (lv >= kBufs) {
+                ok = __all_sync(0xffffffffu, mbar_wait_bounded(drained0 + 8 * buf, ((lv - kBufs) / kBufs) & 1));
+                tc_fence_after();
+                if (!ok) break;
             }
-            if (!ok) atomicOr(A.status, 1u);
+            const uint32_t d = tmem + (uint32_t)(buf * NL);
+            for (int t = 0; t <= lv; ++t) {
+                uint64_t a = dA0 + (uint64_t)(lv - t) * plA, b = dB0 + (uint64_t)t * plB;
+                mma_bf16_elect(d, a, b, idesc, t ? 1u : 0u);
+                for (int ks = 1; ks < nks; ++ks) {
+                    a += stA;
+                    b += stB;
+                    mma_bf16_elect(d, a, b, idesc, 1u);
+                }
+            }
+            mma_commit_elect(full0 + 8 * buf);
         }
-        __syncwarp();
+        if (!ok && lane == 0) atomicOr(A.status, 1u);
     } else if (reader) {
         const int i = 32 * quarter + lane;  // operator row = output entry along the line
         const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(group * kCpw);

@@ -96,13 +96,13 @@ def test_calls_without_workspace_are_rejected(smx):
 
 def test_mode_kernel_selection(smx):
     ctx = smx.Context(3, 4, precision="mixed")
-    assert ctx.mode_kernel() == "simt"  # the mixed default: FP32 CUDA cores
+    assert ctx.mode_kernel() == "tensor"  # the mixed default: four-digit tensor-core products
     ctx.set_mode_kernel("tensor")
     assert ctx.mode_kernel() == "tensor"
     ctx.set_mode_kernel("simt")
     assert smx.library().smx_set_mode_kernel(ctx.h, 7) == smx.EINVAL
     ctx.set_mode_kernel("auto")
-    assert ctx.mode_kernel() == "simt"  # mixed: "auto" is the CUDA-core kernel
+    assert ctx.mode_kernel() == "tensor"  # mixed: "auto" is the tensor-core kernel
     # FP64: per-star choice by default; digit-sliced tensor-core products or recurrences on request
     f64 = smx.Context(3, 20)
     assert f64.mode_kernel() == "auto"

@@ -58,12 +58,14 @@ def _auto_uses_digits(case, separable):
     """The rule of smx_set_mode_kernel's SMX_MODE_AUTO for an FP64 star."""
     p = np.broadcast_to(case["p"], 3)
     nel = np.broadcast_to(case["nel"], 3)
-    return int(np.max(nel + p - 1)) >= 48 and (separable or int(np.max(p)) - 1 >= 3)
+    maxlen = int(np.max(nel + p - 1))
+    return maxlen >= 48 and (separable or int(np.max(p)) - 1 >= 3 or maxlen >= 64)
 
 
 def test_auto_selection(trio):
     """The default ("auto") runs the tensor-core products where they were measured faster: lines of
-    at least 48 entries, for a separable star, and from degree 4 for the sweeps after a mass apply."""
+    at least 48 entries, for a separable star, and from degree 4 or 64-entry lines for the sweeps
+    after a mass apply."""
     from paper_2302_04979_gb300 import smx
     name, S, G = trio
     G.set_mode_kernel("auto")
