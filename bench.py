@@ -104,6 +104,7 @@ DIGIT_PAIRS = {"tensor": 28, "tensor4": 10}
 NCU_TRAFFIC = {
     "mass_solve_axis_kernel": 6.90e6, "solve_axis_kernel": 6.72e6, "hodge_block_kernel": 13.51e6,
     "mode_f32_kernel": None, "hodge_block_f32_kernel": 13.51e6,
+    "mode_digit_kernel<7 digits>": 7.10e6, "mode_digit_kernel<4 digits>": 6.90e6,
 }
 
 
@@ -716,15 +717,16 @@ def run_profile(form):
     """A few eager leapfrog steps of the benchmark workload, for profiler captures: one Hodge star
     and two single steps on the default stream (no CUDA graph, so ncu sees every launch).
     fp64 (default line operators), fp64-tc (every FP64 line operator on the tensor cores),
-    fp64-banded (banded FP64 recurrences), mixed (default), mixed-tc (tensor-core option)."""
+    fp64-banded (banded FP64 recurrences), mixed (default: four-digit tensor-core line operators),
+    mixed-simt (FP32 CUDA-core line operators)."""
     import torch
     from paper_2302_04979_gb300 import smx, synth
     eps = ("blocks", synth.block_material(SEED, EPS_BLOCKS, 1.0, 9.0))
     prec = "mixed" if form.startswith("mixed") else "fp64"
     ctx = smx.Context(P, NEL, eps=eps, mu=1.0, precision=prec).bind()
-    if form in ("mixed-tc", "fp64-tc"):
+    if form == "fp64-tc":
         ctx.set_mode_kernel("tensor")
-    elif form == "fp64-banded":
+    elif form in ("fp64-banded", "mixed-simt"):
         ctx.set_mode_kernel("simt")
     d, b, e, h = make_state(ctx, smx, "cuda", SEED + 1)
     for _ in range(2):
@@ -742,7 +744,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other configurations and the batched run")
-    ap.add_argument("--profile", choices=["fp64", "fp64-tc", "fp64-banded", "mixed", "mixed-tc"])
+    ap.add_argument("--profile", choices=["fp64", "fp64-tc", "fp64-banded", "mixed", "mixed-simt"])
     args = ap.parse_args()
     if args.profile:
         run_profile(args.profile)
