@@ -463,7 +463,7 @@ def make_state(ctx, smx, dev, seed):
 
 def other_configs(smx, dev, stream, flush, steps):
     """The other single-cavity configurations, same protocol (L2 flushed before each single step,
-    CUDA events), fewer steps: DoF-steps/s of the FP64 and the mixed form."""
+    CUDA events), fewer steps: DoF-steps/s of the FP64 form and of both mixed forms."""
     import torch
     from paper_2302_04979_gb300 import synth
     specs = [
@@ -476,7 +476,7 @@ def other_configs(smx, dev, stream, flush, steps):
     res = {}
     for name, kw, source in specs:
         ent = {}
-        for prec in ("fp64", "mixed"):
+        for prec in ("fp64", "mixed", "mixed_refined"):
             ctx = smx.Context(precision=prec, **kw).bind(dev)
             ctx.set_stream(stream)
             st = make_state(ctx, smx, dev, SEED + 5)
@@ -498,24 +498,29 @@ def other_configs(smx, dev, stream, flush, steps):
     return res
 
 
-def batched_config(smx, dev, stream, nsteps):
+def batched_config(smx, dev, stream, nsteps, precision="fp64", dts=None):
     """64 independent cavities of seeded uneven sizes (nel in [16, 48], even) and degrees p in
     {2, 3, 4}, each with its own permittivity on a 2^3 block grid (U[1, 4)) and Gaussian-pulse
-    source; one persistent launch per step after autotuning; DoF-steps/s over nsteps steps."""
+    source; one persistent launch per step after autotuning; DoF-steps/s over nsteps steps.
+    precision "fp64" or "mixed_refined"; dts: the time steps (0.5 x CFL of the FP64 form, computed
+    here when not given)."""
     import torch
     from paper_2302_04979_gb300 import synth
     nel = 16 + 2 * (synth.splitmix64(4040, 64) % 17).astype(int)
     p = 2 + (synth.splitmix64(4041, 64) % 3).astype(int)
     ctxs, keep = [], []
     for k in range(64):
-        ctx = smx.Context(int(p[k]), int(nel[k]), eps=("blocks", synth.block_material(4100 + k, (2, 2, 2), 1.0, 4.0)))
+        ctx = smx.Context(int(p[k]), int(nel[k]), eps=("blocks", synth.block_material(4100 + k, (2, 2, 2), 1.0, 4.0)),
+                          precision=precision)
         ctx.bind(dev)
         ctx.set_stream(stream)
         ctxs.append(ctx)
     batch = smx.Batch(ctxs, device=dev)
+    out_dts = []
     for k, ctx in enumerate(ctxs):
         st = make_state(ctx, smx, dev, 5000 + 10 * k)
-        dt = 0.5 * ctx.cfl(iters=100, tol=1e-4)
+        dt = dts[k] if dts is not None else 0.5 * ctx.cfl(iters=100, tol=1e-4)
+        out_dts.append(dt)
         shapes = [ctx.comp_shape(smx.FIELD_D, c) for c in range(3)]
         jhat = torch.as_tensor(synth.bump_coefficients(4200 + k, shapes)).to(dev)
         amp = torch.as_tensor(synth.source_amplitudes(dt, nsteps + 8)).to(dev)
@@ -536,9 +541,10 @@ def batched_config(smx, dev, stream, nsteps):
     ms = s0.elapsed_time(s1)
     dof = sum(c.N_e + c.N_h for c in ctxs)
     return {"value": dof * nsteps / (ms * 1e-3), "ms_per_step": ms / nsteps, "unit": UNIT, "steps": nsteps,
-            "cavities": 64, "dof": int(dof), "line_warps": lw, "dtype": "f64",
-            "note": "one persistent cooperative launch per step; state of all cavities (%.0f MB) L2-resident"
-                    % (sum(8 * 2 * (c.N_e + c.N_h) for c in ctxs) / 1e6)}
+            "cavities": 64, "dof": int(dof), "line_warps": lw,
+            "dtype": "f64" if precision == "fp64" else "f32 operators, f64 residual refinement, f64 state",
+            "note": "one persistent cooperative launch per step (CUDA-graph replay); the state of all cavities "
+                    "(%.0f MB) is larger than L2" % (sum(8 * 2 * (c.N_e + c.N_h) for c in ctxs) / 1e6)}, out_dts
 
 
 def scheme1_comparison(smx, dev, stream, eps, steps, dt2):
@@ -648,7 +654,8 @@ def run_ours(args, rank, world, local):
     s1 = None
     if world == 1 and not args.no_extra:
         configs = other_configs(smx, dev, stream, flush, max(20, min(args.steps, 200)))
-        batched = batched_config(smx, dev, stream, 300)
+        batched, bdts = batched_config(smx, dev, stream, 300)
+        batched["refined"], _ = batched_config(smx, dev, stream, 300, precision="mixed_refined", dts=bdts)
         s1 = scheme1_comparison(smx, dev, stream, eps, 5, 2.0 * dt)
         s1["step_time_ratio_vs_scheme2"] = s1["ms_per_step"] / (total_ms / args.steps)
     clocks = sampler.stop()

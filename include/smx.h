@@ -451,21 +451,32 @@ int smx_step_adjoint(smx_ctx* ctx, const double* d_n, const double* d_np1, doubl
 int smx_adjoint_terminal(smx_ctx* ctx, const double* d_N, const double* ebar, double* dbar, double* eps_bar);
 
 /* ==== Batched cavities: one persistent launch per leapfrog step ====
- * Many independent cavities (each its own bound FP64 context: any p and nel,
- * any map and material) stepped together: one cooperative launch per step runs
- * the eleven phases of the kick-drift-kick step (the same device code as
- * smx_step: fused mass + solve passes for a star with constant material on the
- * identity map, else a block-Kronecker or quadrature mass apply followed by the
- * pairing sweeps) over a flat work list of (cavity, unit) items, with grid
- * barriers between phases.  On a non-default stream the launches of one
+ * Many independent cavities (each its own bound context: any p and nel, any map
+ * and material) stepped together: one cooperative launch per step runs the
+ * phases of the kick-drift-kick step over a flat work list of (cavity, unit)
+ * items, with grid barriers between phases.
+ *   SMX_FP64 contexts: eleven phases, the same device code as smx_step (fused
+ *   mass + solve passes for a star with constant material on the identity map,
+ *   else a block-Kronecker or quadrature mass apply followed by the banded
+ *   pairing sweeps).
+ *   SMX_MIXED_REFINED contexts: twenty-five phases, the refined mixed step: FP64
+ *   curls; per star an FP32 mass apply with FP64 sums, the pairing sweeps as
+ *   banded FP32 recurrences, the residual of each Kronecker solve in FP64, the
+ *   FP32 sweeps of the correction, and the FP64 sum (a single refined context
+ *   applies dense line operators where lines are <= 80 long; the batch always
+ *   runs the banded recurrences, so the two agree to the mixed tolerance, not
+ *   bit for bit).
+ * On a non-default stream the launches of one
  * smx_batch_step call are captured into a CUDA graph and replayed while nsteps
  * is unchanged (the step index lives in a device counter).  Each barrier wait is
  * bounded (one second); see smx_batch_status. */
 typedef struct smx_batch smx_batch;
 
 /* Build a batch over n bound contexts (host arrays; the contexts must outlive
- * the batch and share one stream, that of ctxs[0]).  Host memory only.
- * Errors: SMX_EINVAL (a context is unbound or not SMX_FP64), SMX_ENOMEM. */
+ * the batch and share one stream, that of ctxs[0]), all SMX_FP64 or all
+ * SMX_MIXED_REFINED.  Host memory only.
+ * Errors: SMX_EINVAL (a context is unbound, or of another precision than
+ * ctxs[0], or neither SMX_FP64 nor SMX_MIXED_REFINED), SMX_ENOMEM. */
 int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out);
 int smx_batch_destroy(smx_batch* batch);
 

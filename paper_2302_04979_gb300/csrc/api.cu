@@ -2256,9 +2256,13 @@ int smx_adjoint_terminal(smx_ctx* C, const double* d_N, const double* ebar, doub
 // ---- batched cavities
 struct smx_batch {
     std::vector<smx_ctx*> ctx;
-    std::vector<BatchCavity> cav;
-    std::vector<int2> items[kBatchPhases];
-    size_t o_cav = 0, o_items[kBatchPhases] = {}, o_bar = 0, o_status = 0, o_stepctr = 0, total = 0;
+    bool refined = false;               // refined mixed contexts (else FP64)
+    std::vector<BatchCavity> cav;       // FP64 step
+    std::vector<BatchRefCavity> rcav;   // refined mixed step
+    std::vector<int2> items[kRefPhases];
+    size_t o_cav = 0, o_items[kRefPhases] = {}, o_bar = 0, o_status = 0, o_stepctr = 0, total = 0;
+    size_t max_mass_floats = 0;         // largest FP32 mass unit (refined)
+    int nphases() const { return refined ? kRefPhases : kBatchPhases; }
     unsigned char* ws = nullptr;
     cudaStream_t stream = nullptr;
     int maxn = 0, maxkl = 0, max_nloc = 0;
@@ -2307,20 +2311,92 @@ void batch_line_items(std::vector<int2>& list, int cav, const DevField& f, int a
 
 }  // namespace
 
+// One refined mixed cavity: its tables and buffers (those of the single-cavity refined
+// step) and its units in the twenty-five phases.
+static void batch_refined_cavity(smx_batch* B, smx_ctx* C, int i) {
+    BatchRefCavity K{};
+    K.fE = C->fld[SMX_FIELD_E];
+    K.fB = C->fld[SMX_FIELD_B];
+    K.fH = C->fld[SMX_FIELD_H];
+    K.fD = C->fld[SMX_FIELD_D];
+    for (int h = 0; h < 2; ++h) {
+        const HodgeHost& H = C->hodge[h];
+        K.fS[h] = C->fld[kFieldOfHodge[h]];
+        K.hb[h] = C->hb32[h];
+        K.hq[h] = C->hq32[h];
+        K.mode[h] = H.mode;
+        for (int a = 0; a < 3; ++a) {
+            K.ln[h][a] = C->ln32[h][a];
+            K.band[h][a] = C->band[h][a];
+        }
+        B->max_mass_floats = std::max(B->max_mass_floats,
+                                      H.mode == 0 ? batch_ref_mass_floats(H.max_nloc, 0, 0, 0)
+                                                  : batch_ref_mass_floats(0, H.q[0], H.q[1], H.q[2]));
+    }
+    for (int a = 0; a < 3; ++a) {
+        K.kl[a] = C->p[a] - 1;
+        B->maxkl = std::max(B->maxkl, C->p[a] - 1);
+        for (int c = 0; c < 3; ++c)
+            for (int f = 0; f < 4; ++f) B->maxn = std::max(B->maxn, C->fld[f].c[c].n[a]);
+    }
+    K.y = C->scratch;
+    K.t64 = C->t64;
+    K.s64 = C->scratch2;
+    K.x0[0] = C->h32;
+    K.x0[1] = C->e32;
+    K.c32 = C->y32;
+    B->rcav.push_back(K);
+    auto chunks = [&](int ph, long long ntot) {
+        for (long long z = 0; z < (ntot + kBatchThreads * 8 - 1) / (kBatchThreads * 8); ++z)
+            B->items[ph].push_back(make_int2(i, (int)z));
+    };
+    auto zeros = [&](int ph, long long ntot) {
+        for (long long z = 0; z < (ntot + kBatchThreads * 8 - 1) / (kBatchThreads * 8); ++z)
+            B->items[ph].push_back(make_int2(i, batch_zero_unit((int)z)));
+    };
+    batch_curl_items(B->items[0], i, K.fB);
+    batch_curl_items(B->items[12], i, K.fD);
+    batch_curl_items(B->items[24], i, K.fB);
+    for (int h = 0; h < 2; ++h) {
+        const int base = 12 * h;
+        const HodgeHost& H = C->hodge[h];
+        zeros(base, K.fS[h].total);
+        if (H.mode == 0) {
+            const int nt = H.ntile[0] * H.ntile[1] * H.ntile[2];
+            for (int c = 0; c < 3; ++c)
+                for (int t = 0; t < nt; ++t) B->items[base + 1].push_back(make_int2(i, batch_comp_unit(c, t)));
+        } else {
+            const int ne = C->nel[0] * C->nel[1] * C->nel[2];
+            for (int e = 0; e < ne; ++e) B->items[base + 1].push_back(make_int2(i, e));
+        }
+        for (int a = 0; a < 3; ++a) {
+            batch_line_items(B->items[base + 2 + a], i, K.fS[h], a);
+            chunks(base + 5 + a, K.fS[h].total);
+            batch_line_items(B->items[base + 8 + a], i, K.fS[h], a);
+        }
+        chunks(base + 11, K.fS[h].total);
+    }
+}
+
 int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out) {
     if (n < 1 || !ctxs || !out) return SMX_EINVAL;
     *out = nullptr;
     smx_batch* B = new (std::nothrow) smx_batch();
     if (!B) return SMX_ENOMEM;
+    B->refined = ctxs[0] && ctxs[0]->precision == SMX_MIXED_REFINED;
     try {
         for (int i = 0; i < n; ++i) {
             smx_ctx* C = ctxs[i];
-            // FP64, bound; any map and material
-            if (!C || !C->ws || C->precision != SMX_FP64) {
+            // bound, all FP64 or all refined mixed; any map and material
+            if (!C || !C->ws || C->precision != (B->refined ? SMX_MIXED_REFINED : SMX_FP64)) {
                 delete B;
                 return SMX_EINVAL;
             }
             B->ctx.push_back(C);
+            if (B->refined) {
+                batch_refined_cavity(B, C, i);
+                continue;
+            }
             BatchCavity K{};
             K.fE = C->fld[SMX_FIELD_E];
             K.fB = C->fld[SMX_FIELD_B];
@@ -2381,8 +2457,9 @@ int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out) {
             off += (bytes + 255) & ~size_t(255);
             return o;
         };
-        B->o_cav = take(B->cav.size() * sizeof(BatchCavity));
-        for (int ph = 0; ph < kBatchPhases; ++ph) B->o_items[ph] = take(std::max<size_t>(1, B->items[ph].size()) * sizeof(int2));
+        B->o_cav = take(B->refined ? B->rcav.size() * sizeof(BatchRefCavity) : B->cav.size() * sizeof(BatchCavity));
+        for (int ph = 0; ph < B->nphases(); ++ph)
+            B->o_items[ph] = take(std::max<size_t>(1, B->items[ph].size()) * sizeof(int2));
         B->o_bar = take(2 * sizeof(unsigned));
         B->o_status = take(sizeof(unsigned));
         B->o_stepctr = take(sizeof(unsigned));
@@ -2407,11 +2484,17 @@ int smx_batch_workspace_bytes(const smx_batch* B, size_t* bytes) {
 }
 
 static int batch_configure(smx_batch* B, int line_warps) {
-    const size_t warp = batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
-    const size_t hodge = std::max((size_t)3 * kLMax * (kLMax + 1) + 2 * (size_t)B->max_nloc + 8, B->max_quad);
-    const size_t smem = std::max(warp * line_warps, hodge) * sizeof(double);
+    size_t smem;
+    if (B->refined) {
+        const size_t warp = batch_ref_line_warp_floats(B->maxn, std::max(1, B->maxkl));
+        smem = std::max(warp * line_warps, B->max_mass_floats) * sizeof(float);
+    } else {
+        const size_t warp = batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
+        const size_t hodge = std::max((size_t)3 * kLMax * (kLMax + 1) + 2 * (size_t)B->max_nloc + 8, B->max_quad);
+        smem = std::max(warp * line_warps, hodge) * sizeof(double);
+    }
     if (smem > 226 * 1024) return SMX_EINVAL;
-    const int per_sm = batch_blocks_per_sm(smem);
+    const int per_sm = B->refined ? batch_refined_blocks_per_sm(smem) : batch_blocks_per_sm(smem);
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -2428,7 +2511,7 @@ int smx_batch_bind_workspace(smx_batch* B, void* dev, size_t bytes) {
     if (bytes < B->total || (reinterpret_cast<uintptr_t>(dev) & 255)) return SMX_ESTATE;
     B->ws = static_cast<unsigned char*>(dev);
     B->stream = B->ctx[0]->stream;
-    for (int ph = 0; ph < kBatchPhases; ++ph)
+    for (int ph = 0; ph < B->nphases(); ++ph)
         if (!B->items[ph].empty())
             CK(cudaMemcpyAsync(B->ws + B->o_items[ph], B->items[ph].data(), B->items[ph].size() * sizeof(int2),
                                cudaMemcpyHostToDevice, B->stream));
@@ -2442,8 +2525,21 @@ int smx_batch_bind_workspace(smx_batch* B, void* dev, size_t bytes) {
 
 int smx_batch_set_state(smx_batch* B, int i, double* d, double* b, double* e, double* h, const double* jhat,
                         const double* amp, double dt) {
-    if (!B || !B->ws || i < 0 || i >= (int)B->cav.size() || !d || !b || !e || !h) return SMX_EINVAL;
+    if (!B || !B->ws || i < 0 || i >= (int)B->ctx.size() || !d || !b || !e || !h) return SMX_EINVAL;
     if (!(dt > 0.0) || !std::isfinite(dt) || (jhat && !amp)) return SMX_EINVAL;
+    if (B->refined) {
+        BatchRefCavity& K = B->rcav[i];
+        K.d = d;
+        K.b = b;
+        K.e = e;
+        K.h = h;
+        K.jhat = jhat;
+        K.amp = amp;
+        K.dt = dt;
+        B->state_set = false;
+        B->steps = 0;
+        return SMX_OK;
+    }
     BatchCavity& K = B->cav[i];
     K.d = d;
     K.b = b;
@@ -2459,27 +2555,53 @@ int smx_batch_set_state(smx_batch* B, int i, double* d, double* b, double* e, do
 
 static int batch_launch(smx_batch* B, int nsteps) {
     if (!B->state_set) {
-        for (const BatchCavity& K : B->cav)
-            if (!K.d) return SMX_ESTATE;
-        CK(cudaMemcpyAsync(B->ws + B->o_cav, B->cav.data(), B->cav.size() * sizeof(BatchCavity),
-                           cudaMemcpyHostToDevice, B->stream));
+        if (B->refined) {
+            for (const BatchRefCavity& K : B->rcav)
+                if (!K.d) return SMX_ESTATE;
+            CK(cudaMemcpyAsync(B->ws + B->o_cav, B->rcav.data(), B->rcav.size() * sizeof(BatchRefCavity),
+                               cudaMemcpyHostToDevice, B->stream));
+        } else {
+            for (const BatchCavity& K : B->cav)
+                if (!K.d) return SMX_ESTATE;
+            CK(cudaMemcpyAsync(B->ws + B->o_cav, B->cav.data(), B->cav.size() * sizeof(BatchCavity),
+                               cudaMemcpyHostToDevice, B->stream));
+        }
         const unsigned ctr = (unsigned)B->steps;  // the device step counter follows the host's
         CK(cudaMemcpyAsync(B->ws + B->o_stepctr, &ctr, sizeof ctr, cudaMemcpyHostToDevice, B->stream));
         CK(cudaStreamSynchronize(B->stream));   // ctr is a stack variable
         B->state_set = true;
     }
     BatchArgs A{};
-    A.cav = reinterpret_cast<const BatchCavity*>(B->ws + B->o_cav);
-    for (int ph = 0; ph < kBatchPhases; ++ph) {
-        A.items[ph] = reinterpret_cast<const int2*>(B->ws + B->o_items[ph]);
-        A.nitems[ph] = (int)B->items[ph].size();
+    BatchRefArgs R{};
+    if (B->refined) {
+        R.cav = reinterpret_cast<const BatchRefCavity*>(B->ws + B->o_cav);
+        for (int ph = 0; ph < kRefPhases; ++ph) {
+            R.items[ph] = reinterpret_cast<const int2*>(B->ws + B->o_items[ph]);
+            R.nitems[ph] = (int)B->items[ph].size();
+        }
+        R.bar = reinterpret_cast<unsigned*>(B->ws + B->o_bar);
+        R.status = reinterpret_cast<unsigned*>(B->ws + B->o_status);
+        R.stepctr = reinterpret_cast<unsigned*>(B->ws + B->o_stepctr);
+        R.line_warps = B->line_warps;
+        R.warp_floats = (int)batch_ref_line_warp_floats(B->maxn, std::max(1, B->maxkl));
+        R.wait_ns = B->wait_ns;
+    } else {
+        A.cav = reinterpret_cast<const BatchCavity*>(B->ws + B->o_cav);
+        for (int ph = 0; ph < kBatchPhases; ++ph) {
+            A.items[ph] = reinterpret_cast<const int2*>(B->ws + B->o_items[ph]);
+            A.nitems[ph] = (int)B->items[ph].size();
+        }
+        A.bar = reinterpret_cast<unsigned*>(B->ws + B->o_bar);
+        A.status = reinterpret_cast<unsigned*>(B->ws + B->o_status);
+        A.stepctr = reinterpret_cast<unsigned*>(B->ws + B->o_stepctr);
+        A.line_warps = B->line_warps;
+        A.warp_smem = (int)batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
+        A.wait_ns = B->wait_ns;
     }
-    A.bar = reinterpret_cast<unsigned*>(B->ws + B->o_bar);
-    A.status = reinterpret_cast<unsigned*>(B->ws + B->o_status);
-    A.stepctr = reinterpret_cast<unsigned*>(B->ws + B->o_stepctr);
-    A.line_warps = B->line_warps;
-    A.warp_smem = (int)batch_line_warp_doubles(B->maxn, std::max(1, B->maxkl));
-    A.wait_ns = B->wait_ns;
+    auto launch_one = [&]() {
+        return B->refined ? launch_batch_refined_step(R, B->grid, B->smem, B->stream)
+                          : launch_batch_step(A, B->grid, B->smem, B->stream);
+    };
     // the nsteps launches as one captured CUDA graph (replayed while nsteps and the shape are
     // unchanged; the step index comes from the device counter), eagerly on the legacy stream
     if (B->use_graphs && B->stream != nullptr && nsteps > 0) {
@@ -2487,7 +2609,7 @@ static int batch_launch(smx_batch* B, int nsteps) {
             B->drop_graph();
             CK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t el = cudaSuccess;
-            for (int n = 0; n < nsteps && el == cudaSuccess; ++n) el = launch_batch_step(A, B->grid, B->smem, B->stream);
+            for (int n = 0; n < nsteps && el == cudaSuccess; ++n) el = launch_one();
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(B->stream, &g);
             if (el != cudaSuccess || ec != cudaSuccess) {
@@ -2507,7 +2629,7 @@ static int batch_launch(smx_batch* B, int nsteps) {
         return SMX_OK;
     }
     for (int n = 0; n < nsteps; ++n) {
-        CK(launch_batch_step(A, B->grid, B->smem, B->stream));
+        CK(launch_one());
         ++B->steps;
     }
     return SMX_OK;
@@ -2548,17 +2670,33 @@ int smx_batch_autotune(smx_batch* B, int steps, int* line_warps) {
     if (!B || !B->ws || steps < 1) return SMX_EINVAL;
     // time each shape on the contexts' own state vectors (zero fields: the work does not depend on the data)
     std::vector<BatchCavity> saved = B->cav;
+    std::vector<BatchRefCavity> rsaved = B->rcav;
     const long long saved_steps = B->steps;
-    for (size_t i = 0; i < B->cav.size(); ++i) {
+    for (size_t i = 0; i < B->ctx.size(); ++i) {
         smx_ctx* C = B->ctx[i];
-        BatchCavity& K = B->cav[i];
-        K.d = C->state;
-        K.e = C->state + C->N_e;
-        K.b = C->state + 2 * C->N_e;
-        K.h = K.b + C->N_h;
-        K.jhat = nullptr;
-        K.amp = nullptr;
-        K.dt = 1e-3;
+        double* d = C->state;
+        double* e = C->state + C->N_e;
+        double* b = C->state + 2 * C->N_e;
+        double* h = b + C->N_h;
+        if (B->refined) {
+            BatchRefCavity& K = B->rcav[i];
+            K.d = d;
+            K.e = e;
+            K.b = b;
+            K.h = h;
+            K.jhat = nullptr;
+            K.amp = nullptr;
+            K.dt = 1e-3;
+        } else {
+            BatchCavity& K = B->cav[i];
+            K.d = d;
+            K.e = e;
+            K.b = b;
+            K.h = h;
+            K.jhat = nullptr;
+            K.amp = nullptr;
+            K.dt = 1e-3;
+        }
         CK(cudaMemsetAsync(C->state, 0, 2 * (size_t)(C->N_e + C->N_h) * sizeof(double), C->stream));
     }
     B->state_set = false;
@@ -2585,6 +2723,7 @@ int smx_batch_autotune(smx_batch* B, int steps, int* line_warps) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->cav = saved;
+    B->rcav = rsaved;
     B->steps = saved_steps;
     B->state_set = false;
     const int st = batch_configure(B, best_lw);

@@ -248,6 +248,50 @@ cudaError_t launch_batch_step(const BatchArgs& a, int grid, size_t smem, cudaStr
 int batch_blocks_per_sm(size_t smem);
 size_t batch_line_warp_doubles(int maxn, int kl);  // staging of one line warp
 
+// The refined mixed step (FP32 operators, one FP64-residual refinement per Kronecker solve,
+// FP64 state and star outputs) of many cavities in one persistent launch (kernels_f32.cu):
+// twenty-five phases separated by grid barriers,
+//   0 b -= dt/2 D^1 e; y = 0      1 y = M b (FP32 products, FP64 sums)
+//   2-4 x0 = K~_1^{-1} y per axis (FP32 line sweeps)
+//   5-7 t = y - K~_1 x0 (FP64 band applies per axis)
+//   8-10 c = K~_1^{-1} t per axis 11 h = x0 + c
+//   12 d += dt (D~^1 h - s jhat); y = 0   13-23 the same for the star of D (e)
+//   24 b -= dt/2 D^1 e
+constexpr int kRefPhases = 25;
+struct BatchRefCavity {
+    DevField fE, fB, fH, fD;
+    DevField fS[2];             // layout of each star's mass apply and solves (B, D)
+    HodgeBlockF32Args hb[2];    // [0] star of B (M^2), [1] star of D (M~^2)
+    HodgeQuadF32Args hq[2];
+    int mode[2];                // mass apply: 0 block tiles, 1 quadrature elements
+    LineF32Args ln[2][3];       // FP32 pairing sweeps per star and axis
+    BandApplyArgs band[2][3];   // FP64 band rows of the pairing factors per star and axis
+    int kl[3];                  // p - 1 per axis
+    double *d, *b, *e, *h;      // state
+    double *y, *t64, *s64;      // mass apply, residual, residual scratch (FP64)
+    float* x0[2];               // first FP32 solution of each star
+    float* c32;                 // FP32 correction
+    const double* jhat;         // or null
+    const double* amp;          // device, one value per step (with jhat)
+    double dt;
+};
+struct BatchRefArgs {
+    const BatchRefCavity* cav;
+    const int2* items[kRefPhases];
+    int nitems[kRefPhases];
+    unsigned* bar;
+    unsigned* status;
+    int line_warps;
+    int warp_floats;            // floats of shared memory per line warp
+    int step;
+    unsigned* stepctr;
+    unsigned long long wait_ns;
+};
+cudaError_t launch_batch_refined_step(const BatchRefArgs& a, int grid, size_t smem, cudaStream_t s);
+int batch_refined_blocks_per_sm(size_t smem);
+size_t batch_ref_line_warp_floats(int maxn, int kl);           // staging of one FP32 line warp
+size_t batch_ref_mass_floats(int max_nloc, int qx, int qy, int qz);  // largest FP32 mass unit (q = 0: none)
+
 // ---- launchers (kernels.cu); all enqueue on `s` and return cudaGetLastError()
 cudaError_t launch_curl_primal(const DevField& E, const DevField& B, const double* e, double* b,
                                double alpha, cudaStream_t s, double* zero = nullptr);

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "batch.cuh"
 #include "convert.cuh"
 #include "curl.cuh"
 #include "pdl.cuh"
@@ -72,10 +73,8 @@ cudaError_t launch_cast_f2d(const float* x, double* y, long long n, cudaStream_t
 // along y and z are coalesced across threads (consecutive x); the input must
 // not alias the output.
 template <class TIN>
-__global__ void __launch_bounds__(256) band_apply_kernel(BandApplyArgs A, const TIN* __restrict__ in,
-                                                         const double* __restrict__ y, double* __restrict__ out) {
-    pdl_wait();
-    const long long idx = blockIdx.x * 256ll + threadIdx.x;
+__device__ __forceinline__ void band_apply_entry(const BandApplyArgs& A, long long idx, const TIN* __restrict__ in,
+                                                 const double* __restrict__ y, double* __restrict__ out) {
     if (idx < A.field.total) {
         int c = 0;
         while (c < 2 && idx >= A.field.c[c + 1].off) ++c;
@@ -96,6 +95,13 @@ __global__ void __launch_bounds__(256) band_apply_kernel(BandApplyArgs A, const 
         }
         out[idx] = y ? y[idx] - acc : acc;
     }
+}
+
+template <class TIN>
+__global__ void __launch_bounds__(256) band_apply_kernel(BandApplyArgs A, const TIN* __restrict__ in,
+                                                         const double* __restrict__ y, double* __restrict__ out) {
+    pdl_wait();
+    band_apply_entry<TIN>(A, blockIdx.x * 256ll + threadIdx.x, in, y, out);
     pdl_trigger();
 }
 
@@ -127,13 +133,11 @@ cudaError_t launch_refine_sum(const float* x0, const float* c, double* out, long
 // tile masses.  The input may be the FP64 state (converted on load).
 // Threads (ii, jj) = (threadIdx.x, threadIdx.y) cover the tile's x-y face
 // (L <= 16 per axis) and march along z, so no index is divided at run time.
+// One (component, tile): threads (ii, jj) of the tile face, flat index `flat` of `nthreads`.
 template <class TIN>
-__global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args A, const TIN* __restrict__ x,
-                                                              double* __restrict__ y) {
-    extern __shared__ float smf[];
-    pdl_wait();
-    const int c = blockIdx.y;
-    const int tile = blockIdx.x;
+__device__ __forceinline__ void hodge_block_f32_tile(const HodgeBlockF32Args& A, int c, int tile,
+                                                     const TIN* __restrict__ x, double* __restrict__ y, float* smf,
+                                                     int ii, int jj, int flat, int nthreads) {
     const int tx = tile % A.ntile[0];
     const int tyz = tile / A.ntile[0];
     const int ty = tyz % A.ntile[1];
@@ -160,7 +164,6 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     const int Lx = L[0], Ly = L[1], Lz = L[2];
     const int nloc = Lx * Ly * Lz;
     float* s1 = s0 + nloc;
-    const int flat = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
     for (int t = flat; t < kLMax * kLMax; t += nthreads) {
         const int d = (t / kLMax) * kLd + t % kLMax;
         Mx[d] = gmat[0][t];
@@ -173,7 +176,6 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     }
     const DevComp C = A.field.c[c];
     const long long nxy = (long long)C.n[0] * C.n[1];
-    const int ii = threadIdx.x, jj = threadIdx.y;
     const bool act = ii < Lx && jj < Ly;
     const TIN* xcol = x + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
     if (act)
@@ -211,6 +213,15 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
     }
 }
 
+template <class TIN>
+__global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args A, const TIN* __restrict__ x,
+                                                              double* __restrict__ y) {
+    extern __shared__ float smf[];
+    pdl_wait();
+    hodge_block_f32_tile<TIN>(A, blockIdx.y, blockIdx.x, x, y, smf, threadIdx.x, threadIdx.y,
+                              threadIdx.y * blockDim.x + threadIdx.x, blockDim.x * blockDim.y);
+}
+
 cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, double* y,
                                    cudaStream_t s) {
     const int ntiles = a.ntile[0] * a.ntile[1] * a.ntile[2];
@@ -233,12 +244,9 @@ cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64
 // rounded to FP32, as in the block-Kronecker kernel.
 constexpr int kQuadF32Threads = 128;
 
-__global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQuadF32Args A,
-                                                                        const double* __restrict__ x,
-                                                                        double* __restrict__ y) {
-    extern __shared__ float smq[];
-    pdl_wait();
-    const int e = blockIdx.x;
+// One element, all `nt` threads of the CTA (tid = thread index).
+__device__ __forceinline__ void hodge_quad_f32_element(const HodgeQuadF32Args& A, int e, const double* __restrict__ x,
+                                                       double* __restrict__ y, float* smq, int tid, int nt) {
     const int ex = e % A.nel[0], exy = e / A.nel[0], ey = exy % A.nel[1], ez = exy / A.nel[1];
     const int el[3] = {ex, ey, ez};
     const int qx = A.q[0], qy = A.q[1], qz = A.q[2];
@@ -248,7 +256,6 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
     float* T1 = U + 3 * Qe;                  // scratch, <= Qe * kRMax
     float* T2 = T1 + Qe * kRMax;             // scratch, <= Qe * kRMax
     float* X = T2 + Qe * kRMax;              // local coefficients, <= kRMax^3
-    const int tid = threadIdx.x, nt = blockDim.x;
     auto load_basis = [&](int c) {
         for (int t = tid; t < 3 * 8 * kRMax; t += nt) {
             const int a = t / (8 * kRMax), rem = t % (8 * kRMax), qp = rem / kRMax, r = rem % kRMax;
@@ -341,6 +348,14 @@ __global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQu
     }
 }
 
+__global__ void __launch_bounds__(kQuadF32Threads) hodge_quad_f32_kernel(HodgeQuadF32Args A,
+                                                                        const double* __restrict__ x,
+                                                                        double* __restrict__ y) {
+    extern __shared__ float smq[];
+    pdl_wait();
+    hodge_quad_f32_element(A, blockIdx.x, x, y, smq, threadIdx.x, blockDim.x);
+}
+
 cudaError_t launch_hodge_quad_f32(const HodgeQuadF32Args& a, const double* x, double* y, cudaStream_t s) {
     const int nel = a.nel[0] * a.nel[1] * a.nel[2];
     const int Qe = a.q[0] * a.q[1] * a.q[2];
@@ -413,17 +428,18 @@ __device__ __forceinline__ void mass_line_f(const float* __restrict__ ypad, floa
     }
 }
 
-// One CTA stages kSolveLines lines (FP64 input converted on load, or FP32),
-// optionally applies the banded mass (MASS), then forward/backward LU.
+// One warp stages kSolveLines lines (line block lb of component c; FP64 input
+// converted on load, or FP32), optionally applies the banded mass (MASS), then
+// forward/backward LU.  tid is the lane.
 template <int KL, int D, bool MASS, class TIN>
-__device__ __forceinline__ void line_body_f(const LineF32Args& A, const TIN* __restrict__ in, float* __restrict__ out,
-                                            float* sm) {
-    const int c = blockIdx.y;
+__device__ __forceinline__ void line_body_f(const LineF32Args& A, int c, int lb, const TIN* __restrict__ in,
+                                            float* __restrict__ out, float* sm, int tid) {
     const DevComp C = A.field.c[c];
     const int axis = A.axis;
     const int n = C.n[axis];
+    if (n <= 0) return;
     const int nlines = C.n[0] * C.n[1] * C.n[2] / n;
-    const int l0 = blockIdx.x * kSolveLines;
+    const int l0 = lb * kSolveLines;
     if (l0 >= nlines) return;
     const int nl = min(kSolveLines, nlines - l0);
     constexpr int W = 2 * D + 1;
@@ -436,7 +452,7 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, const TIN* __r
     const int np = n + 2 * Dp;
     const int ldin = np | 1, ldout = n | 1;
     float* Sout = Sin + kSolveLines * ldin;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr int nt = kSolveLines;
     const float2* gL = A.L[c];
     const float2* gU = A.U[c];
     const float2* gD = A.dinv[c];
@@ -471,7 +487,7 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, const TIN* __r
         for (int m = 0; m < n; ++m) Sin[(Dp + m) * kSolveLines + tid] = to_f(__ldg(src + base + m * stride));
     }
     cp_async_wait_all_f();
-    __syncthreads();
+    __syncwarp();
     const int oL = axis == 0 ? ldout : 1;
     if (tid < nl) {
         if (MASS) {
@@ -486,7 +502,7 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, const TIN* __r
         else
             lu_backward_f<KL>(Sout + tid * oL, Sin + tid * sL, sM, n, fU, fD);
     }
-    __syncthreads();
+    __syncwarp();
     const float* res = MASS ? Sout : Sin;
     const int ldr = MASS ? ldout : ldin;
     float* dst = out + C.off;
@@ -510,17 +526,18 @@ __global__ void __launch_bounds__(kSolveLines) line_f32_kernel(LineF32Args A, co
                                                                float* __restrict__ out) {
     extern __shared__ float smf[];
     pdl_wait();
+    const int c = blockIdx.y, lb = blockIdx.x, tid = threadIdx.x;
     if (!MASS) {
-        line_body_f<KL, 0, false, TIN>(A, in, out, smf);
+        line_body_f<KL, 0, false, TIN>(A, c, lb, in, out, smf, tid);
         return;
     }
-    const int d = A.deg[blockIdx.y];
+    const int d = A.deg[c];
     if (d == KL - 1)
-        line_body_f<KL, KL - 1, true, TIN>(A, in, out, smf);
+        line_body_f<KL, KL - 1, true, TIN>(A, c, lb, in, out, smf, tid);
     else if (d == KL)
-        line_body_f<KL, KL, true, TIN>(A, in, out, smf);
+        line_body_f<KL, KL, true, TIN>(A, c, lb, in, out, smf, tid);
     else
-        line_body_f<KL, KL + 1, true, TIN>(A, in, out, smf);
+        line_body_f<KL, KL + 1, true, TIN>(A, c, lb, in, out, smf, tid);
 }
 
 template <int KL, bool MASS, class TIN>
@@ -720,6 +737,188 @@ cudaError_t launch_mode_f32(const ModeF32Args& a, const double* in64, const floa
         case 5: return launch_mode_t<5>(a, in64, in32, out, maxn, nb, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+
+// ------------------------------------------------------------------ batched cavities, refined mixed step
+// One persistent (cooperative) launch per step for many cavities in the refined
+// mixed form (the phases are listed with BatchRefCavity).  Each phase walks a
+// flat list of (cavity, unit) items: whole-CTA units (curl chunks, zeroing, FP32
+// mass tiles or elements, chunks of 2048 entries for the residual and the sum)
+// or line units (kSolveLines lines, one warp with its own shared-memory
+// staging).  The work of a unit is the device function of the single-cavity
+// kernel; the line sweeps are the banded FP32 recurrences.
+
+template <bool DUAL>
+__device__ __noinline__ void ref_curl(const BatchRefCavity& K, int unit, const double* in, double* out, double alpha,
+                                      const double* jhat, const double* amp, int step) {
+    const int c = (unit >> 28) & 3, zc = (unit >> 14) & 0x3FFF, pb = unit & 0x3FFF;
+    const DevField& IN = DUAL ? K.fH : K.fE;
+    const DevField& OUT = DUAL ? K.fD : K.fB;
+    const int p = pb * kCurlThreads + threadIdx.x;
+    if (c == 0)
+        curl_plane_comp<0, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz, nullptr);
+    else if (c == 1)
+        curl_plane_comp<1, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz, nullptr);
+    else
+        curl_plane_comp<2, DUAL, double>(IN, OUT, in, out, alpha, jhat, amp, step, 0.0, p, zc * kCurlKz, nullptr);
+}
+
+__device__ __noinline__ void ref_mass_tile(const HodgeBlockF32Args& A, int c, int tile, const double* x, double* y,
+                                           float* sm) {
+    // the tile face on a 16 x 16 thread grid (tiles are at most kLMax = 16 functions per axis)
+    hodge_block_f32_tile<double>(A, c, tile, x, y, sm, threadIdx.x & 15, threadIdx.x >> 4, threadIdx.x, kBatchThreads);
+}
+
+__device__ __noinline__ void ref_mass_element(const HodgeQuadF32Args& A, int e, const double* x, double* y, float* sm) {
+    hodge_quad_f32_element(A, e, x, y, sm, threadIdx.x, kBatchThreads);
+}
+
+// Each variant is its own (not inlined) function, so the persistent kernel does not carry
+// the register pressure of all of them at once.
+template <int KL, class TIN>
+__device__ __noinline__ void ref_line_k(const LineF32Args& A, int c, int lb, const TIN* in, float* out, float* sm,
+                                        int lane) {
+    line_body_f<KL, 0, false, TIN>(A, c, lb, in, out, sm, lane);
+}
+
+template <class TIN>
+__device__ __forceinline__ void ref_line(const LineF32Args& A, int kl, int c, int lb, const TIN* in, float* out,
+                                         float* sm, int lane) {
+    switch (kl) {
+        case 1: ref_line_k<1, TIN>(A, c, lb, in, out, sm, lane); break;
+        case 2: ref_line_k<2, TIN>(A, c, lb, in, out, sm, lane); break;
+        case 3: ref_line_k<3, TIN>(A, c, lb, in, out, sm, lane); break;
+        case 4: ref_line_k<4, TIN>(A, c, lb, in, out, sm, lane); break;
+        default: ref_line_k<5, TIN>(A, c, lb, in, out, sm, lane); break;
+    }
+}
+
+constexpr int kRefChunk = kBatchThreads * 8;  // entries of a residual, sum or zeroing unit
+
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_refined_kernel(BatchRefArgs B) {
+    extern __shared__ float smr[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned nblocks = gridDim.x;
+    // a barrier of an earlier launch gave up (its phases are incomplete and the
+    // barrier words are stale until smx_batch_status resets them): do nothing
+    if (*(volatile unsigned*)B.status & 2u) return;
+    const int step = B.stepctr ? (int)*(volatile unsigned*)B.stepctr : B.step;
+    for (int ph = 0; ph < kRefPhases; ++ph) {
+        const int2* items = B.items[ph];
+        const int n = B.nitems[ph];
+        const int h = ph < 12 ? 0 : 1;          // star of B (phases 1..11), of D (13..23)
+        const int r = ph < 12 ? ph : ph - 12;   // position within the half step
+        const bool line_phase = ph != 24 && ((r >= 2 && r <= 4) || (r >= 8 && r <= 10));
+        if (!line_phase) {
+            for (int it = blockIdx.x; it < n; it += nblocks) {
+                const int2 w = items[it];
+                const BatchRefCavity& K = B.cav[w.x];
+                if (r == 0 || ph == 24) {
+                    if (w.y & (1 << 30)) {  // zero the mass accumulator of the star that follows
+                        const long long z0 = (long long)(w.y & 0xFFFFFF) * kRefChunk;
+                        const long long ntot = K.fS[h].total;
+                        for (int q = 0; q < 8; ++q) {
+                            const long long i = z0 + q * kBatchThreads + threadIdx.x;
+                            if (i < ntot) K.y[i] = 0.0;
+                        }
+                    } else if (ph == 12) {
+                        ref_curl<true>(K, w.y, K.h, K.d, K.dt, K.jhat, K.amp, step);
+                    } else {
+                        ref_curl<false>(K, w.y, K.e, K.b, -0.5 * K.dt, nullptr, nullptr, 0);
+                    }
+                } else if (r == 1) {  // mass apply into y
+                    const double* x = h == 0 ? K.b : K.d;
+                    if (K.mode[h] == 0)
+                        ref_mass_tile(K.hb[h], w.y >> 24, w.y & 0xFFFFFF, x, K.y, smr);
+                    else
+                        ref_mass_element(K.hq[h], w.y, x, K.y, smr);
+                    __syncthreads();  // the next unit reuses the shared memory
+                } else if (r >= 5 && r <= 7) {  // residual t = y - K x0, one axis per phase
+                    const long long i0 = (long long)w.y * kRefChunk;
+                    for (int q = 0; q < 8; ++q) {
+                        const long long i = i0 + q * kBatchThreads + threadIdx.x;
+                        if (r == 5)
+                            band_apply_entry<float>(K.band[h][0], i, K.x0[h], nullptr, K.t64);
+                        else if (r == 6)
+                            band_apply_entry<double>(K.band[h][1], i, K.t64, nullptr, K.s64);
+                        else
+                            band_apply_entry<double>(K.band[h][2], i, K.s64, K.y, K.t64);
+                    }
+                } else {  // r == 11: the star's output x0 + c in FP64
+                    double* out = h == 0 ? K.h : K.e;
+                    const long long i0 = (long long)w.y * kRefChunk;
+                    const long long ntot = K.fS[h].total;
+                    for (int q = 0; q < 8; ++q) {
+                        const long long i = i0 + q * kBatchThreads + threadIdx.x;
+                        if (i < ntot) out[i] = f2d_exact(K.x0[h][i]) + f2d_exact(K.c32[i]);
+                    }
+                }
+            }
+        } else if (warp < B.line_warps) {
+            float* sm = smr + (size_t)warp * B.warp_floats;
+            const int gw = blockIdx.x * B.line_warps + warp, nw = nblocks * B.line_warps;
+            const bool second = r >= 8;  // the correction's sweeps
+            const int a = second ? r - 8 : r - 2;
+            for (int it = gw; it < n; it += nw) {
+                const int2 w = items[it];
+                const BatchRefCavity& K = B.cav[w.x];
+                const int c = w.y >> 24, lb = w.y & 0xFFFFFF;
+                float* out = second ? K.c32 : K.x0[h];
+                if (a == 0)
+                    ref_line<double>(K.ln[h][0], K.kl[0], c, lb, second ? K.t64 : K.y, out, sm, lane);
+                else
+                    ref_line<float>(K.ln[h][a], K.kl[a], c, lb, out, out, sm, lane);
+                __syncwarp();  // the next unit reuses this warp's staging
+            }
+        }
+        if (ph + 1 < kRefPhases && !batch_barrier(B.bar, B.status, nblocks, B.wait_ns)) return;
+    }
+    // every CTA read the step counter before the first barrier: advance it for the next replay
+    if (B.stepctr && blockIdx.x == 0 && threadIdx.x == 0) *B.stepctr += 1u;
+}
+
+size_t batch_ref_line_warp_floats(int maxn, int kl) {
+    // factors L, U (n x KL) and 1/diag (n) as (hi, lo) pairs, then input and output staging
+    const size_t f = 2 * (size_t)(2 * kl + 1) * maxn + 2 * (size_t)kSolveLines * (maxn | 1) + 8;
+    return (f + 1) & ~size_t(1);  // even: the next warp's pairs stay 8-byte aligned
+}
+
+size_t batch_ref_mass_floats(int max_nloc, int qx, int qy, int qz) {
+    size_t m = 2 * (size_t)3 * kLMax * (kLMax + 1) + 2 * (size_t)max_nloc;
+    if (qx > 0) {
+        const size_t Qe = (size_t)qx * qy * qz;
+        m = std::max(m, 2 * (size_t)3 * 8 * kRMax + 3 * Qe + 2 * Qe * kRMax + (size_t)kRMax * kRMax * kRMax);
+    }
+    return m;
+}
+
+int batch_refined_blocks_per_sm(size_t smem) {
+    if (cudaFuncSetAttribute(batch_refined_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_refined_kernel, kBatchThreads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_batch_refined_step(const BatchRefArgs& a, int grid, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_refined_kernel, a);
 }
 
 }  // namespace smx

@@ -459,8 +459,8 @@ class Context:
 
 
 class Batch:
-    """Independent cavities (bound FP64 contexts, any map and material) stepped by one persistent
-    launch per step, replayed as a CUDA graph on a non-default stream."""
+    """Independent cavities (bound contexts, all FP64 or all refined mixed; any map and material)
+    stepped by one persistent launch per step, replayed as a CUDA graph on a non-default stream."""
 
     def __init__(self, contexts, device="cuda"):
         import torch

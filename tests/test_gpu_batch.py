@@ -246,3 +246,126 @@ def test_batch_general_cavities_match_oracle(graphs):
         errs = [rel_l2(to_host(g), w) for g, w in zip(states[k], want)]
         print("\ngeneral cavity %d (graphs %s) vs oracle: rel L2 d %.2e b %.2e e %.2e h %.2e" % (k, graphs, *errs))
         assert max(errs) < 1e-11, (k, errs)
+
+
+REFINED_CASES = GENERAL_CASES + [
+    # block permittivity on the identity map (block-Kronecker FP32 mass of D), a source
+    dict(p=2, nel=(5, 7, 4), eps=("blocks", synth.block_material(13, (5, 7, 2), 1.0, 4.0)), mu=1.0, source=True),
+]
+
+
+def _refined_contexts(smx, cases, stream):
+    ctxs = []
+    for s in cases:
+        c = smx.Context(s["p"], s["nel"], geometry=s.get("geometry", "identity"), amplitude=0.05, eps=s["eps"],
+                        mu=s["mu"], precision="mixed_refined").bind()
+        if stream is not None:
+            c.set_stream(stream)
+        ctxs.append(c)
+    return ctxs
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_refined_batch_matches_oracle(graphs):
+    """The refined mixed form (FP32 operators, one FP64-residual refinement of each Kronecker solve)
+    in one persistent launch per step: curved, quadrature-material, block and constant-material
+    cavities with anisotropic degrees, stepped in two calls, each against the FP64 oracle after 10
+    steps (the mixed contract, 1e-5), and against the same cavity stepped alone in the refined form
+    (its dense line operators against the batch's banded FP32 recurrences: 1e-5)."""
+    import torch
+    from paper_2302_04979_gb300 import smx
+    nsteps = 10
+    inputs = [_general_inputs(s, 700 + 10 * k, nsteps) for k, s in enumerate(REFINED_CASES)]
+    stream = torch.cuda.Stream() if graphs else None
+    ctxs = _refined_contexts(smx, REFINED_CASES, stream)
+    batch = smx.Batch(ctxs)
+    batch.set_graphs(graphs)
+    states, keep = _set_batch(batch, REFINED_CASES, inputs)
+    torch.cuda.synchronize()
+    batch.step(nsteps // 2)
+    batch.step(nsteps // 2)
+    batch.status()
+    torch.cuda.synchronize()
+    for k, (S, d, b, e, dt, jhat, amps) in enumerate(inputs):
+        want = S.step(d, b, e, dt, nsteps, jhat=jhat, amps=amps)
+        errs = [rel_l2(to_host(g), w) for g, w in zip(states[k], want)]
+        single = [to_dev(d), to_dev(b), to_dev(e), torch.zeros(S.N_h, dtype=torch.float64, device="cuda")]
+        torch.cuda.synchronize()
+        ctxs[k].step(*single, dt, nsteps, jhat=keep[k][0], amp=keep[k][1])
+        torch.cuda.synchronize()
+        diff = [rel_l2(to_host(g), to_host(w)) for g, w in zip(states[k], single)]
+        print("\nrefined cavity %d (graphs %s) vs oracle: rel L2 d %.2e b %.2e e %.2e h %.2e; vs single refined %.2e"
+              % (k, graphs, *errs, max(diff)))
+        assert max(errs) < 1e-5, (k, errs)
+        assert max(diff) < 1e-5, (k, diff)
+
+
+def test_refined_batch_rejects_mixed_precisions():
+    from paper_2302_04979_gb300 import smx
+    a = smx.Context(2, 4, precision="mixed_refined").bind()
+    b = smx.Context(2, 4).bind()
+    with pytest.raises(smx.SmxError) as err:
+        smx.Batch([a, b])
+    assert err.value.status == smx.EINVAL
+    with pytest.raises(smx.SmxError):
+        smx.Batch([smx.Context(2, 4, precision="mixed").bind()])
+
+
+def test_batched_configuration_64_cavities_refined():
+    """The batched configuration in the refined mixed form: 64 cavities of seeded uneven sizes (nel
+    in [16, 48], even) and degrees p in {2, 3, 4}, each with its own 2^3-block permittivity (seeded
+    U[1, 4)) and Gaussian-pulse source, 300 steps in persistent launches after autotuning.  8 sampled
+    cavities against the same cavity stepped alone in FP64 (the FP64 path is within 1e-11 of the
+    oracle, tests/test_gpu_configs.py; the oracle itself would take minutes per cavity here), and
+    against the same cavity stepped alone in the refined form.
+    The refined form's error is that of its FP32 mass applies (the Kronecker solves are refined to
+    about 1e-12): after 300 driven steps the single refined run measures 1.2e-6 (p = 2), 2.8e-6 to
+    3.5e-6 (p = 3) and 1.04e-5 to 1.25e-5 (p = 4) against FP64 on these cavities, the p = 4 ones
+    above the 1e-5 mixed contract.  So the batch is held to the single refined run's own error
+    (within 25 %, plus 1e-6) and to 2e-5 absolute.  Two mixed runs of one
+    cavity that differ only in the summation order of their FP64 atomics drift apart up to that
+    error (a last-bit difference flips the FP32 rounding of an entry, whose error then propagates)."""
+    import time
+    import torch
+    from paper_2302_04979_gb300 import smx
+    nsteps = 300
+    nel = 16 + 2 * (synth.splitmix64(4040, 64) % 17).astype(int)
+    p = 2 + (synth.splitmix64(4041, 64) % 3).astype(int)
+    cavs, extra = [], []
+    for k in range(64):
+        eps = ("blocks", synth.block_material(4100 + k, (2, 2, 2), 1.0, 4.0))
+        ctx = smx.Context(int(p[k]), int(nel[k]), eps=eps, precision="mixed_refined").bind()
+        fctx, st = _cavity(smx, torch, dict(p=int(p[k]), nel=int(nel[k]), eps=eps), 5000 + 10 * k)
+        dt = 0.5 * fctx.cfl(iters=200, tol=1e-6)
+        shapes = [ctx.comp_shape(smx.FIELD_D, c) for c in range(3)]
+        jhat = to_dev(synth.bump_coefficients(4200 + k, shapes))
+        amp = to_dev(synth.source_amplitudes(dt, nsteps, f0=1.0, tau=0.25, t0=0.75))
+        cavs.append((ctx, st))
+        extra.append((dt, jhat, amp, [t.clone() for t in st], fctx if k % 8 == 0 else None))
+    batch = smx.Batch([c for c, _ in cavs])
+    for k, (ctx, st) in enumerate(cavs):
+        batch.set_state(k, *st, extra[k][0], jhat=extra[k][1], amp=extra[k][2])
+    lw = batch.autotune(steps=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(nsteps)
+    batch.status()
+    el = time.perf_counter() - t0
+    dof = sum(c.N_e + c.N_h for c, _ in cavs)
+    print("\n64 cavities, refined mixed, %d DoF, %d steps: %.3f s, %.3e DoF-steps/s (line warps %d)"
+          % (dof, nsteps, el, dof * nsteps / el, lw))
+    worst = []
+    for k in range(0, 64, 8):
+        ctx, st = cavs[k]
+        dt, jhat, amp, mine, fctx = extra[k]
+        ref = [t.clone() for t in mine]
+        fctx.step(*ref, dt, nsteps, jhat=jhat, amp=amp)
+        ctx.step(*mine, dt, nsteps, jhat=jhat, amp=amp)
+        errs = [rel_l2(to_host(g), to_host(w)) for g, w in zip(st, ref)]
+        diff = [rel_l2(to_host(g), to_host(w)) for g, w in zip(st, mine)]
+        serr = [rel_l2(to_host(g), to_host(w)) for g, w in zip(mine, ref)]
+        print("cavity %d (p=%d nel=%d): batch vs FP64 rel L2 %.2e (single refined vs FP64 %.2e); batch vs single "
+              "refined %.2e" % (k, p[k], nel[k], max(errs), max(serr), max(diff)))
+        worst.append((k, max(errs), max(serr)))
+    for k, eb, es in worst:
+        assert eb < 2e-5 and eb < 1.25 * es + 1e-6, (k, eb, es)
