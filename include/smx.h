@@ -195,12 +195,13 @@ int smx_set_graphs(smx_ctx* ctx, int enable);
 
 /* Kernel for the line operators of the Hodge stars (Eq. kroninverse per axis).
  * Mixed steps (SMX_MIXED, SMX_MIXED_REFINED, every line length <= 80; dense products):
- *   SMX_MODE_TENSOR and SMX_MODE_AUTO (default): tcgen05 tensor cores by exact
- *     digit slicing with four digits -- lines and operator rows as 31-bit
- *     fixed-point integers, the four digit levels accumulated exactly, one
- *     rounding to FP32 at the end (more accurate than an FP32 dot product, no
- *     accumulation bias, and the faster of the two at p = 3, 64^3);
- *   SMX_MODE_SIMT: FP32 CUDA cores with the operator as FP32 (hi, lo) pairs.
+ *   SMX_MODE_TENSOR: tcgen05 tensor cores by exact digit slicing with four
+ *     digits -- lines and operator rows as 31-bit fixed-point integers, the
+ *     four digit levels accumulated exactly, one rounding to FP32 at the end
+ *     (more accurate than an FP32 dot product, no accumulation bias);
+ *   SMX_MODE_SIMT: FP32 CUDA cores with the operator as FP32 (hi, lo) pairs;
+ *   SMX_MODE_AUTO (default): the tensor cores once lines reach 32 entries,
+ *     else the CUDA cores (faster for short lines).
  * FP64 step (SMX_FP64):
  *   SMX_MODE_TENSOR (every line length <= 80): the dense operator applied on
  *     the tcgen05 tensor cores by exact digit slicing -- lines and operator
@@ -221,7 +222,7 @@ int smx_set_graphs(smx_ctx* ctx, int enable);
 int smx_set_mode_kernel(smx_ctx* ctx, int which);
 /* The line-operator selection in effect: the setting above where the
  * context has dense operators (every line length <= 80; SMX_MODE_AUTO of a
- * mixed context reads SMX_MODE_TENSOR), else SMX_MODE_SIMT.  Host only.
+ * mixed context reads the kernel it selects), else SMX_MODE_SIMT.  Host only.
  * Errors: SMX_EINVAL. */
 int smx_mode_kernel(const smx_ctx* ctx, int* which);
 

@@ -96,13 +96,15 @@ def test_calls_without_workspace_are_rejected(smx):
 
 def test_mode_kernel_selection(smx):
     ctx = smx.Context(3, 4, precision="mixed")
-    assert ctx.mode_kernel() == "tensor"  # the mixed default: four-digit tensor-core products
+    assert ctx.mode_kernel() == "simt"  # the mixed default for lines shorter than 32 entries: CUDA cores
+    assert smx.Context(3, (30, 2, 2), precision="mixed").mode_kernel() == "tensor"  # 32-entry lines
+    assert smx.Context(3, (29, 2, 2), precision="mixed").mode_kernel() == "simt"
     ctx.set_mode_kernel("tensor")
     assert ctx.mode_kernel() == "tensor"
     ctx.set_mode_kernel("simt")
     assert smx.library().smx_set_mode_kernel(ctx.h, 7) == smx.EINVAL
     ctx.set_mode_kernel("auto")
-    assert ctx.mode_kernel() == "tensor"  # mixed: "auto" is the tensor-core kernel
+    assert ctx.mode_kernel() == "simt"
     # FP64: per-star choice by default; digit-sliced tensor-core products or recurrences on request
     f64 = smx.Context(3, 20)
     assert f64.mode_kernel() == "auto"
