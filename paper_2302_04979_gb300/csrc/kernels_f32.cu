@@ -181,34 +181,56 @@ __device__ __forceinline__ void hodge_block_f32_tile(const HodgeBlockF32Args& A,
     if (act)
         for (int kk = 0; kk < Lz; ++kk) s0[(kk * Ly + jj) * Lx + ii] = to_f(__ldg(xcol + nxy * kk));
     __syncthreads();
+    // kU of a thread's Lz outputs are accumulated side by side (independent FMA chains)
+    constexpr int kU = 4;
+    const int plane = Ly * Lx;
     if (act) {  // x pass
         const int lo = max(0, ii - dg[0]), hi = min(Lx - 1, ii + dg[0]);
-        for (int kk = 0; kk < Lz; ++kk) {
-            const float* row = s0 + (kk * Ly + jj) * Lx;
-            float acc = 0.0f;
-            for (int m = lo; m <= hi; ++m) acc = fma2(Mx[ii * kLd + m], row[m], acc);
-            s1[(kk * Ly + jj) * Lx + ii] = acc;
+        for (int k0 = 0; k0 < Lz; k0 += kU) {
+            float acc[kU] = {};
+            for (int m = lo; m <= hi; ++m) {
+                const float2 c = Mx[ii * kLd + m];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (k0 + u < Lz) acc[u] = fma2(c, s0[(k0 + u) * plane + jj * Lx + m], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (k0 + u < Lz) s1[(k0 + u) * plane + jj * Lx + ii] = acc[u];
         }
     }
     __syncthreads();
     if (act) {  // y pass
         const int lo = max(0, jj - dg[1]), hi = min(Ly - 1, jj + dg[1]);
-        for (int kk = 0; kk < Lz; ++kk) {
-            const float* col = s1 + kk * Ly * Lx + ii;
-            float acc = 0.0f;
-            for (int m = lo; m <= hi; ++m) acc = fma2(My[jj * kLd + m], col[m * Lx], acc);
-            s0[(kk * Ly + jj) * Lx + ii] = acc;
+        for (int k0 = 0; k0 < Lz; k0 += kU) {
+            float acc[kU] = {};
+            for (int m = lo; m <= hi; ++m) {
+                const float2 c = My[jj * kLd + m];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (k0 + u < Lz) acc[u] = fma2(c, s1[(k0 + u) * plane + m * Lx + ii], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (k0 + u < Lz) s0[(k0 + u) * plane + jj * Lx + ii] = acc[u];
         }
     }
     __syncthreads();
-    if (act) {  // z pass and scatter-add
+    if (act) {  // z pass and scatter-add, over the union of the kU rows' bands (zeros outside a band)
         double* ycol = y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
         const float* col = s0 + jj * Lx + ii;
-        for (int kk = 0; kk < Lz; ++kk) {
-            const int lo = max(0, kk - dg[2]), hi = min(Lz - 1, kk + dg[2]);
-            float acc = 0.0f;
-            for (int m = lo; m <= hi; ++m) acc = fma2(Mz[kk * kLd + m], col[m * Ly * Lx], acc);
-            atomicAdd(ycol + nxy * kk, f2d_exact(acc));
+        for (int k0 = 0; k0 < Lz; k0 += kU) {
+            float acc[kU] = {};
+            const int lo = max(0, k0 - dg[2]), hi = min(Lz - 1, k0 + kU - 1 + dg[2]);
+            for (int m = lo; m <= hi; ++m) {
+                const float v = col[m * plane];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (k0 + u < Lz) acc[u] = fma2(Mz[(k0 + u) * kLd + m], v, acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (k0 + u < Lz) atomicAdd(ycol + nxy * (k0 + u), f2d_exact(acc[u]));
         }
     }
 }
