@@ -221,6 +221,11 @@ __device__ __forceinline__ double scaled_to_double(long long acc, int e2) {
     return __longlong_as_double((long long)(bits | ((unsigned long long)acc & (1ull << 63))));
 }
 
+// Outside the normal range: through the double routine (out of line, as above).
+__device__ __noinline__ float scaled_to_float_slow(long long acc, int e2) {
+    return (float)scaled_to_double(acc, e2);
+}
+
 // acc * 2^e2 rounded to the nearest float (ties to even), the same way (through the
 // double routine outside the normal range).
 __device__ __forceinline__ float scaled_to_float(long long acc, int e2) {
@@ -235,7 +240,7 @@ __device__ __forceinline__ float scaled_to_float(long long acc, int e2) {
         m = (a + ((1ull << (sh - 1)) - 1) + ((a >> sh) & 1ull)) >> sh;
     }
     const int be = 63 - lz + e2 + 127;
-    if (be < 1 || be + (int)(m >> 24) > 254) return (float)scaled_to_double(acc, e2);
+    if (be < 1 || be + (int)(m >> 24) > 254) return scaled_to_float_slow(acc, e2);
     const uint32_t bits = ((uint32_t)(be - 1) << 23) + (uint32_t)m;
     return __uint_as_float(bits | (acc < 0 ? 0x80000000u : 0u));
 }
