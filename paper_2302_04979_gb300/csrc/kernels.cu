@@ -362,10 +362,8 @@ __device__ __forceinline__ void solve_lines(const SolveArgs& A, int c, int lb, c
     const double* src = in + C.off;
     if (axis == 0) {
         const double* chunk = src + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            cp_async8(S + line * ldl + m, chunk + g);
-        }
+        for (int line = 0; line < nl; ++line)  // no run-time division per entry
+            for (int m = tid; m < n; m += nt) cp_async8(S + line * ldl + m, chunk + line * n + m);
     } else if (tid < nl) {
         const int l = l0 + tid;
         const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
@@ -385,10 +383,8 @@ __device__ __forceinline__ void solve_lines(const SolveArgs& A, int c, int lb, c
     double* dst = out + C.off;
     if (axis == 0) {
         double* chunk = dst + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            chunk[g] = S[line * ldl + m];
-        }
+        for (int line = 0; line < nl; ++line)
+            for (int m = tid; m < n; m += nt) chunk[line * n + m] = S[line * ldl + m];
     } else if (tid < nl) {
         const int l = l0 + tid;
         const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
@@ -515,10 +511,8 @@ __device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, int c, i
     const double* src = in + C.off;
     if (axis == 0) {
         const double* chunk = src + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            cp_async8(Sin + line * ldin + D + m, chunk + g);
-        }
+        for (int line = 0; line < nl; ++line)  // no run-time division per entry
+            for (int m = tid; m < n; m += nt) cp_async8(Sin + line * ldin + D + m, chunk + line * n + m);
     } else if (tid < nl) {
         const int l = l0 + tid;
         const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
@@ -539,10 +533,8 @@ __device__ __forceinline__ void mass_solve_body(const MassSolveArgs& A, int c, i
     double* dst = out + C.off;
     if (axis == 0) {
         double* chunk = dst + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            chunk[g] = Sout[line * ldout + m];
-        }
+        for (int line = 0; line < nl; ++line)
+            for (int m = tid; m < n; m += nt) chunk[line * n + m] = Sout[line * ldout + m];
     } else if (tid < nl) {
         const int l = l0 + tid;
         const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;

@@ -498,10 +498,8 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, int c, int lb,
     const TIN* src = in + C.off;
     if (axis == 0) {
         const TIN* chunk = src + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            Sin[line * ldin + Dp + m] = to_f(__ldg(chunk + g));
-        }
+        for (int line = 0; line < nl; ++line)  // no run-time division per entry
+            for (int m = tid; m < n; m += nt) Sin[line * ldin + Dp + m] = to_f(__ldg(chunk + line * n + m));
     } else if (tid < nl) {
         const int l = l0 + tid;
         const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
@@ -530,10 +528,8 @@ __device__ __forceinline__ void line_body_f(const LineF32Args& A, int c, int lb,
     float* dst = out + C.off;
     if (axis == 0) {
         float* chunk = dst + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            chunk[g] = res[line * ldr + m];
-        }
+        for (int line = 0; line < nl; ++line)
+            for (int m = tid; m < n; m += nt) chunk[line * n + m] = res[line * ldr + m];
     } else if (tid < nl) {
         const int l = l0 + tid;
         const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
@@ -651,26 +647,23 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
     for (int t = tid; t < n * NPAD / 2; t += nt) cp_async16f(Bt + 2 * t, Bg + 2 * t);
     const int nx = C.n[0], nxy = C.n[0] * C.n[1];
     const TIN* src = in + C.off;
+    // warps along lines (x sweep) or along entries (y, z), lanes the other way: no run-time
+    // division per entry (kModeLines = 32 lines: one per lane)
+    const int wq = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+    static_assert(kModeLines == 32, "one line per lane");
     if (axis == 0) {
         const TIN* chunk = src + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            T[m * kModeLd + line] = to_f(chunk[g]);
-        }
+        for (int line = wq; line < nl; line += nwarps)
+            for (int m = lane; m < n; m += 32) T[m * kModeLd + line] = to_f(chunk[line * n + m]);
     } else {
         const int stride = axis == 1 ? nx : nxy;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int m = g / nl, w = g - m * nl;
-            const int l = l0 + w;
-            const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-            T[m * kModeLd + w] = to_f(src[base + m * stride]);
-        }
+        const int l = l0 + lane;
+        const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        for (int m = wq; m < n; m += nwarps) T[m * kModeLd + lane] = lane < nl ? to_f(src[base + m * stride]) : 0.0f;
     }
-    if (nl < kModeLines)  // keep the unused tile columns finite
-        for (int g = tid; g < (kModeLines - nl) * n; g += nt) {
-            const int m = g / (kModeLines - nl), w = nl + g - m * (kModeLines - nl);
-            T[m * kModeLd + w] = 0.0f;
-        }
+    if (axis == 0 && nl < kModeLines)  // keep the unused tile columns finite
+        for (int m = wq; m < n; m += nwarps)
+            if (lane >= nl) T[m * kModeLd + lane] = 0.0f;
     cp_async_wait_all_f();
     __syncthreads();
     const int lg = tid % kModeLineGroups, og = tid / kModeLineGroups;
@@ -704,18 +697,13 @@ __global__ void __launch_bounds__(kModeLineGroups* kModeOutGroups) mode_f32_kern
     float* dst = out + C.off;
     if (axis == 0) {
         float* chunk = dst + (long long)l0 * n;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int line = g / n, m = g - line * n;
-            chunk[g] = T[m * kModeLd + line];
-        }
-    } else {
+        for (int line = wq; line < nl; line += nwarps)
+            for (int m = lane; m < n; m += 32) chunk[line * n + m] = T[m * kModeLd + line];
+    } else if (lane < nl) {
         const int stride = axis == 1 ? nx : nxy;
-        for (int g = tid; g < nl * n; g += nt) {
-            const int m = g / nl, ww = g - m * nl;
-            const int l = l0 + ww;
-            const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
-            dst[base + m * stride] = T[m * kModeLd + ww];
-        }
+        const int l = l0 + lane;
+        const int base = axis == 1 ? (l % nx) + (l / nx) * nxy : l;
+        for (int m = wq; m < n; m += nwarps) dst[base + m * stride] = T[m * kModeLd + lane];
     }
 }
 
