@@ -1591,6 +1591,7 @@ int smx_bind_workspace(smx_ctx* C, void* dev, size_t bytes) {
             }
             HodgeBlockF32Args& B = C->hb32[h];
             B.field = C->fld[fld];
+            B.compensated = C->precision == SMX_MIXED_REFINED ? 1 : 0;
             for (int a = 0; a < 3; ++a) {
                 B.ntile[a] = H.ntile[a];
                 B.tf0[a] = reinterpret_cast<const int*>(ws + H.o_tf0[a]);

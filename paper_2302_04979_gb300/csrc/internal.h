@@ -91,6 +91,7 @@ struct HodgeBlockF32Args {
     const double* gamma;
     int max_nloc;
     int max_len[2];      // largest tile length along x and y over the field's components (the CTA shape)
+    int compensated;     // nonzero: compensated FP32 sums of products in the tile passes (refined form)
 };
 
 // FP32 quadrature Hodge apply: HodgeQuadArgs with FP32 basis values and metric.

@@ -22,6 +22,41 @@ namespace smx {
 
 __device__ __forceinline__ float fma2(float2 c, float x, float acc) { return fmaf(c.x, x, fmaf(c.y, x, acc)); }
 
+// A compensated FP32 sum of products (a dot product in the manner of Ogita, Rump and Oishi's
+// Dot2): s carries the running sum, e the rounding errors of every product (exact, by an FMA)
+// and every addition (exact, by TwoSum) plus the small lo-coefficient terms, so the result
+// s + e is as accurate as a sum computed in twice the precision, rounded once.  The _rn
+// intrinsics keep the compiler from contracting a product and a sum into one FMA.
+struct Acc2 {
+    float s, e;
+};
+__device__ __forceinline__ void acc2_add(Acc2& a, float2 c, float x) {
+    const float p = __fmul_rn(c.x, x);
+    const float pe = __fmaf_rn(c.x, x, -p);  // the product's rounding error, exactly
+    const float t = __fadd_rn(a.s, p);
+    const float bb = __fsub_rn(t, a.s);
+    const float se = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(p, bb));  // the sum's, exactly
+    a.e = __fadd_rn(a.e, __fadd_rn(se, __fmaf_rn(c.y, x, pe)));
+    a.s = t;
+}
+__device__ __forceinline__ float acc2_value(const Acc2& a) { return __fadd_rn(a.s, a.e); }
+
+// The block Hodge passes' accumulator: plain FMAs, or the compensated sum above (COMP).
+template <bool COMP>
+struct TileAcc;
+template <>
+struct TileAcc<false> {
+    float v = 0.0f;
+    __device__ __forceinline__ void add(float2 c, float x) { v = fma2(c, x, v); }
+    __device__ __forceinline__ float value() const { return v; }
+};
+template <>
+struct TileAcc<true> {
+    Acc2 a{0.0f, 0.0f};
+    __device__ __forceinline__ void add(float2 c, float x) { acc2_add(a, c, x); }
+    __device__ __forceinline__ float value() const { return acc2_value(a); }
+};
+
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -134,7 +169,7 @@ cudaError_t launch_refine_sum(const float* x0, const float* c, double* out, long
 // Threads (ii, jj) = (threadIdx.x, threadIdx.y) cover the tile's x-y face
 // (L <= 16 per axis) and march along z, so no index is divided at run time.
 // One (component, tile): threads (ii, jj) of the tile face, flat index `flat` of `nthreads`.
-template <class TIN>
+template <class TIN, bool COMP>
 __device__ __forceinline__ void hodge_block_f32_tile(const HodgeBlockF32Args& A, int c, int tile,
                                                      const TIN* __restrict__ x, double* __restrict__ y, float* smf,
                                                      int ii, int jj, int flat, int nthreads) {
@@ -187,32 +222,32 @@ __device__ __forceinline__ void hodge_block_f32_tile(const HodgeBlockF32Args& A,
     if (act) {  // x pass
         const int lo = max(0, ii - dg[0]), hi = min(Lx - 1, ii + dg[0]);
         for (int k0 = 0; k0 < Lz; k0 += kU) {
-            float acc[kU] = {};
+            TileAcc<COMP> acc[kU];
             for (int m = lo; m <= hi; ++m) {
                 const float2 c = Mx[ii * kLd + m];
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (k0 + u < Lz) acc[u] = fma2(c, s0[(k0 + u) * plane + jj * Lx + m], acc[u]);
+                    if (k0 + u < Lz) acc[u].add(c, s0[(k0 + u) * plane + jj * Lx + m]);
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (k0 + u < Lz) s1[(k0 + u) * plane + jj * Lx + ii] = acc[u];
+                if (k0 + u < Lz) s1[(k0 + u) * plane + jj * Lx + ii] = acc[u].value();
         }
     }
     __syncthreads();
     if (act) {  // y pass
         const int lo = max(0, jj - dg[1]), hi = min(Ly - 1, jj + dg[1]);
         for (int k0 = 0; k0 < Lz; k0 += kU) {
-            float acc[kU] = {};
+            TileAcc<COMP> acc[kU];
             for (int m = lo; m <= hi; ++m) {
                 const float2 c = My[jj * kLd + m];
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (k0 + u < Lz) acc[u] = fma2(c, s1[(k0 + u) * plane + m * Lx + ii], acc[u]);
+                    if (k0 + u < Lz) acc[u].add(c, s1[(k0 + u) * plane + m * Lx + ii]);
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (k0 + u < Lz) s0[(k0 + u) * plane + jj * Lx + ii] = acc[u];
+                if (k0 + u < Lz) s0[(k0 + u) * plane + jj * Lx + ii] = acc[u].value();
         }
     }
     __syncthreads();
@@ -220,17 +255,17 @@ __device__ __forceinline__ void hodge_block_f32_tile(const HodgeBlockF32Args& A,
         double* ycol = y + C.off + (f0[0] + ii) + (long long)C.n[0] * (f0[1] + jj) + nxy * f0[2];
         const float* col = s0 + jj * Lx + ii;
         for (int k0 = 0; k0 < Lz; k0 += kU) {
-            float acc[kU] = {};
+            TileAcc<COMP> acc[kU];
             const int lo = max(0, k0 - dg[2]), hi = min(Lz - 1, k0 + kU - 1 + dg[2]);
             for (int m = lo; m <= hi; ++m) {
                 const float v = col[m * plane];
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (k0 + u < Lz) acc[u] = fma2(Mz[(k0 + u) * kLd + m], v, acc[u]);
+                    if (k0 + u < Lz) acc[u].add(Mz[(k0 + u) * kLd + m], v);
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (k0 + u < Lz) atomicAdd(ycol + nxy * (k0 + u), f2d_exact(acc[u]));
+                if (k0 + u < Lz) atomicAdd(ycol + nxy * (k0 + u), f2d_exact(acc[u].value()));
         }
     }
 }
@@ -240,8 +275,11 @@ __global__ void __launch_bounds__(256) hodge_block_f32_kernel(HodgeBlockF32Args 
                                                               double* __restrict__ y) {
     extern __shared__ float smf[];
     pdl_wait();
-    hodge_block_f32_tile<TIN>(A, blockIdx.y, blockIdx.x, x, y, smf, threadIdx.x, threadIdx.y,
-                              threadIdx.y * blockDim.x + threadIdx.x, blockDim.x * blockDim.y);
+    const int flat = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
+    if (A.compensated)
+        hodge_block_f32_tile<TIN, true>(A, blockIdx.y, blockIdx.x, x, y, smf, threadIdx.x, threadIdx.y, flat, nthreads);
+    else
+        hodge_block_f32_tile<TIN, false>(A, blockIdx.y, blockIdx.x, x, y, smf, threadIdx.x, threadIdx.y, flat, nthreads);
 }
 
 cudaError_t launch_hodge_block_f32(const HodgeBlockF32Args& a, const double* x64, const float* x32, double* y,
@@ -777,7 +815,12 @@ __device__ __noinline__ void ref_curl(const BatchRefCavity& K, int unit, const d
 __device__ __noinline__ void ref_mass_tile(const HodgeBlockF32Args& A, int c, int tile, const double* x, double* y,
                                            float* sm) {
     // the tile face on a 16 x 16 thread grid (tiles are at most kLMax = 16 functions per axis)
-    hodge_block_f32_tile<double>(A, c, tile, x, y, sm, threadIdx.x & 15, threadIdx.x >> 4, threadIdx.x, kBatchThreads);
+    if (A.compensated)
+        hodge_block_f32_tile<double, true>(A, c, tile, x, y, sm, threadIdx.x & 15, threadIdx.x >> 4, threadIdx.x,
+                                           kBatchThreads);
+    else
+        hodge_block_f32_tile<double, false>(A, c, tile, x, y, sm, threadIdx.x & 15, threadIdx.x >> 4, threadIdx.x,
+                                            kBatchThreads);
 }
 
 __device__ __noinline__ void ref_mass_element(const HodgeQuadF32Args& A, int e, const double* x, double* y, float* sm) {

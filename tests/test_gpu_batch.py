@@ -319,12 +319,12 @@ def test_batched_configuration_64_cavities_refined():
     oracle, tests/test_gpu_configs.py; the oracle itself would take minutes per cavity here), and
     against the same cavity stepped alone in the refined form.
     The refined form's error is that of its FP32 mass applies (the Kronecker solves are refined to
-    about 1e-12): after 300 driven steps the single refined run measures 1.2e-6 (p = 2), 2.8e-6 to
-    3.5e-6 (p = 3) and 1.04e-5 to 1.25e-5 (p = 4) against FP64 on these cavities, the p = 4 ones
-    above the 1e-5 mixed contract.  So the batch is held to the single refined run's own error
-    (within 25 %, plus 1e-6) and to 2e-5 absolute.  Two mixed runs of one
-    cavity that differ only in the summation order of their FP64 atomics drift apart up to that
-    error (a last-bit difference flips the FP32 rounding of an entry, whose error then propagates)."""
+    about 1e-12; the tile passes use compensated FP32 sums): after 300 driven steps it measures
+    7.3e-7 (p = 2), 1.4e-6 to 1.7e-6 (p = 3) and 4.3e-6 to 5.2e-6 (p = 4) against FP64 on these
+    cavities, in the batch and in single runs alike: the mixed contract, 1e-5.  Two mixed runs of
+    one cavity that differ only in the summation order of their FP64 atomics drift apart up to
+    that error (a last-bit difference flips the FP32 rounding of an entry, whose error then
+    propagates), so the batch and the single refined run are compared at 2e-5."""
     import time
     import torch
     from paper_2302_04979_gb300 import smx
@@ -366,6 +366,6 @@ def test_batched_configuration_64_cavities_refined():
         serr = [rel_l2(to_host(g), to_host(w)) for g, w in zip(mine, ref)]
         print("cavity %d (p=%d nel=%d): batch vs FP64 rel L2 %.2e (single refined vs FP64 %.2e); batch vs single "
               "refined %.2e" % (k, p[k], nel[k], max(errs), max(serr), max(diff)))
-        worst.append((k, max(errs), max(serr)))
-    for k, eb, es in worst:
-        assert eb < 2e-5 and eb < 1.25 * es + 1e-6, (k, eb, es)
+        worst.append((k, max(errs), max(serr), max(diff)))
+    for k, eb, es, ed in worst:
+        assert eb < 1e-5 and es < 1e-5 and ed < 2e-5, (k, eb, es, ed)
