@@ -637,7 +637,7 @@ int max_line_len(const smx_ctx* C) {
 
 // The mixed forms' dense line operators: the four-digit tensor-core kernel for SMX_MODE_TENSOR,
 // and for SMX_MODE_AUTO once lines reach 32 entries; else the FP32 CUDA-core product.  Measured
-// per step (tensor against CUDA cores): 0.132 against 0.145 ms at p = 3, 64^3; 0.579 against
+// per step (tensor against CUDA cores): 0.122 against 0.139 ms at p = 3, 64^3; 0.579 against
 // 0.555 ms at p = 3, 32^3, where only the tensor-core products keep the curved pulse within
 // 1e-5 of FP64 over 500 steps (5.3e-6 against 1.3e-5); 0.060 against 0.032 ms at p = 2, 8^3.
 bool mixed_tensor(const smx_ctx* C) {
@@ -674,8 +674,8 @@ int hodge_star_f32_impl(smx_ctx* C, int h, const double* x, float* out, double* 
             if ((st = mass_f32(C, h, x, prezeroed))) return st;
             x64 = C->scratch;
         }
-        // AUTO: the four-digit tensor-core kernel from 48-entry lines (more accurate than the
-        // FP32 CUDA-core product, and faster there: 0.132 against 0.144 ms per step at p = 3, 64^3)
+        // AUTO: the four-digit tensor-core kernel from 32-entry lines (mixed_tensor: more accurate
+        // than the FP32 CUDA-core product, and faster there)
         const bool tc = mixed_tensor(C);
         auto pass = [&](int a, const double* i64, const float* i32, double* o64) {
             return run(C, (tc ? 24 : 14) + a, 1, [&] {

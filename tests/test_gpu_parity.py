@@ -32,9 +32,12 @@ CASES = {
 
 # Solves amplify rounding by the condition numbers of the 1D pairing factors:
 # about 30 for p <= 4, 1e2 for p = 5 and 4e2 for p = 6 (oracle, Sec. 4.1
-# matrices), and a 3D Kronecker solve multiplies three of them.  The FP64
-# contract (1e-11) is stated for the configurations' degrees p <= 4; p = 5, 6
-# get the same bound scaled by the growth of that product.
+# matrices), and a 3D Kronecker solve multiplies three of them (kappa eps is
+# about 7e-9 at p = 6).  The FP64 contract (1e-11) is stated for the
+# configurations' degrees p <= 4; p = 5, 6 get the same bound scaled by the
+# growth of that product.  Measured on GB300, every p = 5, 6 error but one sits
+# below the unscaled bound; the exception is the star of B at p = 6,
+# 3.3e-11 (the printed errors show it).
 COND_SCALE = {5: 10.0, 6: 100.0}
 
 
@@ -132,7 +135,9 @@ def test_hodge_star(pair):
     b = synth.uniform(31, S.N_h, -1, 1)
     h = torch.empty(S.N_h, dtype=torch.float64, device="cuda")
     G.hodge_star(smx.FIELD_B, to_dev(b), h)
-    assert rel_l2(to_host(h), S.h_from_b(b)) < 1e-11 * cond_scale(name)
+    err = rel_l2(to_host(h), S.h_from_b(b))
+    print("%s Hodge star of B: rel L2 %.2e" % (name, err))
+    assert err < 1e-11 * cond_scale(name)
 
 
 def test_leapfrog_steps_with_source(pair):
