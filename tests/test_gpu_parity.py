@@ -160,6 +160,35 @@ def test_leapfrog_steps_with_source(pair):
     assert max(errs) < 1e-11 * cond_scale(name)
 
 
+
+def test_step_host(pair):
+    """smx_step_host: the same steps from host buffers, pinned and pageable, with the copies in and
+    out inside the call; equal to smx_step on device buffers up to the atomics' summation order
+    (1e-13) and within the FP64 contract of the oracle."""
+    import torch
+    name, S, G = pair
+    nsteps = 5
+    d = synth.uniform(60, S.N_e, -1, 1)
+    b = S.D1 @ synth.uniform(61, S.N_e, -1, 1)
+    e = S.e_from_d(d)
+    jhat = synth.uniform(62, S.N_e, -1, 1)
+    dt = 0.02 / max(np.max(S.nel), 1)
+    amps = synth.source_amplitudes(dt, nsteps)
+    ref = S.step(d, b, e, dt, nsteps, jhat=jhat, amps=amps)
+    jd, ad = to_dev(jhat), to_dev(amps)
+    dd, bd, ed = to_dev(d), to_dev(b), to_dev(e)
+    hd = torch.zeros(S.N_h, dtype=torch.float64, device="cuda")
+    G.step(dd, bd, ed, hd, dt, nsteps, jhat=jd, amp=ad)
+    dev = [to_host(t) for t in (dd, bd, ed, hd)]
+    for pinned in (True, False):
+        host = [torch.from_numpy(v.copy()) for v in (d, b, e)] + [torch.zeros(S.N_h, dtype=torch.float64)]
+        if pinned:
+            host = [t.pin_memory() for t in host]
+        G.step_host(*host, dt, nsteps, jhat=jd, amp=ad)
+        got = [t.numpy() for t in host]
+        assert max(rel_l2(g, w) for g, w in zip(got, dev)) < 1e-13
+        assert max(rel_l2(g, w) for g, w in zip(got, ref)) < 1e-11 * cond_scale(name)
+
 def test_energy(pair):
     _, S, G = pair
     d = synth.uniform(50, S.N_e, -1, 1)
