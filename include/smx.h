@@ -288,7 +288,10 @@ int smx_cfl(smx_ctx* ctx, int iters, double tol, double* v, double* w, double* t
 /* nsteps leapfrog steps on HOST state: copies d, b, e (host, FP64) into the
  * workspace's state vectors, runs smx_step there, copies d, b, e, h back and
  * synchronises.  Host buffers should be pinned for asynchronous copies.
- * jhat and amp as in smx_step (device pointers or NULL). */
+ * jhat and amp as in smx_step (device pointers or NULL).  On an error the
+ * stream is synchronised before the return, so no copy is left reading or
+ * writing the host buffers; an error of the step itself leaves d, b, e, h
+ * unchanged.  Errors: those of smx_step, SMX_ECUDA (a copy). */
 int smx_step_host(smx_ctx* ctx, double* d, double* b, double* e, double* h,
                   const double* jhat, const double* amp, double dt, int nsteps);
 
@@ -474,8 +477,9 @@ int smx_adjoint_terminal(smx_ctx* ctx, const double* d_N, const double* ebar, do
 typedef struct smx_batch smx_batch;
 
 /* Build a batch over n bound contexts (host arrays; the contexts must outlive
- * the batch and share one stream, that of ctxs[0]), all SMX_FP64 or all
- * SMX_MIXED_REFINED.  Host memory only.
+ * the batch, stay bound to the workspaces they had here -- the batch keeps
+ * their table and buffer addresses -- and share one stream, that of ctxs[0]),
+ * all SMX_FP64 or all SMX_MIXED_REFINED.  Host memory only.
  * Errors: SMX_EINVAL (a context is unbound, or of another precision than
  * ctxs[0], or neither SMX_FP64 nor SMX_MIXED_REFINED), SMX_ENOMEM. */
 int smx_batch_create(int n, smx_ctx* const* ctxs, smx_batch** out);

@@ -1910,15 +1910,22 @@ int smx_step_host(smx_ctx* C, double* d, double* b, double* e, double* h, const 
     double* bd = ed + C->N_e;
     double* hd = bd + C->N_h;
     const size_t se = C->N_e * sizeof(double), sh = C->N_h * sizeof(double);
-    CK(cudaMemcpyAsync(dd, d, se, cudaMemcpyHostToDevice, C->stream));
-    CK(cudaMemcpyAsync(ed, e, se, cudaMemcpyHostToDevice, C->stream));
-    CK(cudaMemcpyAsync(bd, b, sh, cudaMemcpyHostToDevice, C->stream));
-    int st = smx_step(C, dd, bd, ed, hd, jhat, amp, dt, nsteps);
-    if (st) return st;
-    CK(cudaMemcpyAsync(d, dd, se, cudaMemcpyDeviceToHost, C->stream));
-    CK(cudaMemcpyAsync(e, ed, se, cudaMemcpyDeviceToHost, C->stream));
-    CK(cudaMemcpyAsync(b, bd, sh, cudaMemcpyDeviceToHost, C->stream));
-    CK(cudaMemcpyAsync(h, hd, sh, cudaMemcpyDeviceToHost, C->stream));
+    // on any error, no copy may still read or write the caller's host buffers after the return
+    auto fail = [&](int st) {
+        cudaStreamSynchronize(C->stream);
+        return st;
+    };
+    auto copy = [&](void* dst, const void* src, size_t n, cudaMemcpyKind kind) {
+        return cudaMemcpyAsync(dst, src, n, kind, C->stream) == cudaSuccess;
+    };
+    if (!copy(dd, d, se, cudaMemcpyHostToDevice) || !copy(ed, e, se, cudaMemcpyHostToDevice) ||
+        !copy(bd, b, sh, cudaMemcpyHostToDevice))
+        return fail(SMX_ECUDA);
+    const int st = smx_step(C, dd, bd, ed, hd, jhat, amp, dt, nsteps);
+    if (st) return fail(st);
+    if (!copy(d, dd, se, cudaMemcpyDeviceToHost) || !copy(e, ed, se, cudaMemcpyDeviceToHost) ||
+        !copy(b, bd, sh, cudaMemcpyDeviceToHost) || !copy(h, hd, sh, cudaMemcpyDeviceToHost))
+        return fail(SMX_ECUDA);
     CK(cudaStreamSynchronize(C->stream));
     return SMX_OK;
 }
