@@ -26,6 +26,11 @@ maxwell   scheme 2 leapfrog step, energy, CFL by power iteration,
           L2 projection and error norms (Sec. 3.4, Sec. 4.2, Sec. 5)
 scheme1   scheme 1: 1-form mass matrices M^1_eps, M~^1_mu and the leapfrog
           with mass-matrix Hodge stars, energy, CFL (Sec. 3.3, Sec. 5.2)
+lifting   scheme 2 with a prescribed tangential trace of E: the whole spaces
+          X^1_h, X^2_h, the local projection of the boundary data, and the
+          lifted leapfrog (Sec. 3.5, Sec. 5.1.2)
+adjoint   the discrete adjoint of the scheme-2 step (a derivative of the
+          discrete map, not a passage of the paper)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against closed forms, identities the paper states,

@@ -15,6 +15,9 @@ Paper passages followed:
     C-ordered array of shape (N_z, N_y, N_x).
   * Remark on incidence matrices after Table 1: D^k and D~^k are Kronecker
     products of 1D incidence matrices and identities.
+  * Sec. 3.5: with a prescribed tangential trace of E, E_h and B_h live in the
+    whole X^1_h and X^2_h ('EF', 'BF': the 'PF' kind in place of 'P0') and
+    D^1 maps X^1_h to X^2_h.
 
 Component k of a 2-form is the coefficient of dy^dz, dz^dx, dx^dy for
 k = 0, 1, 2; component k of a 1-form is that of dx, dy, dz.  A global vector
@@ -31,6 +34,9 @@ FIELD_KINDS = {
     "B": (("P0", "P1", "P1"), ("P1", "P0", "P1"), ("P1", "P1", "P0")),
     "H": (("D1", "D0", "D0"), ("D0", "D1", "D0"), ("D0", "D0", "D1")),
     "D": (("D0", "D1", "D1"), ("D1", "D0", "D1"), ("D1", "D1", "D0")),
+    # the whole primal spaces X^1_h, X^2_h (boundary functions kept, Sec. 3.5)
+    "EF": (("P1", "PF", "PF"), ("PF", "P1", "PF"), ("PF", "PF", "P1")),
+    "BF": (("PF", "P1", "P1"), ("P1", "PF", "P1"), ("P1", "P1", "PF")),
     # 3-forms (targets of the divergence), single component
     "B3": (("P1", "P1", "P1"),),
     "D3": (("D1", "D1", "D1"),),
@@ -93,20 +99,22 @@ def _axis_operator(op1d, axis, in_kinds, p, nel):
 def _derivative_1d(kind, p, nel):
     if kind == "P0":
         return splines.incidence_primal(p, nel)
+    if kind == "PF":
+        return splines.incidence_full(p, nel)
     if kind == "D0":
         return splines.incidence_dual(p, nel)
     raise ValueError("no derivative from kind " + kind)
 
 
 def curl_matrix(src, p, nel):
-    """3D incidence for the curl: D^1 (src='E', E -> B) or D~^1 (src='H', H -> D).
+    """3D incidence for the curl: D^1 (src='E', E -> B; src='EF', X^1_h -> X^2_h) or D~^1 (src='H', H -> D).
 
     (curl u)_c = d_{c+1} u_{c+2} - d_{c+2} u_{c+1}, indices mod 3
     (Eq. maxwell_discrete; Remark on incidence matrices after Table 1).
     """
     p, nel = as3(p), as3(nel)
     kinds = FIELD_KINDS[src]
-    dst = {"E": "B", "H": "D"}[src]
+    dst = {"E": "B", "H": "D", "EF": "BF"}[src]
     in_sizes = comp_sizes(src, p, nel)
     out_sizes = comp_sizes(dst, p, nel)
     blocks = [[None] * 3 for _ in range(3)]
@@ -125,12 +133,12 @@ def curl_matrix(src, p, nel):
     return out
 
 
-def grad_matrix(p, nel, dual=False):
-    """3D incidence D^0 (primal, 0-forms of S_p,0^3 -> E) or D~^0 (dual, S_{p-1}^3 -> H)."""
+def grad_matrix(p, nel, dual=False, full=False):
+    """3D incidence D^0 (primal, 0-forms of S_p,0^3 -> E; full=True: S_p^3 -> X^1_h) or D~^0 (dual, S_{p-1}^3 -> H)."""
     p, nel = as3(p), as3(nel)
-    k0 = "D0" if dual else "P0"
+    k0 = "D0" if dual else ("PF" if full else "P0")
     kinds0 = (k0, k0, k0)
-    dst = "H" if dual else "E"
+    dst = "H" if dual else ("EF" if full else "E")
     rows = []
     for c in range(3):
         d = _derivative_1d(k0, p[c], nel[c])

@@ -139,7 +139,8 @@ def integrate(Bx, By, Bz, V):
 # ---------------------------------------------------------------- Hodge mass
 
 class HodgeMass:
-    """Mass matrix of the 2-form space of ``field`` ('B': X^2_{h,0}, 'D': X~^2) weighted by gamma.
+    """Mass matrix of the 2-form space of ``field`` ('B': X^2_{h,0}, 'D': X~^2, 'BF': the whole X^2_h
+    of Sec. 3.5) weighted by gamma.
 
     gamma is 1/mu for B (Eq. discrete2_hodge_mu) and 1/eps for D
     (Eq. discrete2_hodge_eps); ``gamma_spec`` is given as the material
@@ -147,7 +148,7 @@ class HodgeMass:
     """
 
     def __init__(self, field, p, nel, geometry, material_spec, invert=True):
-        assert field in ("B", "D")
+        assert field in ("B", "D", "BF")
         self.field = field
         self.p, self.nel = forms3d.as3(p), forms3d.as3(nel)
         g = QuadGrid(self.p, self.nel, geometry)

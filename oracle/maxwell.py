@@ -143,7 +143,8 @@ class Scheme2:
 
     # ---- projection and errors (Sec. 5.1.1: initial data by projection)
     def project_2form(self, field, V, rtol=1e-14):
-        """L2 projection of a physical 2-form (vector proxy V(x, y, z) -> (3,...)) onto X~^2 or X^2_{h,0}."""
+        """L2 projection of a physical 2-form (vector proxy V(x, y, z) -> (3,...)) onto X~^2 ('D'), X^2_{h,0}
+        ('B') or the whole X^2_h ('BF', Sec. 3.5)."""
         M1 = hodge.HodgeMass(field, self.p, self.nel, self.geometry, 1.0)
         g = M1.grid
         Vp = np.asarray(V(*g.phys))
@@ -158,11 +159,11 @@ class Scheme2:
         return x
 
     def l2_error(self, field, coeffs, exact, extra=2):
-        """(||u_h - u||_L2, ||u||_L2) for a 1-form ('E', 'H') or 2-form ('D', 'B') against exact(x,y,z)."""
+        """(||u_h - u||_L2, ||u||_L2) for a 1-form ('E', 'H', 'EF') or 2-form ('D', 'B', 'BF') against exact(x,y,z)."""
         g = hodge.QuadGrid(self.p, self.nel, self.geometry, extra=extra)
         xs = forms3d.split(field, np.asarray(coeffs, dtype=np.float64), self.p, self.nel)
         uh = np.array([hodge.interpolate(*g.basis(field, c), xs[c]) for c in range(3)])
-        if field in ("E", "H"):
+        if field in ("E", "H", "EF"):
             # 1-form: u = J^{-T} u^
             Jinv = np.linalg.inv(np.moveaxis(g.J, (0, 1), (-2, -1)))
             u = np.einsum("...ki,k...->i...", Jinv, uh)

@@ -23,10 +23,14 @@ The four univariate space kinds are named after where they sit in 3D:
   'D0'  dual   S_{p-1}(Xi')  (B-splines)
   'D1'  dual   S_{p-2}(Xi'') (Curry-Schoenberg)
 With n = nel + p: dim P0 = n-2, dim P1 = n-1, dim D0 = n-1, dim D1 = n-2.
+A fifth kind, 'PF', is the whole primal S_p(Xi) (n B-splines, boundary
+functions kept): the spaces X^1_h and X^2_h of Sec. 3.5, where the tangential
+trace of E is prescribed by a lifting instead of set to zero.  Function 0
+(n-1) is the only one that is nonzero at x = 0 (x = 1).
 """
 import numpy as np
 
-SPACE_KINDS = ("P0", "P1", "D0", "D1")
+SPACE_KINDS = ("P0", "P1", "D0", "D1", "PF")
 
 
 def open_knot_vector(p, nel):
@@ -79,12 +83,12 @@ def curry_schoenberg_values(knots, degree, x):
 
 
 def space_degree(kind, p):
-    return {"P0": p, "P1": p - 1, "D0": p - 1, "D1": p - 2}[kind]
+    return {"P0": p, "P1": p - 1, "D0": p - 1, "D1": p - 2, "PF": p}[kind]
 
 
 def space_dim(kind, p, nel):
     n = nel + p
-    return {"P0": n - 2, "P1": n - 1, "D0": n - 1, "D1": n - 2}[kind]
+    return {"P0": n - 2, "P1": n - 1, "D0": n - 1, "D1": n - 2, "PF": n}[kind]
 
 
 def space_values(kind, p, nel, x):
@@ -92,6 +96,8 @@ def space_values(kind, p, nel, x):
     xi = open_knot_vector(p, nel)
     if kind == "P0":
         return bspline_values(xi, p, x)[:, 1:-1]
+    if kind == "PF":
+        return bspline_values(xi, p, x)
     if kind == "P1":
         return curry_schoenberg_values(xi[1:-1], p - 1, x)
     if kind == "D0":
@@ -159,6 +165,21 @@ def incidence_primal(p, nel):
             Dm[j, j] = 1.0
         if j - 1 >= 0:
             Dm[j, j - 1] = -1.0
+    return Dm
+
+
+def incidence_full(p, nel):
+    """1D derivative PF -> P1 on the whole S_p(Xi): (d c)_k = c_{k+1} - c_k.  Shape (n-1, n).
+
+    The same identity d/dx B_{i,p} = D_{i-1} - D_i as ``incidence_primal``, with
+    the boundary functions kept (Sec. 3.5: D^1 between X^1_h and X^2_h).
+    ``incidence_primal`` is this matrix without its first and last column.
+    """
+    n = nel + p
+    Dm = np.zeros((n - 1, n))
+    for k in range(n - 1):
+        Dm[k, k + 1] = 1.0
+        Dm[k, k] = -1.0
     return Dm
 
 
