@@ -13,6 +13,9 @@ Paper passages followed:
     whole X^2_h, D^1 maps X^1_h to X^2_h, and M^2_{1/mu} takes its columns in
     X^2_h while its rows stay the test functions of X^2_{h,0}: these matrices
     are applied, never inverted.
+  * Sec. 3.5, scheme 1: with M^1_eps on the whole X^1_h split into blocks,
+    the star of D becomes M^1_{eps,00} e_0 = K~_2 d - M^1_{eps,0b} e_b, and
+    K_2 in the star of B takes its columns in X^2_h.
   * Sec. 5.1.2: boundary data that is a separable function of space and time
     is lifted once; every step multiplies the lifted coefficient vectors by
     the known functions of time.
@@ -40,7 +43,8 @@ component.
 import numpy as np
 import scipy.sparse as sp
 
-from . import forms3d, hodge, maxwell, splines
+
+from . import forms3d, hodge, maxwell, scheme1, splines
 
 
 # ---------------------------------------------------------------- index sets
@@ -261,6 +265,44 @@ class LiftedScheme2:
             e0 = self.e0_from_d(d, t + dt)
             b = b - 0.5 * dt * (self.D1F @ self.e_full(e0, t + dt))
         return d, b, e0, h
+
+
+class LiftedScheme1(LiftedScheme2):
+    """Scheme 1 (Sec. 3.3) with the tangential trace of E prescribed (Sec. 3.5); same state and
+    time levels as ``LiftedScheme2``.
+
+    Stars: M~^1_mu h = K_2 b with K_2 pairing X~^1 (rows) with the whole X^2_h,
+    and M^1_{eps,00} e_0 = K~_2 d - M^1_{eps,0b} e_b(t), both solved directly
+    (sparse LU of the assembled interior blocks, as ``scheme1.Scheme1``).
+    """
+
+    def __init__(self, p, nel, geometry=None, eps=1.0, mu=1.0, boundary=()):
+        super().__init__(p, nel, geometry=geometry, eps=eps, mu=mu, boundary=boundary)
+        self.S1 = scheme1.Scheme1(self.p, self.nel, geometry=self.geometry, eps=eps, mu=mu)
+        # M^1_eps on the whole X^1_h (rows and columns), then its interior rows
+        g = self.S1.M1.grid
+        Bf = [g.basis("EF", c) for c in range(3)]
+        Bk = [forms3d._kron3(*[sp.csr_matrix(m) for m in Bf[c]]) for c in range(3)]
+        G = self.S1.M1.G
+        blocks = [[(Bk[c].T @ sp.diags(G[c, c2].reshape(-1)) @ Bk[c2]).tocsr() for c2 in range(3)]
+                  for c in range(3)]
+        self.M1F = sp.bmat(blocks, format="csr")
+        self.M1_0b = self.M1F[self.e_in][:, self.e_bd]
+        # K_2: X~^1 rows against the whole X^2_h
+        kb = []
+        for c in range(3):
+            rk, ck = forms3d.FIELD_KINDS["H"][c], forms3d.FIELD_KINDS["BF"][c]
+            f = [splines.pairing_1d(rk[a], ck[a], self.p[a], self.nel[a]) for a in range(3)]
+            kb.append(forms3d._kron3(f[0], f[1], f[2]))
+        self.K2F = sp.block_diag(kb, format="csr")
+
+    def e0_from_d(self, d, t):
+        """M^1_{eps,00} e_0 = K~_2 d - M^1_{eps,0b} e_b(t) (Sec. 3.5, scheme 1)."""
+        return self.S1._lu_e.solve(self.S1.Kt2 @ np.asarray(d, dtype=np.float64) - self.M1_0b @ self.e_b(t))
+
+    def h_from_b(self, b):
+        """M~^1_mu h = K_2 b with b on the whole X^2_h."""
+        return self.S1._lu_h.solve(self.K2F @ np.asarray(b, dtype=np.float64))
 
 
 # ---------------------------------------------------------------- a travelling wave through the cube

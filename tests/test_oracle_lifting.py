@@ -11,7 +11,10 @@ What fixes each part independently of the oracle's own formulas:
   * the lifted leapfrog: with zero data it is scheme 2; on a plane wave that
     crosses the cube (tangential E nonzero on four faces) it converges at the
     rates of Sec. 5.1 (E ~ h^p, D ~ h^(p-1)) on the identity and the curved
-    map, while scheme 2 without the lifting does not converge at all.
+    map, while scheme 2 without the lifting does not converge at all;
+  * scheme 1 with the lifting (Sec. 3.5's first form): its whole-space
+    operators restrict to scheme 1's, zero data gives scheme 1's step, and the
+    plane wave converges at the same rates.
 """
 import numpy as np
 import pytest
@@ -121,15 +124,16 @@ def test_zero_data_is_scheme_2():
     assert not np.any(got[1][L.b_bd])
 
 
-def _plane_wave_errors(p, nel, geometry, lifted=True, T=0.5):
+def _plane_wave_errors(p, nel, geometry, lifted=True, T=0.5, scheme=2, frac=0.1):
     """Relative L2 errors (E, D) of the discrete solution against the plane wave at time T
-    (dt = h / 10, about a third of the CFL limit)."""
+    (dt = frac h; frac = 0.1 is about a third of scheme 2's CFL limit)."""
     E0, B0 = lifting.plane_wave(0.0)
     ET, _ = lifting.plane_wave(T)
-    nst = int(round(T / (0.1 / nel)))
+    nst = int(round(T / (frac / nel)))
     dt = T / nst
     if lifted:
-        L = lifting.LiftedScheme2(p, nel, geometry=geometry, boundary=lifting.plane_wave_boundary())
+        cls = lifting.LiftedScheme2 if scheme == 2 else lifting.LiftedScheme1
+        L = cls(p, nel, geometry=geometry, boundary=lifting.plane_wave_boundary())
         S = L.S
         d = S.project_2form("D", E0)
         b = S.project_2form("BF", B0)
@@ -159,3 +163,31 @@ def test_without_the_lifting_the_wave_is_lost():
     lifted = _plane_wave_errors(2, 8, hodge.IdentityMap())[0]
     homogeneous = _plane_wave_errors(2, 8, hodge.IdentityMap(), lifted=False)[0]
     assert lifted < 0.02 and homogeneous > 0.5
+
+
+def test_scheme1_whole_space_operators_and_zero_data():
+    """Scheme 1 (Sec. 3.3) with the lifting: K_2 and M^1_eps on the whole spaces restrict to the
+    homogeneous ones, and with zero data the lifted step is scheme 1's."""
+    L = lifting.LiftedScheme1(P, NEL, geometry=hodge.SineBumpMap(0.05), eps=2.0, mu=1.5)
+    S = L.S1
+    assert np.array_equal(L.K2F[:, L.b_in].toarray(), S.K2.toarray())
+    np.testing.assert_allclose(L.M1F[L.e_in][:, L.e_in].toarray(), S.M1.matrix().toarray(), rtol=0, atol=1e-14)
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal(S.N_e)
+    b = S.D1 @ rng.standard_normal(S.N_e)
+    e = S.e_from_d(d)
+    ref = S.step(d, b, e, 0.01, 5)
+    bF = np.zeros(L.N_bf)
+    bF[L.b_in] = b
+    got = L.step(d, bF, e, 0.0, 0.01, 5)
+    for g, w in zip((got[0], got[1][L.b_in], got[2], got[3]), ref):
+        assert np.linalg.norm(g - w) <= 1e-13 * np.linalg.norm(w)
+
+
+@pytest.mark.parametrize("p,frac", [(2, 0.05), (3, 0.025)])
+def test_scheme1_plane_wave_converges_at_order_p(p, frac):
+    """Scheme 1's leapfrog error dominates at dt = h/10 for p = 3 (rate 2.5 there, 3.1 at h/40):
+    smaller steps keep the spatial rate visible."""
+    errs = np.array([_plane_wave_errors(p, n, hodge.IdentityMap(), scheme=1, frac=frac) for n in (2, 4, 8)])
+    rates = np.log2(errs[1] / errs[2])
+    assert rates[0] > p - 0.25 and rates[1] > p - 1 - 0.1
