@@ -327,3 +327,32 @@ def plane_wave_boundary(k=np.pi):
     def E2(x, y, z):
         return np.array([0.0 * x, np.cos(k * x), 0.0 * x])
     return [(E1, lambda t: np.cos(k * t)), (E2, lambda t: -np.sin(k * t))]
+
+
+# ---------------------------------------------------------------- the TEM mode of the coaxial cable
+
+def coax_tem(t, k=np.pi):
+    """TEM mode of a coaxial line along z with eps = mu = 1 (Sec. 5.1.2; the textbook mode):
+    E = (x, y, 0) / r^2 sin k(z - t), B = H = (-y, x, 0) / r^2 sin k(z - t).  E is normal to the
+    cylinders r = const (PEC there) and tangential to the planes x = 0, y = 0 and z = const, where
+    the lifting carries it.  Returns (E, B) as callables of the physical point."""
+    def E(x, y, z):
+        s = np.sin(k * (z - t)) / (x * x + y * y)
+        return np.array([x * s, y * s, 0.0 * x])
+
+    def B(x, y, z):
+        s = np.sin(k * (z - t)) / (x * x + y * y)
+        return np.array([-y * s, x * s, 0.0 * x])
+    return E, B
+
+
+def coax_tem_boundary(k=np.pi):
+    """The TEM mode's E as two separable terms: sin k(z - t) = sin kz cos kt - cos kz sin kt."""
+    def E1(x, y, z):
+        s = np.sin(k * z) / (x * x + y * y)
+        return np.array([x * s, y * s, 0.0 * x])
+
+    def E2(x, y, z):
+        s = np.cos(k * z) / (x * x + y * y)
+        return np.array([x * s, y * s, 0.0 * x])
+    return [(E1, lambda t: np.cos(k * t)), (E2, lambda t: -np.sin(k * t))]

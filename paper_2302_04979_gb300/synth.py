@@ -131,6 +131,45 @@ class ShearMap:
                          [0.1 * y, 0.1 * x, 0.8 * one]])
 
 
+class QuarterCoaxNURBS:
+    """The same quarter coaxial cable as a degree-2 NURBS patch (the paper's description of the
+    geometry gives no control points; these are the textbook ones): along y^ the quarter circle as a
+    rational quadratic with control points (1, 0), (1, 1), (0, 1) and weights 1, sqrt(2)/2, 1; along
+    x^ the radius 1 + (sqrt 2 - 1) x^ (degree 1, unchanged by elevation to 2); along z^ the identity.
+    F = (r(x^) C_x(y^), r(x^) C_y(y^), z^): the same domain as ``QuarterCoaxMap`` with a non-uniform
+    angular speed."""
+
+    dr = np.sqrt(2.0) - 1.0
+    w1 = np.sqrt(0.5)
+
+    def _arc(self, y):
+        y = np.asarray(y, dtype=np.float64)
+        b0, b1, b2 = (1.0 - y) ** 2, 2.0 * y * (1.0 - y), y * y
+        den = b0 + self.w1 * b1 + b2
+        cx = (b0 + self.w1 * b1) / den
+        cy = (self.w1 * b1 + b2) / den
+        # derivatives of the quotients
+        d0, d1, d2 = -2.0 * (1.0 - y), 2.0 - 4.0 * y, 2.0 * y
+        dden = d0 + self.w1 * d1 + d2
+        dcx = ((d0 + self.w1 * d1) - cx * dden) / den
+        dcy = ((self.w1 * d1 + d2) - cy * dden) / den
+        return cx, cy, dcx, dcy
+
+    def __call__(self, x, y, z):
+        r = 1.0 + self.dr * np.asarray(x, dtype=np.float64)
+        cx, cy, _, _ = self._arc(y)
+        return r * cx, r * cy, np.asarray(z, dtype=np.float64) + 0.0 * r
+
+    def jacobian(self, x, y, z):
+        x, y, z = np.broadcast_arrays(np.asarray(x, dtype=np.float64), y, z)
+        r = 1.0 + self.dr * x
+        cx, cy, dcx, dcy = self._arc(y)
+        zero, one = np.zeros_like(x), np.ones_like(x)
+        return np.array([[self.dr * cx, r * dcx, zero],
+                         [self.dr * cy, r * dcy, zero],
+                         [zero, zero, one]])
+
+
 class QuarterCoaxMap:
     """The quarter coaxial cable {1 < x^2 + y^2 < 2, x, y > 0, 0 < z < 1}: radius r = 1 + (sqrt 2 - 1) x^
     and angle theta = (pi/2) y^ (the exact annular geometry that a degree-2 NURBS patch also

@@ -11,7 +11,25 @@ from oracle import maxwell as mx
 from paper_2302_04979_gb300 import smx, synth
 from tests.gpu_util import rel_l2
 
-MAPS = {"sine_bump": synth.SineBumpMap(0.05), "shear": synth.ShearMap(), "coax": synth.QuarterCoaxMap()}
+MAPS = {"sine_bump": synth.SineBumpMap(0.05), "shear": synth.ShearMap(), "coax": synth.QuarterCoaxMap(),
+        "coax_nurbs": synth.QuarterCoaxNURBS()}
+
+
+def test_nurbs_coax_traces_the_annulus():
+    """The degree-2 NURBS patch (Sec. 5.1.2) maps onto the quarter annulus exactly: r = 1 + (sqrt 2 - 1) x^
+    at every point, the angle runs monotonically from 0 to pi/2 along y^, and the patch's corners
+    are the polar map's."""
+    m, polar = synth.QuarterCoaxNURBS(), synth.QuarterCoaxMap()
+    x, y, z = synth.uniform(9, 3 * 200, 0.0, 1.0).reshape(3, 200)
+    X, Y, Z = m(x, y, z)
+    np.testing.assert_allclose(np.hypot(X, Y), 1.0 + (np.sqrt(2.0) - 1.0) * x, rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(Z, z)
+    ys = np.linspace(0.0, 1.0, 101)
+    theta = np.arctan2(*m(np.zeros_like(ys), ys, ys)[1::-1])
+    assert theta[0] == 0.0 and abs(theta[-1] - np.pi / 2) < 1e-15 and np.all(np.diff(theta) > 0)
+    for cx in (0.0, 1.0):
+        for cy in (0.0, 1.0):
+            np.testing.assert_allclose(m(cx, cy, 0.5), polar(cx, cy, 0.5), rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("name", sorted(MAPS))
