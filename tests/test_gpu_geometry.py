@@ -1,7 +1,8 @@
 """A general geometry map given by a host callback (SMX_GEOM_CALLBACK, Sec. 2.3) on the GPU: the
 Hodge stars and leapfrog steps through the callback map against the oracle with the same map
 (1e-11), the callback sine bump against the built-in one, and the refined mixed form on the
-sheared domain (1e-5), and scheme 1 on the quarter coaxial cable (Sec. 5.1.2)."""
+sheared domain (1e-5), and scheme 1 on the quarter coaxial cable (Sec. 5.1.2), whose polar map and
+degree-2 NURBS patch both run through the callback."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,8 @@ from tests.gpu_util import rel_l2, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-MAPS = {"sine_bump": synth.SineBumpMap(0.05), "shear": synth.ShearMap(), "coax": synth.QuarterCoaxMap()}
+MAPS = {"sine_bump": synth.SineBumpMap(0.05), "shear": synth.ShearMap(), "coax": synth.QuarterCoaxMap(),
+        "coax_nurbs": synth.QuarterCoaxNURBS()}
 
 
 def _case(name, p=3, nel=(6, 5, 7)):
