@@ -79,6 +79,10 @@ def test_argument_errors(smx):
     assert status(p=3, nel=4, eps=("blocks", -np.ones((2, 2, 2)))) == smx.EMAT
     assert status(p=3, nel=4, geometry="sine_bump", amplitude=0.5) == smx.EGEOM  # det J <= 0 somewhere
     assert status(p=3, nel=4, geometry="sine_bump", eps=lambda x, y, z: 0.0 * x) == smx.EMAT
+    assert status(p=7, nel=2) == smx.EINVAL                        # degrees 2..6
+    assert status(p=2, nel=(4, 801, 4)) == smx.EINVAL             # at most 800 elements per axis
+    assert status(p=3, nel=4, geometry="sine_bump", amplitude=float("nan")) == smx.EINVAL
+    assert status(p=(2, 6, 3), nel=(1, 2, 3)) == smx.OK
 
 
 def test_calls_without_workspace_are_rejected(smx):
@@ -86,6 +90,7 @@ def test_calls_without_workspace_are_rejected(smx):
     lib = smx.library()
     assert lib.smx_hodge_apply(ctx.h, smx.FIELD_B, ctypes.c_void_p(8), ctypes.c_void_p(16)) == smx.ESTATE
     assert lib.smx_step(ctx.h, *([ctypes.c_void_p(8)] * 4), None, None, 0.1, 1) == smx.ESTATE
+    assert lib.smx_step_host(ctx.h, *([ctypes.c_void_p(8)] * 4), None, None, 0.1, 1) == smx.ESTATE
     assert lib.smx_bind_workspace(ctx.h, ctypes.c_void_p(256), 16) == smx.ESTATE
     assert lib.smx_bind_workspace(ctx.h, None, 1 << 30) == smx.EINVAL
     assert lib.smx_strerror(smx.EGEOM).startswith(b"geometry")
