@@ -23,7 +23,11 @@
  * All device work is enqueued on the stream set with smx_set_stream (default
  * the legacy default stream) and returns after enqueue unless stated.
  * Every call returns SMX_OK (0) or a negative status; smx_strerror names it.
- * A call that fails argument checks enqueues nothing.
+ * A call that fails argument checks enqueues nothing.  Unless a call lists
+ * its own errors, these are the only ones it returns: SMX_EINVAL (a null
+ * context or pointer, an out-of-range field, axis, class or count),
+ * SMX_ESTATE (the call needs a bound workspace and none is bound), SMX_ECUDA
+ * (a launch, copy or event call failed).
  */
 #ifndef SMX_H
 #define SMX_H
@@ -175,13 +179,16 @@ int smx_step_scheme1(smx_ctx* ctx, double* d, double* b, double* e, double* h, c
                      const double* amp, double dt, int nsteps, double tol, int maxit, int* max_iters);
 
 /* E_h = 1/2 (e^T K~_2 d + h^T K_2 b) of scheme 1 (Sec. 3.3; equal to 1/2 (e^T M^1 e + h^T M~^1 h)
- * when e, h are the stars of d, b).  Synchronises.  out[0] receives it. */
+ * when e, h are the stars of d, b).  Synchronises.  out[0] receives it.
+ * Errors: SMX_EINVAL, SMX_ESTATE (no workspace, or not a scheme-1 context), SMX_ENONFINITE,
+ * SMX_ECUDA. */
 int smx_energy_scheme1(smx_ctx* ctx, const double* d, const double* b, const double* e, const double* h,
                        double* out);
 
 /* CFL limit of scheme 1 (Sec. 5.2): 2 / sqrt(lambda_max) of D~^1 S_H D^1 S_E by power iteration (as
  * smx_cfl; v, w of N_e, t of N_h, device), with the mass solves to cg_tol in at most cg_maxit
- * iterations. */
+ * iterations.  Errors: those of smx_scheme1_star (a mass solve), SMX_ENONFINITE (a non-finite or
+ * non-positive Rayleigh quotient). */
 int smx_cfl_scheme1(smx_ctx* ctx, int iters, double tol, double* v, double* w, double* t, double cg_tol,
                     int cg_maxit, double* dt_max);
 
@@ -233,7 +240,8 @@ int smx_mode_kernel(const smx_ctx* ctx, int* which);
 int smx_device_status(smx_ctx* ctx);
 
 /* b += alpha * D^1 e: primal curl by the +-1 incidence matrix (Eq. discrete2_faraday,
- * Remark on incidence matrices after Table 1).  e: N_e, b: N_h, device, no aliasing. */
+ * Remark on incidence matrices after Table 1).  e: N_e, b: N_h, device, no aliasing.
+ * Errors: SMX_EINVAL, SMX_ESTATE, SMX_ECUDA (likewise the four calls below). */
 int smx_curl_primal(smx_ctx* ctx, const double* e, double* b, double alpha);
 
 /* d += alpha * (D~^1 h - s * jhat): dual curl plus the current source
@@ -281,7 +289,9 @@ int smx_energy(smx_ctx* ctx, const double* d, const double* b, const double* e,
  * L = D~^1 K~_1^{-1} (Sec. 5.2 CFL), by power iteration on the device from a
  * fixed pseudo-random start; stops after iters or when the Rayleigh quotient
  * changes by less than tol (relative).  Uses 3 device vectors of the caller:
- * v (N_e), w (N_e), t (N_h).  Synchronises the stream. */
+ * v (N_e), w (N_e), t (N_h).  Synchronises the stream.
+ * Errors: SMX_EINVAL, SMX_ESTATE, SMX_ENONFINITE (a non-finite or non-positive
+ * Rayleigh quotient), SMX_ECUDA. */
 int smx_cfl(smx_ctx* ctx, int iters, double tol, double* v, double* w, double* t,
             double* dt_max);
 
@@ -377,7 +387,9 @@ int smx_kernel_work(const smx_ctx* ctx, int cls, int field, double* flops, doubl
  *    (an asynchronous host-to-device copy on the context stream) when another
  *    context used the array last, and clears the intermediate vector itself;
  *  - calls that overlap on the GPU (different streams, or different contexts
- *    without ordering between them) race on the array; serialise them. */
+ *    without ordering between them) race on the array; serialise them.
+ * Errors: SMX_EINVAL (null argument, field not B or D, quadrature Hodge,
+ * stream of another device), SMX_ENOSPACE, SMX_ECUDA. */
 #define SMX_NOALLOC_BYTES (16u << 20)
 int smx_hodge_star_noalloc(smx_ctx* ctx, int field, const double* x, double* out);
 
@@ -429,7 +441,7 @@ int smx_receivers_set(smx_ctx* ctx, int n, const double* xhat);
 /* out (device, 3n) = R e (device, N_e).  Errors: SMX_EINVAL (no receivers), SMX_ECUDA. */
 int smx_receivers_eval(smx_ctx* ctx, const double* e, double* out);
 
-/* ebar (device, N_e) += alpha R^T w (w device, 3n). */
+/* ebar (device, N_e) += alpha R^T w (w device, 3n).  Errors: as smx_receivers_eval, SMX_ESTATE. */
 int smx_receivers_adjoint(smx_ctx* ctx, const double* w, double alpha, double* ebar);
 
 /* New permittivity values on the context's block grid (host, b_x b_y b_z
@@ -446,12 +458,16 @@ int smx_set_material_blocks(smx_ctx* ctx, int field, const double* values);
  * jhat (device N_e or NULL).  Out: dbar, bbar overwritten with dL/dd_n,
  * dL/db_n; amp_bar (device, 1 value, if jhat): dL/ds_n; eps_bar (device, one
  * value per permittivity block, or NULL): += the step's dL/deps.
- * Asynchronous on the context stream. */
+ * Asynchronous on the context stream.  Errors: SMX_EINVAL (null state or
+ * adjoint pointer, dt not finite and positive, eps_bar without a block
+ * permittivity), SMX_ESTATE (no workspace, or an SMX_MIXED context),
+ * SMX_ECUDA. */
 int smx_step_adjoint(smx_ctx* ctx, const double* d_n, const double* d_np1, double* dbar, double* bbar,
                      const double* ebar, const double* jhat, double dt, double* amp_bar, double* eps_bar);
 
 /* Start of the reverse sweep at the last step N: dbar = S_E^T ebar_N (bbar_N
- * is zero), eps_bar += the eps derivative of ebar_N^T S_E d_N. */
+ * is zero), eps_bar += the eps derivative of ebar_N^T S_E d_N.  Errors: as
+ * smx_step_adjoint. */
 int smx_adjoint_terminal(smx_ctx* ctx, const double* d_N, const double* ebar, double* dbar, double* eps_bar);
 
 /* ==== Batched cavities: one persistent launch per leapfrog step ====
@@ -487,7 +503,9 @@ int smx_batch_destroy(smx_batch* batch);
 
 /* Device workspace of the batch (cavity table, work lists, barrier words),
  * caller-allocated as for a context; binding uploads the work lists and picks
- * a default shape (line warps per CTA) that fits shared memory. */
+ * a default shape (line warps per CTA) that fits shared memory.  Binding
+ * errors: SMX_EINVAL (null pointer), SMX_ESTATE (fewer bytes than
+ * smx_batch_workspace_bytes, or not 256-byte aligned), SMX_ECUDA. */
 int smx_batch_workspace_bytes(const smx_batch* batch, size_t* bytes);
 int smx_batch_bind_workspace(smx_batch* batch, void* device_ptr, size_t bytes);
 
@@ -498,7 +516,8 @@ int smx_batch_set_state(smx_batch* batch, int i, double* d, double* b, double* e
                         const double* amp, double dt);
 
 /* nsteps leapfrog steps of every cavity: nsteps launches on the stream (one graph launch when
- * captured). */
+ * captured).  Errors: SMX_EINVAL, SMX_ESTATE (workspace not bound, or a cavity whose state was
+ * never set), SMX_ECUDA. */
 int smx_batch_step(smx_batch* batch, int nsteps);
 
 /* CUDA-graph capture of smx_batch_step (default on; used on a non-default stream).  enable = 0
