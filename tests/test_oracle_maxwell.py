@@ -137,3 +137,27 @@ def test_cfl_scaling_and_stability():
     bad = S.step(d, b, e, 1.05 * dtm, 400)
     assert S.energy(ok[0], ok[1])[0] < 10 * E0
     assert S.energy(bad[0], bad[1])[0] > 1e3 * E0
+
+
+def test_energy_oscillation_shrinks_with_h_and_p():
+    """Sec. 5.1.1 (energy against time, TE mode, dt from the CFL condition): the leapfrog's
+    oscillation of E_h shrinks when the mesh is refined and when the degree is raised, and so does
+    the gap between the mean discrete energy and the exact 1/8."""
+    stats = {}
+    for p, nel in [(3, 2), (3, 4), (4, 2), (4, 4)]:
+        S = mx.Scheme2(p, nel)
+        d = S.project_2form("D", mx.te111_E(0.0))
+        b = np.zeros(S.N_h)
+        e = S.e_from_d(d)
+        dt = 0.5 * S.cfl(tol=1e-8)[0]
+        n = int(np.ceil(2 * np.pi / mx.OMEGA_TE111 / dt))  # one period
+        Es = []
+        for _ in range(n):
+            d, b, e, _ = S.step(d, b, e, dt, 1)
+            Es.append(S.energy(d, b)[0])
+        Es = np.array(Es)
+        stats[(p, nel)] = ((Es.max() - Es.min()) / Es.mean(), abs(Es.mean() - 0.125) / 0.125)
+    for i in range(2):  # 0: oscillation amplitude, 1: error of the mean energy
+        assert stats[(3, 4)][i] < 0.5 * stats[(3, 2)][i]
+        assert stats[(4, 4)][i] < 0.5 * stats[(4, 2)][i]
+        assert stats[(4, 2)][i] < stats[(3, 2)][i] and stats[(4, 4)][i] < stats[(3, 4)][i]
