@@ -219,3 +219,21 @@ def test_coax_tem_mode_converges_on_the_nurbs_map(scheme, p, frac):
     errs = np.array(errs)
     rates = np.log2(errs[1] / errs[2])
     assert rates[0] > p - 0.25 and rates[1] > p - 1 - 0.1
+
+
+def test_both_schemes_reach_errors_of_the_same_size_on_the_cable():
+    """Sec. 5.1.2: on the cable the two schemes' errors are of very similar size, neither clearly
+    ahead (here within a factor of three at p = 2 on 4 elements per direction)."""
+    geom = synth.QuarterCoaxNURBS()
+    T, n = 0.5, 4
+    nst = int(round(T / (0.05 / n)))
+    dt = T / nst
+    errs = []
+    for cls in (lifting.LiftedScheme2, lifting.LiftedScheme1):
+        L = cls(2, n, geometry=geom, boundary=lifting.coax_tem_boundary())
+        E0, B0 = lifting.coax_tem(0.0)
+        d, b = L.S.project_2form("D", E0), L.S.project_2form("BF", B0)
+        d, b, e0, _ = L.step(d, b, L.e0_from_d(d, 0.0), 0.0, dt, nst)
+        ee = L.S.l2_error("EF", L.e_full(e0, T), lifting.coax_tem(T)[0])
+        errs.append(ee[0] / ee[1])
+    assert 1 / 3 < errs[0] / errs[1] < 3
